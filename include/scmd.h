@@ -1,0 +1,246 @@
+/*
+ * scmd.h -- C ABI of libscmd: Sutton-Chen molecular dynamics of free nickel
+ * clusters on one NVIDIA GB300 (sm_103a).
+ *
+ * What it computes (Yakubovich, Sushko, Schramm, Solov'yov, "Kinetics of
+ * liquid-solid phase transition in large nickel clusters", arXiv:1210.3559):
+ *   - the Sutton-Chen potential energy of an isolated cluster (Eq. 1)
+ *       U = eps * sum_i [ 1/2 sum_{j!=i} (a/r_ij)^n - c * sqrt(rho_i) ],
+ *   - with the local density (Eq. 2)  rho_i = sum_{j!=i} (a/r_ij)^m,
+ *   - evaluated, as in the paper's GPU code, as two successive two-body sweeps:
+ *     first every rho_i, then the forces (Sec. II, "Computational approach"),
+ *   - the forces F_i = -dU/dr_i (not printed in the paper; derived from Eq. 1):
+ *       F_i = eps sum_{j!=i} [ n s^n - (c m / 2)(rho_i^-1/2 + rho_j^-1/2) s^m ]
+ *             (r_i - r_j) / r_ij^2,   s = a / r_ij,
+ *   - velocity-Verlet integration with a Langevin thermostat (Sec. II,
+ *     "Computational approach": Verlet integrator, Langevin damping), here in
+ *     the BAOAB splitting, plus plain NVE and a Berendsen weak-coupling option,
+ *     driven by a target temperature that ramps linearly within a call (the
+ *     paper's heating/cooling ramps, Sec. III).
+ *
+ * Units: Angstrom, femtosecond, atomic mass unit, electron-volt, kelvin.
+ * Arrays of 3-vectors are row-major [N][3] doubles (x0 y0 z0 x1 y1 z1 ...).
+ * Several independent clusters ("batch") live in one context, stored back to
+ * back: cluster b owns atoms off_b .. off_b + sizes[b] - 1, off_b = sum_{c<b} sizes[c].
+ *
+ * Conventions shared by every entry point:
+ *   - Ownership: the caller owns every pointer it passes; the library copies
+ *     inputs and never keeps a caller pointer after returning. Device memory is
+ *     owned by the context and freed by md_destroy.
+ *   - Errors: every call returns an md_status and never aborts, prints or traps
+ *     the GPU. After an error the context stays valid for md_last_error and
+ *     md_destroy; MD_ERR_CUDA means a CUDA call failed (message in
+ *     md_last_error) and the context should be destroyed.
+ *   - Streams: all GPU work is ordered on one CUDA stream (md_config.stream, or
+ *     a stream the library creates). Calls that return host data synchronise
+ *     that stream; md_step does not return before its work has completed.
+ *   - Threads: one context must not be used by two host threads at once.
+ *   - No CPU fallback: without a usable sm_103a GPU every call that needs the
+ *     GPU fails with MD_ERR_CUDA.
+ */
+#ifndef SCMD_H
+#define SCMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCMD_ABI_VERSION 1
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID = 1,   /* bad argument (null pointer, size, non-finite input, ...) */
+    MD_ERR_CUDA = 2,      /* a CUDA runtime call failed or no suitable GPU            */
+    MD_ERR_OOM = 3,       /* device or host allocation failed                         */
+    MD_ERR_NONFINITE = 4, /* a force, position or velocity became NaN/Inf on the GPU  */
+    MD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up                       */
+    MD_ERR_STATE = 6      /* call not valid in the context's current state            */
+} md_status;
+
+typedef enum {
+    MD_PREC_FP64 = 0,  /* every pair term, sum and update in IEEE double                 */
+    MD_PREC_MIXED = 1  /* FP32 pair terms and forces; FP64 rho, energies, x and v        */
+} md_precision;
+
+typedef enum {
+    MD_PATH_AUTO = 0,     /* all pairs, or the cell list when rcut_A > 0                */
+    MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
+    MD_PATH_CELLS = 2     /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
+} md_path;
+
+/* Sutton-Chen parameters (Eq. 1, Eq. 2). Paper's Ni set (Sec. II A):
+ * eps_eV = 1.5707e-2, a_A = 3.52, c = 39.432, n = 9, m = 6.
+ * rcut_A <= 0: all pairs. rcut_A > 0: a pair enters both rho and the pair sum
+ * only when r_ij < rcut_A (plain truncation, no shift). */
+typedef struct {
+    double eps_eV;
+    double c;
+    double a_A;
+    int32_t n;
+    int32_t m;
+    double rcut_A;
+} md_sc_params;
+
+/* Context configuration. Zero-initialise, then set what you need. */
+typedef struct {
+    int32_t precision;        /* md_precision                                              */
+    int32_t path;             /* md_path                                                   */
+    int32_t obs_every;        /* md_step records observables every this many steps; 0 = never */
+    int32_t graph_chunk;      /* steps per captured CUDA graph; 0 = library default (256)  */
+    int32_t tune;             /* 0: built-in launch table; 1: autotune at create time      */
+    int32_t obs_capacity;     /* samples kept by md_obs_history (ring); 0 = 4096           */
+    const char* tune_cache;   /* JSON file read/written by the autotuner; NULL = none      */
+    uint64_t stream;          /* cudaStream_t to use; 0 = the library creates one          */
+} md_config;
+
+typedef enum { MD_NVE = 0, MD_LANGEVIN = 1, MD_BERENDSEN = 2 } md_thermo_kind;
+
+/* Thermostat of one md_step call. The target temperature of local step
+ * k = 0..nsteps-1 is T0_K + (T1_K - T0_K) * k / nsteps (a linear ramp; equal
+ * values give a fixed temperature). Langevin: friction gamma_per_ps, Gaussian
+ * noise from Philox4x32-10 keyed by seed with counter (atom, cluster, step).
+ * Berendsen: coupling time tau_ps (> dt). NVE ignores every field but kind. */
+typedef struct {
+    int32_t kind;         /* md_thermo_kind */
+    int32_t reserved;
+    double T0_K;
+    double T1_K;
+    double gamma_per_ps;
+    double tau_ps;
+    uint64_t seed;
+} md_thermostat;
+
+/* Per-cluster observables. E_pot from Eq. 1; E_kin = 1/2 sum m v^2;
+ * T = 2 E_kin / (3 N k_B); com = centre of mass; mom = sum m v (amu A/fs);
+ * angmom = sum m (x - com) x v (amu A^2/fs). status: 0, or MD_ERR_NONFINITE. */
+typedef struct {
+    double epot_eV, ekin_eV, etot_eV, T_K;
+    double com_A[3];
+    double mom[3];
+    double angmom[3];
+    int64_t step;
+    double time_fs;
+    int32_t status;
+    int32_t reserved;
+} md_obs;
+
+typedef struct md_ctx md_ctx;
+
+/* ABI version compiled into the library (SCMD_ABI_VERSION). */
+int32_t md_abi_version(void);
+
+/*
+ * Create a context holding n_clusters independent clusters.
+ *   sizes[n_clusters]   atoms per cluster, each >= 1
+ *   pos_A[Ntot][3]      positions (Angstrom), vel[Ntot][3] velocities (A/fs),
+ *   mass_amu[Ntot]      masses (> 0), Ntot = sum(sizes)
+ * vel_A_per_fs may be NULL (all zero). Every value must be finite. Computes the
+ * forces of the initial state (velocity Verlet needs F at step 0) and sets the
+ * step counter to 0. On success *out receives the context; on failure *out is
+ * NULL and md_last_error(NULL) describes the error (per host thread).
+ */
+md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* sizes,
+                    const double* pos_A, const double* vel_A_per_fs, const double* mass_amu,
+                    const md_sc_params* params, md_ctx** out);
+
+/*
+ * Evaluate the potential energy and forces at the current positions with the
+ * two passes (density, then forces). epot_eV[n_clusters] and
+ * forces_eV_per_A[Ntot][3] are host arrays; either may be NULL.
+ */
+md_status md_energy_forces(md_ctx* ctx, double* epot_eV, double* forces_eV_per_A);
+
+/* Densities rho_i (Eq. 2) of the last force evaluation, host array [Ntot]. */
+md_status md_get_density(md_ctx* ctx, double* rho);
+
+/*
+ * Advance every cluster by nsteps steps of length dt_fs under thermostat th
+ * (NULL = NVE). Work is issued as replays of captured CUDA graphs of
+ * graph_chunk steps; the call returns after the last step completed. Returns
+ * MD_ERR_NONFINITE if any force, position or velocity became non-finite (the
+ * state is then undefined; restore a checkpoint with md_set_state).
+ */
+md_status md_step(md_ctx* ctx, int64_t nsteps, double dt_fs, const md_thermostat* th);
+
+/* Observables of every cluster at the current state (one fresh force
+ * evaluation). out[n_clusters]. */
+md_status md_observables(md_ctx* ctx, md_obs* out);
+
+/*
+ * Observables recorded by md_step every obs_every steps, oldest first.
+ * out receives up to max_samples samples of n_clusters records each
+ * (out[s * n_clusters + b]); *n_samples receives the number written. Samples
+ * older than obs_capacity are dropped. md_clear_history empties the ring.
+ */
+md_status md_obs_history(md_ctx* ctx, md_obs* out, int32_t max_samples, int32_t* n_samples);
+md_status md_clear_history(md_ctx* ctx);
+
+/* Checkpoint: copy positions, velocities (host [Ntot][3]) and the step counter
+ * out of, or into, the context. md_set_state recomputes the forces. Because the
+ * Langevin noise is a pure function of (seed, cluster, atom, step), resuming
+ * from a checkpoint reproduces an uninterrupted run bit for bit. */
+md_status md_get_state(md_ctx* ctx, double* pos_A, double* vel_A_per_fs, int64_t* step);
+md_status md_set_state(md_ctx* ctx, const double* pos_A, const double* vel_A_per_fs, int64_t step);
+
+/* Forces of the current state as held by the context (host [Ntot][3]). */
+md_status md_get_forces(md_ctx* ctx, double* forces_eV_per_A);
+
+/*
+ * Launch shape of the two pair passes: i-atoms per thread (ipt), warps per
+ * CTA (warps) and CTAs per thread-block cluster (cluster). md_get_launch
+ * reads the current choice; md_set_launch overrides it (values outside
+ * ipt in {1,2}, warps in {2,4,8,16}, cluster in {1,2,4,8} -> MD_ERR_INVALID).
+ * which: 0 = density pass, 1 = force pass.
+ */
+md_status md_get_launch(const md_ctx* ctx, int32_t which, int32_t* ipt, int32_t* warps, int32_t* cluster);
+md_status md_set_launch(md_ctx* ctx, int32_t which, int32_t ipt, int32_t warps, int32_t cluster);
+
+/*
+ * Autotuner: time every launch shape of both passes on the context's own
+ * clusters (CUDA events, reps launches each) and keep the fastest. With
+ * cfg.tune_cache set, results are stored in (and later read from) that JSON
+ * file, keyed by GPU name, SM count, precision, path and workload shape.
+ */
+md_status md_autotune(md_ctx* ctx, int32_t reps);
+
+/*
+ * Mean device time (ms) of one launch of the density pass and of the force
+ * pass, timed alone with CUDA events on the context's stream over reps
+ * launches after warm-up. Pair-evaluation counts per launch are returned in
+ * *pairs (ordered pairs visited per pass). Any output may be NULL.
+ */
+md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* ms_force,
+                         double* pairs);
+
+/* Number of GPU kernels issued per md_step step and per graph replay
+ * overhead (launches per chunk), for launch accounting. */
+md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);
+
+/* Last error message of ctx, or of the calling thread's last failed md_create when ctx is NULL. */
+const char* md_last_error(const md_ctx* ctx);
+
+/* Free the context and its device memory. NULL is ignored. */
+void md_destroy(md_ctx* ctx);
+
+/*
+ * Philox4x32-10 (Salmon et al., SC'11) evaluated by the GPU kernel code the
+ * Langevin thermostat uses: in[k*6 .. k*6+5] = (ctr0, ctr1, ctr2, ctr3, key0,
+ * key1), out[k*4 .. k*4+3] = the four output words; host arrays, count >= 0.
+ */
+md_status md_philox4x32_10(const uint32_t* in, uint32_t* out, int32_t count);
+
+/*
+ * The Langevin thermostat's standard normals as the GPU computes them, for
+ * atoms 0..n_atoms-1 of one cluster at one step (Box-Muller on Philox output,
+ * counter (atom, cluster, step lo, step hi), key (seed lo, seed hi)).
+ * precision selects the FP32 (MD_PREC_MIXED) or FP64 transform. out[n_atoms][3].
+ */
+md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int32_t n_atoms,
+                              int32_t precision, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCMD_H */

@@ -1,0 +1,951 @@
+// scmd_api.cu -- host side of the libscmd C ABI (declared in include/scmd.h).
+//
+// A context owns the device-resident state of a batch of clusters and issues,
+// per MD step, the density pass and the force pass (whose epilogue integrates),
+// plus a Berendsen kernel when that thermostat is selected and an observables
+// reduction when a sample is due. md_step replays CUDA graphs that each hold
+// one chunk of steps (origin refresh, step start, 2-3 kernels per step, step
+// counter advance); graphs are cached by chunk length, the observation phase
+// of the chunk's first step, the thermostat kind and the launch shapes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/scmd.h"
+#include "scmd_internal.cuh"
+
+using namespace scmd;
+
+namespace {
+
+// (eV/amu) in (A/fs)^2 = e / u * 1e-10 (e exact SI 2019, u CODATA 2018); k_B in eV/K (exact).
+constexpr double kConv = 1.602176634e-19 / 1.66053906660e-27 * 1.0e-10;
+constexpr double kKB = 8.617333262e-5;
+
+thread_local std::string g_create_error;
+
+struct GraphKey {
+    int M, phase, kind, obs_every;
+    int dens[3], force[3];
+    bool operator<(const GraphKey& o) const {
+        return std::tie(M, phase, kind, obs_every, dens[0], dens[1], dens[2], force[0], force[1], force[2]) <
+               std::tie(o.M, o.phase, o.kind, o.obs_every, o.dens[0], o.dens[1], o.dens[2], o.force[0], o.force[1],
+                        o.force[2]);
+    }
+};
+
+}  // namespace
+
+struct md_ctx {
+    md_config cfg{};
+    Pot pot{};
+    int B = 0;
+    int64_t ntot = 0;
+    int npad = 0, ngroups = 0;
+    std::vector<int32_t> sizes, off, poff, cl_of_group;
+    std::vector<Item> items_h[2];  // ipt 1 and 2
+    Item* items_d[2] = {nullptr, nullptr};
+    Shape shape[2] = {{1, 4, 1}, {1, 4, 1}};  // density, force
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device buffers
+    int32_t *d_poff = nullptr, *d_nreal = nullptr, *d_clg = nullptr, *d_status = nullptr;
+    double *d_x = nullptr, *d_v = nullptr, *d_mass = nullptr, *d_rho = nullptr, *d_origin = nullptr;
+    double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr;
+    void *d_f = nullptr, *d_mirror = nullptr, *d_posg = nullptr;
+    int64_t* d_step = nullptr;
+    Run* d_run = nullptr;
+    // pinned staging
+    double* h_stage = nullptr;
+    size_t h_stage_n = 0;
+    Run* h_run = nullptr;
+    int64_t* h_step = nullptr;
+    // state
+    int64_t step = 0;
+    double time_fs = 0.0;
+    int hist_cap = 4096;
+    std::deque<std::pair<int64_t, double>> samples;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::string err;
+    Dev dev{};
+};
+
+namespace {
+
+md_status fail(md_ctx* c, md_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CK(ctx, call)                                                                             \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            md_status st_ = (e_ == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA;         \
+            return fail(ctx, st_, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                \
+        }                                                                                         \
+    } while (0)
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(p[k])) return false;
+    return true;
+}
+
+int elem_size(const md_ctx* c) { return c->cfg.precision == MD_PREC_MIXED ? 4 : 8; }
+int vec4_size(const md_ctx* c) { return c->cfg.precision == MD_PREC_MIXED ? 16 : 32; }
+
+void fill_dev(md_ctx* c) {
+    Dev& d = c->dev;
+    d.B = c->B;
+    d.npad = c->npad;
+    d.ngroups = c->ngroups;
+    d.prec = c->cfg.precision;
+    d.poff = c->d_poff;
+    d.nreal = c->d_nreal;
+    d.cl_of_group = c->d_clg;
+    d.x = c->d_x;
+    d.v = c->d_v;
+    d.mass = c->d_mass;
+    d.f = c->d_f;
+    d.mirror = c->d_mirror;
+    d.posg = c->d_posg;
+    d.rho = c->d_rho;
+    d.origin = c->d_origin;
+    d.part = c->d_part;
+    d.ke_grp = c->d_ke;
+    d.hist = c->d_hist;
+    d.step_base = c->d_step;
+    d.status = c->d_status;
+    d.run = c->d_run;
+    d.pot = c->pot;
+    d.conv = kConv;
+}
+
+Shape default_shape(const md_ctx* c, int which) {
+    (void)which;
+    const int items = (int)c->items_h[0].size();
+    const int target = 152 * 16;  // warps in flight
+    Shape s{1, 4, 1};
+    int need = (target + items * s.warps - 1) / (items * s.warps);
+    while (s.cluster < need && s.cluster < 8) s.cluster *= 2;
+    return s;
+}
+
+bool shape_ok(Shape s) {
+    return (s.ipt == 1 || s.ipt == 2) && (s.warps == 2 || s.warps == 4 || s.warps == 8 || s.warps == 16) &&
+           (s.cluster == 1 || s.cluster == 2 || s.cluster == 4 || s.cluster == 8);
+}
+
+const Item* items_for(const md_ctx* c, Shape s, int* n) {
+    const int k = s.ipt == 2 ? 1 : 0;
+    *n = (int)c->items_h[k].size();
+    return c->items_d[k];
+}
+
+// Host AoS [N][3] <-> padded SoA [3][npad] via the pinned staging buffer.
+void pack(const md_ctx* c, const double* aos, double* soa) {
+    for (int b = 0; b < c->B; ++b)
+        for (int a = 0; a < c->sizes[b]; ++a) {
+            const int64_t s = (int64_t)c->off[b] + a;
+            const int p = c->poff[b] + a;
+            for (int k = 0; k < 3; ++k) soa[(size_t)k * c->npad + p] = aos[3 * s + k];
+        }
+}
+void unpack(const md_ctx* c, const double* soa, double* aos) {
+    for (int b = 0; b < c->B; ++b)
+        for (int a = 0; a < c->sizes[b]; ++a) {
+            const int64_t s = (int64_t)c->off[b] + a;
+            const int p = c->poff[b] + a;
+            for (int k = 0; k < 3; ++k) aos[3 * s + k] = soa[(size_t)k * c->npad + p];
+        }
+}
+
+md_status upload_state(md_ctx* c, const double* pos, const double* vel) {
+    double* st = c->h_stage;
+    std::fill(st, st + 3 * (size_t)c->npad, 0.0);
+    pack(c, pos, st);
+    CK(c, cudaMemcpyAsync(c->d_x, st, sizeof(double) * 3 * c->npad, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::fill(st, st + 3 * (size_t)c->npad, 0.0);
+    if (vel) pack(c, vel, st);
+    CK(c, cudaMemcpyAsync(c->d_v, st, sizeof(double) * 3 * c->npad, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MD_OK;
+}
+
+md_status set_step_base(md_ctx* c, int64_t s) {
+    *c->h_step = s;
+    CK(c, cudaMemcpyAsync(c->d_step, c->h_step, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    return MD_OK;
+}
+
+// Forces (and optionally observable partials) of the current positions.
+md_status evaluate(md_ctx* c, bool observe) {
+    const Dev& d = c->dev;
+    int n0, n1;
+    const Item* i0 = items_for(c, c->shape[0], &n0);
+    const Item* i1 = items_for(c, c->shape[1], &n1);
+    CK(c, launch_mirror(d, c->stream));
+    CK(c, launch_density(d, i0, n0, c->shape[0], observe ? 1 : 0, c->stream));
+    CK(c, launch_force(d, i1, n1, c->shape[1], observe ? 1 : 0, 0, 0, c->stream));
+    if (observe) CK(c, launch_obs_reduce(d, 0, 0, c->stream));
+    return MD_OK;
+}
+
+md_status reset_origin_and_forces(md_ctx* c) {
+    CK(c, launch_origin(c->dev, c->stream));
+    md_status st = evaluate(c, false);
+    if (st != MD_OK) return st;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MD_OK;
+}
+
+// Issue one chunk of M steps whose first step has global index s0 (only s0 mod obs_every matters).
+md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
+    const Dev& d = c->dev;
+    int n0, n1;
+    const Item* i0 = items_for(c, c->shape[0], &n0);
+    const Item* i1 = items_for(c, c->shape[1], &n1);
+    const int oe = c->cfg.obs_every;
+    CK(c, launch_origin(d, c->stream));
+    CK(c, launch_start(d, 0, c->stream));
+    for (int k = 0; k < M; ++k) {
+        const int64_t next = s0 + k + 1;
+        const bool obs = oe > 0 && next % oe == 0;
+        const bool last = k == M - 1;
+        CK(c, launch_density(d, i0, n0, c->shape[0], obs ? 1 : 0, c->stream));
+        CK(c, launch_force(d, i1, n1, c->shape[1], 2, k, (last ? 1 : 0) | (obs ? 2 : 0), c->stream));
+        if (kind == MD_BERENDSEN) CK(c, launch_berendsen(d, k, last ? 1 : 0, c->stream));
+        if (obs) CK(c, launch_obs_reduce(d, k, 1, c->stream));
+    }
+    CK(c, launch_advance(d, M, c->stream));
+    return MD_OK;
+}
+
+md_status get_graph(md_ctx* c, int M, int64_t s0, int kind, cudaGraphExec_t* out) {
+    GraphKey key{};
+    key.M = M;
+    key.obs_every = c->cfg.obs_every;
+    key.phase = c->cfg.obs_every > 0 ? (int)(s0 % c->cfg.obs_every) : 0;
+    key.kind = kind;
+    key.dens[0] = c->shape[0].ipt;
+    key.dens[1] = c->shape[0].warps;
+    key.dens[2] = c->shape[0].cluster;
+    key.force[0] = c->shape[1].ipt;
+    key.force[1] = c->shape[1].warps;
+    key.force[2] = c->shape[1].cluster;
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+        *out = it->second;
+        return MD_OK;
+    }
+    if (c->graphs.size() >= 32) {
+        for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+        c->graphs.clear();
+    }
+    cudaGraph_t g = nullptr;
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    md_status st = enqueue_chunk(c, M, s0, kind);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != MD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    CK(c, e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(c, e);
+    c->graphs[key] = ex;
+    *out = ex;
+    return MD_OK;
+}
+
+void drop_graphs(md_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+    c->graphs.clear();
+}
+
+void free_all(md_ctx* c) {
+    drop_graphs(c);
+    void* ptrs[] = {c->d_poff, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
+                    c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
+                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_run) cudaFreeHost(c->h_run);
+    if (c->h_step) cudaFreeHost(c->h_step);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+void fill_obs(const md_ctx* c, const double* h, int64_t step, double time_fs, md_obs* o) {
+    o->epot_eV = h[0];
+    o->ekin_eV = h[1];
+    o->etot_eV = h[2];
+    o->T_K = h[3];
+    for (int k = 0; k < 3; ++k) {
+        o->com_A[k] = h[4 + k];
+        o->mom[k] = h[7 + k];
+        o->angmom[k] = h[10 + k];
+    }
+    o->step = step;
+    o->time_fs = time_fs;
+    o->status = h[15] != 0.0 ? MD_ERR_NONFINITE : MD_OK;
+    o->reserved = 0;
+    (void)c;
+}
+
+md_status check_status(md_ctx* c) {
+    int32_t s = 0;
+    CK(c, cudaMemcpyAsync(&s, c->d_status, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (s & 1) return fail(c, MD_ERR_NONFINITE, "a force, position or velocity became non-finite");
+    return MD_OK;
+}
+
+std::string tune_key(const md_ctx* c) {
+    cudaDeviceProp p{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&p, dev);
+    int maxn = 0;
+    for (int s : c->sizes) maxn = std::max(maxn, s);
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|%d|prec%d|rc%g|B%d|N%lld|max%d", p.name, p.multiProcessorCount,
+             c->cfg.precision, c->pot.rcut, c->B, (long long)c->ntot, maxn);
+    std::string k = buf;
+    for (char& ch : k)
+        if (ch == '"' || ch == '\\') ch = '_';
+    return k;
+}
+
+// Tiny JSON cache: {"key": [d_ipt, d_warps, d_cluster, f_ipt, f_warps, f_cluster], ...}
+bool cache_lookup(const char* path, const std::string& key, Shape out[2]) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    std::string s;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
+    fclose(f);
+    const std::string q = "\"" + key + "\"";
+    size_t p = s.find(q);
+    if (p == std::string::npos) return false;
+    p = s.find('[', p);
+    if (p == std::string::npos) return false;
+    int v[6];
+    if (sscanf(s.c_str() + p, "[%d,%d,%d,%d,%d,%d]", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) != 6) return false;
+    Shape a{v[0], v[1], v[2]}, b{v[3], v[4], v[5]};
+    if (!shape_ok(a) || !shape_ok(b)) return false;
+    out[0] = a;
+    out[1] = b;
+    return true;
+}
+
+void cache_store(const char* path, const std::string& key, const Shape s[2]) {
+    if (!path) return;
+    std::map<std::string, std::string> entries;
+    if (FILE* f = fopen(path, "r")) {
+        std::string txt;
+        char buf[4096];
+        size_t n;
+        while ((n = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+        fclose(f);
+        size_t p = 0;
+        while ((p = txt.find('"', p)) != std::string::npos) {
+            size_t e = txt.find('"', p + 1);
+            if (e == std::string::npos) break;
+            std::string k = txt.substr(p + 1, e - p - 1);
+            size_t a = txt.find('[', e), b = txt.find(']', e);
+            if (a == std::string::npos || b == std::string::npos) break;
+            entries[k] = txt.substr(a, b - a + 1);
+            p = b + 1;
+        }
+    }
+    char val[128];
+    snprintf(val, sizeof val, "[%d,%d,%d,%d,%d,%d]", s[0].ipt, s[0].warps, s[0].cluster, s[1].ipt, s[1].warps,
+             s[1].cluster);
+    entries[key] = val;
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t k = 0;
+    for (auto& e : entries) fprintf(f, "  \"%s\": %s%s\n", e.first.c_str(), e.second.c_str(), ++k < entries.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t md_abi_version(void) { return SCMD_ABI_VERSION; }
+
+const char* md_last_error(const md_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* sizes, const double* pos,
+                    const double* vel, const double* mass, const md_sc_params* prm, md_ctx** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, MD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!cfg || !sizes || !pos || !mass || !prm) return fail(nullptr, MD_ERR_INVALID, "NULL argument");
+    if (n_clusters < 1) return fail(nullptr, MD_ERR_INVALID, "n_clusters must be >= 1");
+    if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED)
+        return fail(nullptr, MD_ERR_INVALID, "unknown precision %d", cfg->precision);
+    if (cfg->path != MD_PATH_AUTO && cfg->path != MD_PATH_ALLPAIRS)
+        return fail(nullptr, MD_ERR_INVALID, "path %d is not available in this build", cfg->path);
+    if (cfg->obs_every < 0 || cfg->graph_chunk < 0 || cfg->obs_capacity < 0)
+        return fail(nullptr, MD_ERR_INVALID, "negative obs_every, graph_chunk or obs_capacity");
+    if (!(std::isfinite(prm->eps_eV) && std::isfinite(prm->c) && std::isfinite(prm->a_A) && prm->a_A > 0 &&
+          std::isfinite(prm->rcut_A) && prm->rcut_A >= 0 && prm->n >= 1 && prm->n <= 32 && prm->m >= 1 &&
+          prm->m <= 32))
+        return fail(nullptr, MD_ERR_INVALID, "invalid Sutton-Chen parameters");
+    int64_t ntot = 0;
+    for (int b = 0; b < n_clusters; ++b) {
+        if (sizes[b] < 1) return fail(nullptr, MD_ERR_INVALID, "cluster %d has size %d", b, sizes[b]);
+        ntot += sizes[b];
+    }
+    if (ntot > 200000000) return fail(nullptr, MD_ERR_INVALID, "too many atoms");
+    if (!finite_all(pos, 3 * ntot)) return fail(nullptr, MD_ERR_INVALID, "non-finite position");
+    if (vel && !finite_all(vel, 3 * ntot)) return fail(nullptr, MD_ERR_INVALID, "non-finite velocity");
+    for (int64_t k = 0; k < ntot; ++k)
+        if (!(std::isfinite(mass[k]) && mass[k] > 0)) return fail(nullptr, MD_ERR_INVALID, "mass %lld invalid", (long long)k);
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1)
+        return fail(nullptr, MD_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    if (prop.major < 10) return fail(nullptr, MD_ERR_CUDA, "device %s (sm_%d%d) is not an sm_103a part", prop.name, prop.major, prop.minor);
+
+    md_ctx* c = new md_ctx();
+    c->cfg = *cfg;
+    if (c->cfg.graph_chunk == 0) c->cfg.graph_chunk = 256;
+    c->hist_cap = cfg->obs_capacity > 0 ? cfg->obs_capacity : 4096;
+    c->B = n_clusters;
+    c->ntot = ntot;
+    c->sizes.assign(sizes, sizes + n_clusters);
+    c->off.resize(n_clusters + 1);
+    c->poff.resize(n_clusters + 1);
+    c->off[0] = c->poff[0] = 0;
+    for (int b = 0; b < n_clusters; ++b) {
+        c->off[b + 1] = c->off[b] + sizes[b];
+        c->poff[b + 1] = c->poff[b] + ((sizes[b] + kPad - 1) / kPad) * kPad;
+    }
+    c->npad = c->poff[n_clusters];
+    c->ngroups = c->npad / kGroup;
+    c->cl_of_group.resize(c->ngroups);
+    for (int b = 0; b < n_clusters; ++b)
+        for (int g = c->poff[b] / kGroup; g < c->poff[b + 1] / kGroup; ++g) c->cl_of_group[g] = b;
+    for (int k = 0; k < 2; ++k) {
+        const int BI = 32 * (k + 1);
+        for (int b = 0; b < n_clusters; ++b)
+            for (int a = 0; a < sizes[b]; a += BI) {
+                Item it{};
+                it.i0 = c->poff[b] + a;
+                it.ni = std::min(BI, sizes[b] - a);
+                it.j0 = c->poff[b];
+                it.nj = sizes[b];
+                it.cl = b;
+                c->items_h[k].push_back(it);
+            }
+        // largest clusters first: long items start early, short ones fill the tail
+        std::stable_sort(c->items_h[k].begin(), c->items_h[k].end(),
+                         [](const Item& x, const Item& y) { return x.nj > y.nj; });
+    }
+    // potential constants
+    Pot& P = c->pot;
+    P.eps = prm->eps_eV;
+    P.c = prm->c;
+    P.a = prm->a_A;
+    P.n = prm->n;
+    P.m = prm->m;
+    P.rcut = prm->rcut_A;
+    P.rcut2 = prm->rcut_A > 0 ? prm->rcut_A * prm->rcut_A : 0.0;
+    P.A9 = P.eps * P.n * std::pow(P.a, P.n);
+    P.B6 = P.eps * P.c * P.m * 0.5 * std::pow(P.a, P.m);
+    P.am = std::pow(P.a, P.m);
+    P.ecoef = 0.5 * P.eps * std::pow(P.a, P.n);
+    P.A9f = (float)P.A9;
+    P.rcut2f = (float)P.rcut2;
+    P.special = (P.n == 9 && P.m == 6) ? 1 : 0;
+
+    auto bail = [&](md_status st) {
+        free_all(c);
+        g_create_error = c->err;
+        delete c;
+        return st;
+    };
+#define CKC(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            fail(c, e_ == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA, "%s failed: %s", #call, \
+                 cudaGetErrorString(e_));                                                          \
+            return bail(e_ == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA);               \
+        }                                                                                          \
+    } while (0)
+
+    if (cfg->stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+    } else {
+        CKC(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    CKC(configure_kernels());
+    const size_t np = c->npad;
+    CKC(cudaMalloc(&c->d_poff, sizeof(int32_t) * (n_clusters + 1)));
+    CKC(cudaMalloc(&c->d_nreal, sizeof(int32_t) * n_clusters));
+    CKC(cudaMalloc(&c->d_clg, sizeof(int32_t) * c->ngroups));
+    CKC(cudaMalloc(&c->d_status, sizeof(int32_t)));
+    CKC(cudaMalloc(&c->d_x, sizeof(double) * 3 * np));
+    CKC(cudaMalloc(&c->d_v, sizeof(double) * 3 * np));
+    CKC(cudaMalloc(&c->d_mass, sizeof(double) * np));
+    CKC(cudaMalloc(&c->d_rho, sizeof(double) * np));
+    CKC(cudaMalloc(&c->d_origin, sizeof(double) * 3 * n_clusters));
+    CKC(cudaMalloc(&c->d_part, sizeof(double) * kObsFields * c->ngroups));
+    CKC(cudaMalloc(&c->d_ke, sizeof(double) * c->ngroups));
+    CKC(cudaMalloc(&c->d_hist, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
+    CKC(cudaMalloc(&c->d_f, (size_t)elem_size(c) * 3 * np));
+    CKC(cudaMalloc(&c->d_mirror, (size_t)vec4_size(c) * np));
+    CKC(cudaMalloc(&c->d_posg, (size_t)vec4_size(c) * np));
+    CKC(cudaMalloc(&c->d_step, sizeof(int64_t)));
+    CKC(cudaMalloc(&c->d_run, sizeof(Run)));
+    for (int k = 0; k < 2; ++k) {
+        CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
+        CKC(cudaMemcpy(c->items_d[k], c->items_h[k].data(), sizeof(Item) * c->items_h[k].size(), cudaMemcpyHostToDevice));
+    }
+    c->h_stage_n = std::max<size_t>(4 * np, 16);
+    CKC(cudaMallocHost(&c->h_stage, sizeof(double) * c->h_stage_n));
+    CKC(cudaMallocHost(&c->h_run, sizeof(Run)));
+    CKC(cudaMallocHost(&c->h_step, sizeof(int64_t)));
+    std::vector<int32_t> nreal(sizes, sizes + n_clusters);
+    CKC(cudaMemcpy(c->d_poff, c->poff.data(), sizeof(int32_t) * (n_clusters + 1), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(c->d_nreal, nreal.data(), sizeof(int32_t) * n_clusters, cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(c->d_clg, c->cl_of_group.data(), sizeof(int32_t) * c->ngroups, cudaMemcpyHostToDevice));
+    CKC(cudaMemset(c->d_status, 0, sizeof(int32_t)));
+    CKC(cudaMemset(c->d_part, 0, sizeof(double) * kObsFields * c->ngroups));
+    CKC(cudaMemset(c->d_ke, 0, sizeof(double) * c->ngroups));
+    CKC(cudaMemset(c->d_hist, 0, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
+    CKC(cudaMemset(c->d_f, 0, (size_t)elem_size(c) * 3 * np));
+    CKC(cudaMemset(c->d_rho, 0, sizeof(double) * np));
+    CKC(cudaMemset(c->d_step, 0, sizeof(int64_t)));
+    // masses (padding atoms get mass 1 so that no division by zero can occur)
+    {
+        std::vector<double> m(np, 1.0);
+        for (int b = 0; b < n_clusters; ++b)
+            for (int a = 0; a < sizes[b]; ++a) m[c->poff[b] + a] = mass[c->off[b] + a];
+        CKC(cudaMemcpy(c->d_mass, m.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
+    }
+    // padding atoms of the mirror and posg buffers: far apart and far from everything, g = 0
+    {
+        const bool mixed = cfg->precision == MD_PREC_MIXED;
+        std::vector<unsigned char> pad((size_t)vec4_size(c) * np, 0);
+        for (int b = 0; b < n_clusters; ++b)
+            for (int a = sizes[b]; a < c->poff[b + 1] - c->poff[b]; ++a) {
+                const size_t p = c->poff[b] + a;
+                const double far = (mixed ? 1.0e18 : 1.0e150) * (1.0 + (a - sizes[b]));
+                if (mixed) {
+                    float v[4] = {(float)far, 0.f, 0.f, 0.f};
+                    memcpy(pad.data() + 16 * p, v, 16);
+                } else {
+                    double v[4] = {far, 0.0, 0.0, 0.0};
+                    memcpy(pad.data() + 32 * p, v, 32);
+                }
+            }
+        CKC(cudaMemcpy(c->d_mirror, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_posg, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+    }
+    fill_dev(c);
+    c->shape[0] = default_shape(c, 0);
+    c->shape[1] = default_shape(c, 1);
+    {
+        Shape cached[2];
+        if (cfg->tune_cache && cache_lookup(cfg->tune_cache, tune_key(c), cached)) {
+            c->shape[0] = cached[0];
+            c->shape[1] = cached[1];
+        }
+    }
+    md_status st = upload_state(c, pos, vel);
+    if (st != MD_OK) return bail(st);
+    // Run parameters used by the observable reduction before the first md_step
+    memset(c->h_run, 0, sizeof(Run));
+    c->h_run->kb = kKB;
+    c->h_run->nsteps = 1;
+    c->h_run->hist_cap = c->hist_cap;
+    c->h_run->obs_every = c->cfg.obs_every;
+    CKC(cudaMemcpyAsync(c->d_run, c->h_run, sizeof(Run), cudaMemcpyHostToDevice, c->stream));
+    st = reset_origin_and_forces(c);
+    if (st != MD_OK) return bail(st);
+    if (cfg->tune == 1) {
+        st = md_autotune(c, 10);
+        if (st != MD_OK) return bail(st);
+    }
+#undef CKC
+    *out = c;
+    return MD_OK;
+}
+
+void md_destroy(md_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+md_status md_energy_forces(md_ctx* c, double* epot, double* forces) {
+    if (!c) return MD_ERR_INVALID;
+    md_status st = evaluate(c, true);
+    if (st != MD_OK) return st;
+    if (epot) {
+        double* h = c->h_stage;
+        CK(c, cudaMemcpyAsync(h, c->d_hist + (size_t)c->hist_cap * c->B * kHistFields,
+                              sizeof(double) * kHistFields * c->B, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (int b = 0; b < c->B; ++b) epot[b] = h[(size_t)b * kHistFields];
+    }
+    if (forces) {
+        st = md_get_forces(c, forces);
+        if (st != MD_OK) return st;
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_status(c);
+}
+
+md_status md_get_forces(md_ctx* c, double* forces) {
+    if (!c || !forces) return MD_ERR_INVALID;
+    double* st = c->h_stage;
+    if (c->cfg.precision == MD_PREC_MIXED) {
+        float* tmp = reinterpret_cast<float*>(st + 3 * (size_t)c->npad);
+        CK(c, cudaMemcpyAsync(tmp, c->d_f, sizeof(float) * 3 * c->npad, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (size_t k = 0; k < 3 * (size_t)c->npad; ++k) st[k] = tmp[k];
+    } else {
+        CK(c, cudaMemcpyAsync(st, c->d_f, sizeof(double) * 3 * c->npad, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    unpack(c, st, forces);
+    return MD_OK;
+}
+
+md_status md_get_density(md_ctx* c, double* rho) {
+    if (!c || !rho) return MD_ERR_INVALID;
+    double* st = c->h_stage;
+    CK(c, cudaMemcpyAsync(st, c->d_rho, sizeof(double) * c->npad, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->B; ++b)
+        for (int a = 0; a < c->sizes[b]; ++a) rho[c->off[b] + a] = st[c->poff[b] + a];
+    return MD_OK;
+}
+
+md_status md_step(md_ctx* c, int64_t nsteps, double dt, const md_thermostat* th) {
+    if (!c) return MD_ERR_INVALID;
+    if (nsteps < 0) return fail(c, MD_ERR_INVALID, "nsteps < 0");
+    if (nsteps == 0) return MD_OK;
+    if (!(std::isfinite(dt) && dt > 0)) return fail(c, MD_ERR_INVALID, "dt must be finite and > 0");
+    md_thermostat nve{};
+    nve.kind = MD_NVE;
+    const md_thermostat& t = th ? *th : nve;
+    if (t.kind != MD_NVE && t.kind != MD_LANGEVIN && t.kind != MD_BERENDSEN)
+        return fail(c, MD_ERR_INVALID, "unknown thermostat kind %d", t.kind);
+    if (t.kind != MD_NVE && !(std::isfinite(t.T0_K) && std::isfinite(t.T1_K) && t.T0_K >= 0 && t.T1_K >= 0))
+        return fail(c, MD_ERR_INVALID, "invalid target temperatures");
+    if (t.kind == MD_LANGEVIN && !(std::isfinite(t.gamma_per_ps) && t.gamma_per_ps >= 0))
+        return fail(c, MD_ERR_INVALID, "invalid Langevin friction");
+    if (t.kind == MD_BERENDSEN && !(std::isfinite(t.tau_ps) && t.tau_ps * 1e3 > dt))
+        return fail(c, MD_ERR_INVALID, "Berendsen tau must exceed dt");
+    Run& r = *c->h_run;
+    memset(&r, 0, sizeof r);
+    r.dt = dt;
+    r.h = 0.5 * dt;
+    r.c1 = t.kind == MD_LANGEVIN ? std::exp(-t.gamma_per_ps * 1e-3 * dt) : 1.0;
+    r.noise_k = t.kind == MD_LANGEVIN ? (1.0 - r.c1 * r.c1) * kKB * kConv : 0.0;
+    r.T0 = t.T0_K;
+    r.T1 = t.T1_K;
+    r.dt_over_tau = t.kind == MD_BERENDSEN ? dt / (t.tau_ps * 1e3) : 0.0;
+    r.kb = kKB;
+    r.step0 = c->step;
+    r.nsteps = nsteps;
+    r.seed = t.seed;
+    r.kind = t.kind;
+    r.obs_every = c->cfg.obs_every;
+    r.hist_cap = c->hist_cap;
+    CK(c, cudaMemcpyAsync(c->d_run, c->h_run, sizeof(Run), cudaMemcpyHostToDevice, c->stream));
+    md_status st = set_step_base(c, c->step);
+    if (st != MD_OK) return st;
+    const int chunk = c->cfg.graph_chunk;
+    int64_t done = 0;
+    const double t_call0 = c->time_fs;
+    while (done < nsteps) {
+        const int M = (int)std::min<int64_t>(chunk, nsteps - done);
+        cudaGraphExec_t ex = nullptr;
+        st = get_graph(c, M, c->step + done, t.kind, &ex);
+        if (st != MD_OK) return st;
+        CK(c, cudaGraphLaunch(ex, c->stream));
+        done += M;
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    // bookkeeping of recorded samples
+    const int oe = c->cfg.obs_every;
+    if (oe > 0) {
+        for (int64_t s = ((c->step / oe) + 1) * oe; s <= c->step + nsteps; s += oe) {
+            c->samples.emplace_back(s, t_call0 + (double)(s - c->step) * dt);
+            if ((int)c->samples.size() > c->hist_cap) c->samples.pop_front();
+        }
+    }
+    c->step += nsteps;
+    c->time_fs = t_call0 + (double)nsteps * dt;
+    return check_status(c);
+}
+
+md_status md_observables(md_ctx* c, md_obs* out) {
+    if (!c || !out) return MD_ERR_INVALID;
+    md_status st = evaluate(c, true);
+    if (st != MD_OK) return st;
+    double* h = c->h_stage;
+    CK(c, cudaMemcpyAsync(h, c->d_hist + (size_t)c->hist_cap * c->B * kHistFields, sizeof(double) * kHistFields * c->B,
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->B; ++b) fill_obs(c, h + (size_t)b * kHistFields, c->step, c->time_fs, out + b);
+    return check_status(c);
+}
+
+md_status md_obs_history(md_ctx* c, md_obs* out, int32_t max_samples, int32_t* n_samples) {
+    if (!c || !n_samples || (max_samples > 0 && !out)) return MD_ERR_INVALID;
+    const int n = std::min<int>((int)c->samples.size(), std::max(0, max_samples));
+    *n_samples = n;
+    if (n == 0) return MD_OK;
+    std::vector<double> h((size_t)kHistFields * c->B * c->hist_cap);
+    CK(c, cudaMemcpyAsync(h.data(), c->d_hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const size_t first = c->samples.size() - n;
+    for (int s = 0; s < n; ++s) {
+        const auto& smp = c->samples[first + s];
+        const int slot = (int)((smp.first / c->cfg.obs_every) % c->hist_cap);
+        for (int b = 0; b < c->B; ++b)
+            fill_obs(c, h.data() + ((size_t)slot * c->B + b) * kHistFields, smp.first, smp.second, out + (size_t)s * c->B + b);
+    }
+    return MD_OK;
+}
+
+md_status md_clear_history(md_ctx* c) {
+    if (!c) return MD_ERR_INVALID;
+    c->samples.clear();
+    return MD_OK;
+}
+
+md_status md_get_state(md_ctx* c, double* pos, double* vel, int64_t* step) {
+    if (!c) return MD_ERR_INVALID;
+    double* st = c->h_stage;
+    if (pos) {
+        CK(c, cudaMemcpyAsync(st, c->d_x, sizeof(double) * 3 * c->npad, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        unpack(c, st, pos);
+    }
+    if (vel) {
+        CK(c, cudaMemcpyAsync(st, c->d_v, sizeof(double) * 3 * c->npad, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        unpack(c, st, vel);
+    }
+    if (step) *step = c->step;
+    return MD_OK;
+}
+
+md_status md_set_state(md_ctx* c, const double* pos, const double* vel, int64_t step) {
+    if (!c || !pos || !vel) return MD_ERR_INVALID;
+    if (step < 0) return fail(c, MD_ERR_INVALID, "step < 0");
+    if (!finite_all(pos, 3 * c->ntot) || !finite_all(vel, 3 * c->ntot))
+        return fail(c, MD_ERR_INVALID, "non-finite position or velocity");
+    md_status st = upload_state(c, pos, vel);
+    if (st != MD_OK) return st;
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
+    c->step = step;
+    st = reset_origin_and_forces(c);
+    if (st != MD_OK) return st;
+    return check_status(c);
+}
+
+md_status md_get_launch(const md_ctx* c, int32_t which, int32_t* ipt, int32_t* warps, int32_t* cluster) {
+    if (!c || which < 0 || which > 1) return MD_ERR_INVALID;
+    if (ipt) *ipt = c->shape[which].ipt;
+    if (warps) *warps = c->shape[which].warps;
+    if (cluster) *cluster = c->shape[which].cluster;
+    return MD_OK;
+}
+
+md_status md_set_launch(md_ctx* c, int32_t which, int32_t ipt, int32_t warps, int32_t cluster) {
+    if (!c || which < 0 || which > 1) return MD_ERR_INVALID;
+    Shape s{ipt, warps, cluster};
+    if (!shape_ok(s)) return fail(c, MD_ERR_INVALID, "launch shape (%d,%d,%d) not supported", ipt, warps, cluster);
+    c->shape[which] = s;
+    drop_graphs(c);
+    return MD_OK;
+}
+
+md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, double* pairs) {
+    if (!c || reps < 1) return MD_ERR_INVALID;
+    const Dev& d = c->dev;
+    int n0, n1;
+    const Item* i0 = items_for(c, c->shape[0], &n0);
+    const Item* i1 = items_for(c, c->shape[1], &n1);
+    CK(c, launch_mirror(d, c->stream));
+    for (int w = 0; w < 3; ++w) {
+        CK(c, launch_density(d, i0, n0, c->shape[0], 0, c->stream));
+        CK(c, launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream));
+    }
+    std::vector<cudaEvent_t> ev(2 * reps + 2);
+    for (auto& e : ev) CK(c, cudaEventCreate(&e));
+    double td = 0, tf = 0;
+    md_status st = MD_OK;
+    for (int k = 0; k < reps && st == MD_OK; ++k) {
+        cudaEventRecord(ev[2 * k], c->stream);
+        if (launch_density(d, i0, n0, c->shape[0], 0, c->stream) != cudaSuccess) st = MD_ERR_CUDA;
+        cudaEventRecord(ev[2 * k + 1], c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < reps && st == MD_OK; ++k) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+        td += ms;
+    }
+    for (int k = 0; k < reps && st == MD_OK; ++k) {
+        cudaEventRecord(ev[2 * k], c->stream);
+        if (launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream) != cudaSuccess) st = MD_ERR_CUDA;
+        cudaEventRecord(ev[2 * k + 1], c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < reps && st == MD_OK; ++k) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+        tf += ms;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
+    if (ms_d) *ms_d = td / reps;
+    if (ms_f) *ms_f = tf / reps;
+    if (pairs) {
+        double p = 0;
+        for (int s : c->sizes) p += (double)s * (double)(s - 1);
+        *pairs = p;
+    }
+    return MD_OK;
+}
+
+md_status md_autotune(md_ctx* c, int32_t reps) {
+    if (!c || reps < 1) return MD_ERR_INVALID;
+    const Dev& d = c->dev;
+    const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[4] = {1, 2, 4, 8};
+    Shape best[2] = {c->shape[0], c->shape[1]};
+    float best_t[2] = {1e30f, 1e30f};
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    CK(c, launch_mirror(d, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int which = 0; which < 2; ++which)
+        for (int ip : ipts)
+            for (int w : warps)
+                for (int cl : clus) {
+                    Shape s{ip, w, cl};
+                    int n;
+                    const Item* it = items_for(c, s, &n);
+                    auto run = [&]() {
+                        return which == 0 ? launch_density(d, it, n, s, 0, c->stream)
+                                          : launch_force(d, it, n, s, 0, 0, 0, c->stream);
+                    };
+                    // feasibility: the cluster shape must be schedulable
+                    if (run() != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    run();
+                    cudaEventRecord(e0, c->stream);
+                    for (int k = 0; k < reps; ++k) run();
+                    cudaEventRecord(e1, c->stream);
+                    CK(c, cudaEventSynchronize(e1));
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_t[which]) {
+                        best_t[which] = ms;
+                        best[which] = s;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->shape[0] = best[0];
+    c->shape[1] = best[1];
+    drop_graphs(c);
+    cache_store(c->cfg.tune_cache, tune_key(c), c->shape);
+    // the forces must again belong to the current state
+    md_status st = evaluate(c, false);
+    if (st != MD_OK) return st;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MD_OK;
+}
+
+md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
+    if (!c) return MD_ERR_INVALID;
+    if (per_step) *per_step = 2;
+    if (per_chunk) *per_chunk = 3;
+    return MD_OK;
+}
+
+md_status md_philox4x32_10(const uint32_t* in, uint32_t* out, int32_t count) {
+    if (count < 0 || (count > 0 && (!in || !out))) return fail(nullptr, MD_ERR_INVALID, "bad arguments");
+    if (count == 0) return MD_OK;
+    uint32_t *din = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&din, sizeof(uint32_t) * 6 * count);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(uint32_t) * 4 * count);
+    if (e == cudaSuccess) e = cudaMemcpy(din, in, sizeof(uint32_t) * 6 * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(din, dout, count, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(uint32_t) * 4 * count, cudaMemcpyDeviceToHost);
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, MD_ERR_CUDA, "philox: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
+md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int32_t n_atoms, int32_t precision,
+                              double* out) {
+    if (n_atoms < 0 || (n_atoms > 0 && !out)) return fail(nullptr, MD_ERR_INVALID, "bad arguments");
+    if (n_atoms == 0) return MD_OK;
+    double* dout = nullptr;
+    cudaError_t e = cudaMalloc(&dout, sizeof(double) * 3 * n_atoms);
+    if (e == cudaSuccess) e = launch_normals(seed, cluster, step, n_atoms, precision, dout, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToHost);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, MD_ERR_CUDA, "normals: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
+}  // extern "C"

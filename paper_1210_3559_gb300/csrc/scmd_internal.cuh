@@ -1,0 +1,130 @@
+// scmd_internal.cuh -- internal types shared by the kernels and the host API of libscmd.
+//
+// Data layout in HBM (per context; Ntot real atoms, Npad padded):
+//   * every cluster's atoms occupy a contiguous padded segment whose length is
+//     a multiple of kPad (64) so that 32- and 64-atom i-blocks and 32-atom
+//     j-tiles never straddle two clusters;
+//   * FP64 state (positions x, velocities v) in structure-of-arrays form
+//     x[3][Npad], v[3][Npad]; masses m[Npad];
+//   * forces F[3][Npad] in the pass precision (float for MIXED, double for FP64);
+//   * "mirror": the positions the density pass reads, relative to a per-cluster
+//     origin (the cluster's centre of mass at the start of a graph chunk), as
+//     float4(x, y, z, 0) or, in FP64 mode, double4;
+//   * "posg": what the force pass reads, (x, y, z, B6 * rho^-1/2) per atom,
+//     written by the density pass;
+//   * rho[Npad] (FP64) and per-32-atom-group observable partials.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace scmd {
+
+constexpr int kPad = 64;        // per-cluster padding granularity (atoms)
+constexpr int kGroup = 32;      // atoms per observable partial record (one warp)
+constexpr int kObsFields = 16;  // doubles per observable partial record
+constexpr int kMaxWarps = 16;
+constexpr int kMaxCluster = 8;
+
+// Fields of an observable partial record (per 32-atom group).
+enum ObsField {
+    OF_EEMB = 0,   // sum over the group of -eps c sqrt(rho_i)                (eV)
+    OF_EPAIR = 1,  // sum over the group of sum_j r_ij^-n   (times 1/2 eps a^n later)
+    OF_KE2 = 2,    // sum m v^2                                               (amu A^2/fs^2)
+    OF_P = 3,      // sum m v (3)
+    OF_MX = 6,     // sum m x (3), absolute frame
+    OF_L = 9,      // sum m x cross v (3), absolute frame
+    OF_MASS = 12,  // sum m
+    OF_BAD = 13,   // number of non-finite values seen
+};
+
+// One work item of a pair pass: an i-block of one cluster.
+struct Item {
+    int32_t i0;   // padded global index of the first i atom
+    int32_t ni;   // real atoms in this block (<= 32 * ipt)
+    int32_t j0;   // padded global index of the cluster's first atom
+    int32_t nj;   // real atoms in the cluster
+    int32_t cl;   // cluster index
+    int32_t pad;
+};
+
+// Derived potential constants.
+struct Pot {
+    double eps, c, a, rcut, rcut2;
+    int n, m;
+    double A9;   // eps * n * a^n        (force, repulsive part)
+    double B6;   // eps * c * m / 2 * a^m (force, embedding part; multiplies rho^-1/2)
+    double am;   // a^m                  (density scale)
+    double ecoef;// 1/2 eps a^n          (pair energy scale)
+    float A9f, rcut2f;
+    int special; // 1 when (n, m) = (9, 6): compile-time exponents
+};
+
+// Integrator / thermostat parameters of the current md_step call (device resident).
+struct Run {
+    double dt, h;            // step, half step (fs)
+    double c1;               // Langevin exp(-gamma dt)
+    double noise_k;          // (1 - c1^2) k_B * conv  (sigma_i^2 = noise_k * T / m_i)
+    double T0, T1;           // ramp end points
+    double dt_over_tau;      // Berendsen
+    double kb;               // k_B
+    int64_t step0;           // global step at the start of the call
+    int64_t nsteps;          // steps of the call
+    uint64_t seed;
+    int32_t kind;            // md_thermo_kind
+    int32_t obs_every;       // 0 = never
+    int32_t hist_cap;        // ring capacity (samples)
+    int32_t pad;
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    int32_t B;           // clusters
+    int32_t npad;        // padded atoms
+    int32_t ngroups;     // npad / 32
+    int32_t prec;        // md_precision
+    const int32_t* poff; // [B+1] padded offsets
+    const int32_t* nreal;// [B] real atoms per cluster
+    const int32_t* cl_of_group; // [ngroups] cluster of each 32-atom group
+    double* x;           // [3][npad]
+    double* v;           // [3][npad]
+    const double* mass;  // [npad]
+    void* f;             // [3][npad] float or double
+    void* mirror;        // float4 / double4 [npad]
+    void* posg;          // float4 / double4 [npad]
+    double* rho;         // [npad]
+    double* origin;      // [B][3]
+    double* part;        // [ngroups][kObsFields]
+    double* ke_grp;      // [ngroups] sum m v^2 (Berendsen)
+    double* hist;        // ring [cap][B][kHistFields]
+    int64_t* step_base;  // [1] global step of local step 0 of the running chunk
+    int32_t* status;     // [1] bit 0: non-finite value
+    Run* run;            // device copy of Run
+    Pot pot;
+    double conv;         // (eV/amu) in (A/fs)^2
+};
+
+constexpr int kHistFields = 20;  // doubles per history record (see md_obs packing in the API)
+
+// ---------------------------------------------------------------- launchers
+struct Shape { int ipt, warps, cluster; };
+
+// Kernels are launched through these wrappers (defined in scmd_kernels.cu).
+cudaError_t launch_mirror(const Dev& d, cudaStream_t s);
+cudaError_t launch_origin(const Dev& d, cudaStream_t s);
+cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s);
+// mode: 0 = forces only (store F), 1 = forces + all observable partials (no integration),
+//       2 = MD step: finish the half kick, record observables if due, start the next step unless last.
+// flags (mode 2): bit 0 = last step of the chunk, bit 1 = observables are due at the end of this step.
+cudaError_t launch_force(const Dev& d, const Item* items, int nitems, Shape sh, int mode, int k_local,
+                         int flags, cudaStream_t s);
+cudaError_t launch_start(const Dev& d, int k_local, cudaStream_t s);
+cudaError_t launch_berendsen(const Dev& d, int k_local, int last, cudaStream_t s);
+cudaError_t launch_obs_reduce(const Dev& d, int k_local, int slot_mode, cudaStream_t s);
+cudaError_t launch_advance(const Dev& d, int nsteps, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t s);
+cudaError_t launch_normals(uint64_t seed, uint32_t cluster, int64_t step, int n, int prec, double* out,
+                           cudaStream_t s);
+size_t pass_smem_bytes(int prec, Shape sh);
+cudaError_t configure_kernels();
+
+}  // namespace scmd

@@ -1,0 +1,891 @@
+// scmd_kernels.cu -- sm_103a kernels of the Sutton-Chen cluster MD hot path.
+//
+// Per MD step two pair passes run, the paper's "two successive two-body
+// problems" (Sec. II, "Computational approach"):
+//   density pass  rho_i = a^m sum_{j!=i} r_ij^-m                      (Eq. 2)
+//   force pass    F_i = sum_{j!=i} r_ij^-2 [A r_ij^-n - B (g_i + g_j) r_ij^-m] (r_i - r_j)
+//                 with A = eps n a^n, B = eps c m/2 a^m, g = rho^-1/2  (-dU/dr of Eq. 1)
+// and the force pass's epilogue finishes the velocity-Verlet step and starts the
+// next one (BAOAB Langevin, NVE, or the Berendsen split) for the atoms it owns.
+//
+// Work decomposition of a pair pass (no tensor cores: the work is FP32 SIMT
+// arithmetic plus one MUFU reciprocal / reciprocal square root per pair):
+//   * a work item is an i-block of 32*IPT atoms of one cluster; each thread
+//     keeps IPT i-atoms in registers;
+//   * the item's j-range (all atoms of the cluster, in 32-atom tiles) is split
+//     over the W warps of a CTA and the C CTAs of a thread-block cluster; each
+//     warp stages its own j-tile in shared memory with one coalesced 16-byte
+//     load per lane and reads it back with broadcast loads;
+//   * per-thread partial sums are reduced over warps in shared memory and over
+//     the CTAs of the cluster through distributed shared memory, in a fixed
+//     order (results are run-to-run deterministic); the cluster's rank-0 CTA
+//     owns the epilogue.
+// Precision (MIXED): pair terms in FP32 on COM-relative FP32 coordinates; each
+// 32-pair tile is summed in FP32, tiles are summed in FP32 spans of 4 tiles,
+// spans are folded into FP64 (density, energy) or into FP32 running sums
+// (forces); reductions over warps/CTAs are FP64 (density, energy) or FP32
+// (forces); positions and velocities are integrated in FP64.
+// Precision (FP64): every operation in IEEE double.
+#include <cooperative_groups.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "scmd_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace scmd {
+
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+template <int PREC> struct Tr;
+template <> struct Tr<1> {
+    using R = float;
+    using V4 = float4;
+};
+template <> struct Tr<0> {
+    using R = double;
+    using V4 = dbl4;
+};
+
+// PTX approximate reciprocal / reciprocal square root (one MUFU op each).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float inv_r2(float r2) { return rcp_approx(r2); }
+__device__ __forceinline__ double inv_r2(double r2) { return 1.0 / r2; }
+__device__ __forceinline__ float inv_r(float r2) { return rsqrt_approx(r2); }
+__device__ __forceinline__ double inv_r(double r2) { return rsqrt(r2); }
+
+template <class R> __device__ __forceinline__ R ipow(R b, int e) {
+    R r = R(1);
+    for (int k = 0; k < e; ++k) r *= b;
+    return r;
+}
+// r^-k from ir = r^-1 and inv = r^-2 (runtime exponent)
+template <class R> __device__ __forceinline__ R rpow(R inv, R ir, int k) {
+    R p = ipow(inv, k >> 1);
+    return (k & 1) ? p * ir : p;
+}
+
+template <class R> __device__ __forceinline__ R big();
+template <> __device__ __forceinline__ float big<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double big<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------ Philox / normals
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint32_t lo0 = M0 * c[0], hi0 = __umulhi(M0, c[0]);
+        const uint32_t lo1 = M1 * c[2], hi1 = __umulhi(M1, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// Three standard normals for (atom, cluster, step): Box-Muller on (w0,w1), (w2,w3).
+__device__ __forceinline__ void normals_f32(uint64_t seed, uint32_t cl, int64_t step, uint32_t atom, float z[3]) {
+    uint32_t c[4] = {atom, cl, (uint32_t)((uint64_t)step & 0xffffffffu), (uint32_t)((uint64_t)step >> 32)};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    const float s32 = 2.3283064365386963e-10f;  // 2^-32
+    const float u1 = fmaf((float)c[0], s32, s32), u2 = fmaf((float)c[1], s32, s32);
+    const float u3 = fmaf((float)c[2], s32, s32), u4 = fmaf((float)c[3], s32, s32);
+    const float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * u2, &s1, &c1);
+    sincospif(2.0f * u4, &s2, &c2);
+    z[0] = r1 * c1;
+    z[1] = r1 * s1;
+    z[2] = r2 * c2;
+}
+__device__ __forceinline__ void normals_f64(uint64_t seed, uint32_t cl, int64_t step, uint32_t atom, double z[3]) {
+    uint32_t c[4] = {atom, cl, (uint32_t)((uint64_t)step & 0xffffffffu), (uint32_t)((uint64_t)step >> 32)};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    const double s32 = 2.3283064365386963e-10;
+    const double u1 = ((double)c[0] + 1.0) * s32, u2 = ((double)c[1] + 1.0) * s32;
+    const double u3 = ((double)c[2] + 1.0) * s32, u4 = ((double)c[3] + 1.0) * s32;
+    const double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u3));
+    double s1, c1, s2, c2;
+    sincospi(2.0 * u2, &s1, &c1);
+    sincospi(2.0 * u4, &s2, &c2);
+    z[0] = r1 * c1;
+    z[1] = r1 * s1;
+    z[2] = r2 * c2;
+}
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double ramp_T(const Run& r, int64_t step) {
+    const double k = (double)(step - r.step0);
+    return r.T0 + (r.T1 - r.T0) * k / (double)r.nsteps;
+}
+
+template <int PREC> __device__ __forceinline__ void store_mirror(const Dev& d, int i, int cl, double x, double y, double z) {
+    using V4 = typename Tr<PREC>::V4;
+    const double* o = d.origin + 3 * cl;
+    V4 p;
+    p.x = (typename Tr<PREC>::R)(x - o[0]);
+    p.y = (typename Tr<PREC>::R)(y - o[1]);
+    p.z = (typename Tr<PREC>::R)(z - o[2]);
+    p.w = 0;
+    reinterpret_cast<V4*>(d.mirror)[i] = p;
+}
+
+template <int PREC> __device__ __forceinline__ void load_force(const Dev& d, int i, double& fx, double& fy, double& fz) {
+    using R = typename Tr<PREC>::R;
+    const R* f = reinterpret_cast<const R*>(d.f);
+    fx = (double)f[i];
+    fy = (double)f[d.npad + i];
+    fz = (double)f[2 * d.npad + i];
+}
+
+// Start of a step for one atom from (x, v, F): B, then A O A (Langevin) or A A (NVE, Berendsen).
+template <int PREC>
+__device__ __forceinline__ void begin_step(const Dev& d, const Run& r, int i, int cl, int atom, int64_t step,
+                                           double fx, double fy, double fz) {
+    const int np = d.npad;
+    const double hs = r.h * d.conv / d.mass[i];
+    double vx = d.v[i] + hs * fx, vy = d.v[np + i] + hs * fy, vz = d.v[2 * np + i] + hs * fz;
+    double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
+    if (r.kind == 1) {
+        x += r.h * vx;
+        y += r.h * vy;
+        z += r.h * vz;
+        const double T = ramp_T(r, step);
+        const double sig = sqrt(fmax(r.noise_k * T / d.mass[i], 0.0));
+        if (PREC == 1) {
+            float zz[3];
+            normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
+            const float sf = (float)sig;
+            vx = r.c1 * vx + (double)(sf * zz[0]);
+            vy = r.c1 * vy + (double)(sf * zz[1]);
+            vz = r.c1 * vz + (double)(sf * zz[2]);
+        } else {
+            double zz[3];
+            normals_f64(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
+            vx = r.c1 * vx + sig * zz[0];
+            vy = r.c1 * vy + sig * zz[1];
+            vz = r.c1 * vz + sig * zz[2];
+        }
+        x += r.h * vx;
+        y += r.h * vy;
+        z += r.h * vz;
+    } else {
+        x += r.dt * vx;
+        y += r.dt * vy;
+        z += r.dt * vz;
+    }
+    d.v[i] = vx;
+    d.v[np + i] = vy;
+    d.v[2 * np + i] = vz;
+    d.x[i] = x;
+    d.x[np + i] = y;
+    d.x[2 * np + i] = z;
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+        atomicOr(d.status, 1);
+    store_mirror<PREC>(d, i, cl, x, y, z);
+}
+
+// Velocity-dependent observable partials of one warp-group (lane values -> lane 0 writes).
+__device__ __forceinline__ void obs_velocity_partials(const Dev& d, int group, bool real, double m, double x, double y,
+                                                      double z, double vx, double vy, double vz, int lane) {
+    double ke2 = real ? m * (vx * vx + vy * vy + vz * vz) : 0.0;
+    double px = real ? m * vx : 0.0, py = real ? m * vy : 0.0, pz = real ? m * vz : 0.0;
+    double lx = real ? m * (y * vz - z * vy) : 0.0;
+    double ly = real ? m * (z * vx - x * vz) : 0.0;
+    double lz = real ? m * (x * vy - y * vx) : 0.0;
+    ke2 = warp_sum(ke2);
+    px = warp_sum(px);
+    py = warp_sum(py);
+    pz = warp_sum(pz);
+    lx = warp_sum(lx);
+    ly = warp_sum(ly);
+    lz = warp_sum(lz);
+    if (lane == 0) {
+        double* p = d.part + (size_t)group * kObsFields;
+        p[OF_KE2] = ke2;
+        p[OF_P] = px;
+        p[OF_P + 1] = py;
+        p[OF_P + 2] = pz;
+        p[OF_L] = lx;
+        p[OF_L + 1] = ly;
+        p[OF_L + 2] = lz;
+    }
+}
+__device__ __forceinline__ void obs_position_partials(const Dev& d, int group, bool real, double m, double x, double y,
+                                                      double z, int lane) {
+    double mx = real ? m * x : 0.0, my = real ? m * y : 0.0, mz = real ? m * z : 0.0, mm = real ? m : 0.0;
+    mx = warp_sum(mx);
+    my = warp_sum(my);
+    mz = warp_sum(mz);
+    mm = warp_sum(mm);
+    if (lane == 0) {
+        double* p = d.part + (size_t)group * kObsFields;
+        p[OF_MX] = mx;
+        p[OF_MX + 1] = my;
+        p[OF_MX + 2] = mz;
+        p[OF_MASS] = mm;
+    }
+}
+
+// ------------------------------------------------------------- density pass
+// Shared memory: tiles [W][32] V4 | red [W][32*IPT] double | cta [32*IPT] double
+template <int PREC, int IPT, int SPECIAL, int CUT>
+__global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __restrict__ items, int C, int obs) {
+    using R = typename Tr<PREC>::R;
+    using V4 = typename Tr<PREC>::V4;
+    constexpr int BI = 32 * IPT;
+    extern __shared__ __align__(32) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster.block_rank();
+    const Item it = items[blockIdx.x / C];
+    V4* tiles = reinterpret_cast<V4*>(smem);
+    double* red = reinterpret_cast<double*>(smem + (size_t)W * 32 * sizeof(V4));
+    double* cta = red + W * BI;
+    const V4* mir = reinterpret_cast<const V4*>(d.mirror);
+    const R rc2 = (R)d.pot.rcut2;
+    const int mexp = d.pot.m;
+
+    R xi[IPT], yi[IPT], zi[IPT];
+    double racc[IPT];
+    R sacc[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const V4 p = mir[it.i0 + lane + 32 * q];
+        xi[q] = p.x;
+        yi[q] = p.y;
+        zi[q] = p.z;
+        racc[q] = 0.0;
+        sacc[q] = R(0);
+    }
+    const int ntile = (it.nj + 31) >> 5;
+    const int Q = C * W, qi = rank * W + warp;
+    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
+    const int tdiag = (it.i0 - it.j0) >> 5;
+    V4* tile = tiles + warp * 32;
+    int span = 0;
+    for (int t = t_beg; t < t_end; ++t) {
+        const int jb = it.j0 + (t << 5);
+        __syncwarp();
+        tile[lane] = mir[jb + lane];
+        __syncwarp();
+        const int valid = min(32, it.nj - (t << 5));
+        const bool diag = (t >= tdiag) && (t < tdiag + IPT);
+        R tacc[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) tacc[q] = R(0);
+        if (!diag && valid == 32) {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const V4 p = tile[k];
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) {
+                    const R dx = xi[q] - p.x, dy = yi[q] - p.y, dz = zi[q] - p.z;
+                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    if (CUT) r2 = (r2 < rc2) ? r2 : big<R>();
+                    if (SPECIAL) {
+                        const R inv = inv_r2(r2);
+                        tacc[q] = fma(inv * inv, inv, tacc[q]);
+                    } else {
+                        const R ir = inv_r(r2);
+                        tacc[q] += rpow(ir * ir, ir, mexp);
+                    }
+                }
+            }
+        } else {
+            for (int k = 0; k < valid; ++k) {
+                const V4 p = tile[k];
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) {
+                    const R dx = xi[q] - p.x, dy = yi[q] - p.y, dz = zi[q] - p.z;
+                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    if (CUT) r2 = (r2 < rc2) ? r2 : big<R>();
+                    if (jb + k == it.i0 + lane + 32 * q) r2 = big<R>();
+                    if (SPECIAL) {
+                        const R inv = inv_r2(r2);
+                        tacc[q] = fma(inv * inv, inv, tacc[q]);
+                    } else {
+                        const R ir = inv_r(r2);
+                        tacc[q] += rpow(ir * ir, ir, mexp);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) sacc[q] += tacc[q];
+        if (++span == 4) {
+            span = 0;
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                racc[q] += (double)sacc[q];
+                sacc[q] = R(0);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) red[warp * BI + q * 32 + lane] = racc[q] + (double)sacc[q];
+    __syncthreads();
+    if (threadIdx.x < BI) {
+        double s = 0.0;
+        for (int w = 0; w < W; ++w) s += red[w * BI + threadIdx.x];
+        cta[threadIdx.x] = s;
+    }
+    cluster.sync();
+    if (rank == 0 && threadIdx.x < BI) {
+        double tot = 0.0;
+        for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(cta + threadIdx.x, r);
+        const int t = threadIdx.x, i = it.i0 + t;
+        const bool real = t < it.ni;
+        const double rho = tot * d.pot.am;
+        V4 p = mir[i];
+        if (real) {
+            d.rho[i] = rho;
+            if (PREC == 1) {
+                const float rf = (float)rho;
+                float y = rsqrt_approx(rf);
+                y = y * (1.5f - 0.5f * rf * y * y);  // one Newton step
+                p.w = rho > 0.0 ? (float)d.pot.B6 * y : 0.0f;
+            } else {
+                p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
+            }
+            reinterpret_cast<V4*>(d.posg)[i] = p;
+        }
+        if (obs) {
+            double e = real ? -d.pot.eps * d.pot.c * sqrt(rho) : 0.0;
+            e = warp_sum(e);
+            if (lane == 0) d.part[(size_t)(i >> 5) * kObsFields + OF_EEMB] = e;
+        }
+    }
+    cluster.sync();
+}
+
+// --------------------------------------------------------------- force pass
+// Shared memory: tiles [W][32] V4 | redf [W][32*IPT][3] R | rede [W][32*IPT] double
+//                | ctaf [32*IPT][3] R | ctae [32*IPT] double
+template <int PREC, int IPT, int SPECIAL, int CUT, int ENERGY>
+__global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __restrict__ items, int C, int mode, int k_local,
+                                               int last) {
+    using R = typename Tr<PREC>::R;
+    using V4 = typename Tr<PREC>::V4;
+    constexpr int BI = 32 * IPT;
+    extern __shared__ __align__(32) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster.block_rank();
+    const Item it = items[blockIdx.x / C];
+    V4* tiles = reinterpret_cast<V4*>(smem);
+    double* rede = reinterpret_cast<double*>(smem + (size_t)W * 32 * sizeof(V4));
+    double* ctae = rede + W * BI;
+    R* redf = reinterpret_cast<R*>(ctae + BI);
+    R* ctaf = redf + W * BI * 3;
+    const V4* pg = reinterpret_cast<const V4*>(d.posg);
+    const R A = (R)d.pot.A9;
+    const R rc2 = (R)d.pot.rcut2;
+    const int nexp = d.pot.n, mexp = d.pot.m;
+
+    R xi[IPT], yi[IPT], zi[IPT], gi[IPT];
+    R fx[IPT], fy[IPT], fz[IPT], sx[IPT], sy[IPT], sz[IPT];
+    R es[IPT];
+    double ea[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const V4 p = pg[it.i0 + lane + 32 * q];
+        xi[q] = p.x;
+        yi[q] = p.y;
+        zi[q] = p.z;
+        gi[q] = p.w;
+        fx[q] = fy[q] = fz[q] = R(0);
+        sx[q] = sy[q] = sz[q] = R(0);
+        es[q] = R(0);
+        ea[q] = 0.0;
+    }
+    const int ntile = (it.nj + 31) >> 5;
+    const int Q = C * W, qi = rank * W + warp;
+    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
+    const int tdiag = (it.i0 - it.j0) >> 5;
+    V4* tile = tiles + warp * 32;
+    int span = 0;
+    for (int t = t_beg; t < t_end; ++t) {
+        const int jb = it.j0 + (t << 5);
+        __syncwarp();
+        tile[lane] = pg[jb + lane];
+        __syncwarp();
+        const int valid = min(32, it.nj - (t << 5));
+        const bool diag = (t >= tdiag) && (t < tdiag + IPT);
+        R tx[IPT], ty[IPT], tz[IPT], te[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) tx[q] = ty[q] = tz[q] = te[q] = R(0);
+#define SCMD_FORCE_BODY(MASK)                                                  \
+    {                                                                          \
+        const V4 p = tile[k];                                                  \
+        _Pragma("unroll") for (int q = 0; q < IPT; ++q) {                      \
+            const R dx = xi[q] - p.x, dy = yi[q] - p.y, dz = zi[q] - p.z;      \
+            R r2 = fma(dx, dx, fma(dy, dy, dz * dz));                          \
+            if (CUT) r2 = (r2 < rc2) ? r2 : big<R>();                          \
+            if (MASK && jb + k == it.i0 + lane + 32 * q) r2 = big<R>();        \
+            const R ir = inv_r(r2);                                            \
+            const R inv = ir * ir;                                             \
+            R coef, rn;                                                        \
+            if (SPECIAL) {                                                     \
+                const R inv2 = inv * inv, inv4 = inv2 * inv2;                  \
+                coef = inv4 * fma(A, inv * ir, -(gi[q] + p.w));                \
+                rn = inv4 * ir;                                                \
+            } else {                                                           \
+                rn = rpow(inv, ir, nexp);                                      \
+                const R rm = rpow(inv, ir, mexp);                              \
+                coef = inv * (A * rn - (gi[q] + p.w) * rm);                    \
+            }                                                                  \
+            tx[q] = fma(coef, dx, tx[q]);                                      \
+            ty[q] = fma(coef, dy, ty[q]);                                      \
+            tz[q] = fma(coef, dz, tz[q]);                                      \
+            if (ENERGY) te[q] += rn;                                           \
+        }                                                                      \
+    }
+        if (!diag && valid == 32) {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) SCMD_FORCE_BODY(false)
+        } else {
+            for (int k = 0; k < valid; ++k) SCMD_FORCE_BODY(true)
+        }
+#undef SCMD_FORCE_BODY
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            sx[q] += tx[q];
+            sy[q] += ty[q];
+            sz[q] += tz[q];
+            if (ENERGY) es[q] += te[q];
+        }
+        if (++span == 4) {
+            span = 0;
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                fx[q] += sx[q];
+                fy[q] += sy[q];
+                fz[q] += sz[q];
+                sx[q] = sy[q] = sz[q] = R(0);
+                if (ENERGY) {
+                    ea[q] += (double)es[q];
+                    es[q] = R(0);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int s = warp * BI + q * 32 + lane;
+        redf[3 * s + 0] = fx[q] + sx[q];
+        redf[3 * s + 1] = fy[q] + sy[q];
+        redf[3 * s + 2] = fz[q] + sz[q];
+        if (ENERGY) rede[s] = ea[q] + (double)es[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < BI) {
+        R ax = R(0), ay = R(0), az = R(0);
+        double ae = 0.0;
+        for (int w = 0; w < W; ++w) {
+            const int s = w * BI + threadIdx.x;
+            ax += redf[3 * s];
+            ay += redf[3 * s + 1];
+            az += redf[3 * s + 2];
+            if (ENERGY) ae += rede[s];
+        }
+        ctaf[3 * threadIdx.x] = ax;
+        ctaf[3 * threadIdx.x + 1] = ay;
+        ctaf[3 * threadIdx.x + 2] = az;
+        if (ENERGY) ctae[threadIdx.x] = ae;
+    }
+    cluster.sync();
+    if (rank == 0 && threadIdx.x < BI) {
+        R Fx = R(0), Fy = R(0), Fz = R(0);
+        double Ep = 0.0;
+        for (int r = 0; r < C; ++r) {
+            const R* rf = cluster.map_shared_rank(ctaf, r);
+            Fx += rf[3 * threadIdx.x];
+            Fy += rf[3 * threadIdx.x + 1];
+            Fz += rf[3 * threadIdx.x + 2];
+            if (ENERGY) Ep += *cluster.map_shared_rank(ctae + threadIdx.x, r);
+        }
+        const int t = threadIdx.x, i = it.i0 + t, np = d.npad;
+        const bool real = t < it.ni;
+        R* fo = reinterpret_cast<R*>(d.f);
+        if (real) {
+            fo[i] = Fx;
+            fo[np + i] = Fy;
+            fo[2 * np + i] = Fz;
+            if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+        }
+        const int group = i >> 5;
+        const double m = real ? d.mass[i] : 0.0;
+        if (mode == 1) {
+            // fresh evaluation: all observable partials at the current (x, v)
+            if (ENERGY) {
+                const double e = warp_sum(real ? Ep : 0.0);
+                if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
+            }
+            const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
+            const double vx = real ? d.v[i] : 0.0, vy = real ? d.v[np + i] : 0.0, vz = real ? d.v[2 * np + i] : 0.0;
+            obs_velocity_partials(d, group, real, m, x, y, z, vx, vy, vz, lane);
+            obs_position_partials(d, group, real, m, x, y, z, lane);
+        } else if (mode == 2) {
+            const Run r = *d.run;
+            const int64_t step = *d.step_base + k_local;  // this pass completes step -> step + 1
+            double vx = 0.0, vy = 0.0, vz = 0.0;
+            if (real) {
+                const double hs = r.h * d.conv / m;
+                vx = d.v[i] + hs * (double)Fx;
+                vy = d.v[np + i] + hs * (double)Fy;
+                vz = d.v[2 * np + i] + hs * (double)Fz;
+                d.v[i] = vx;
+                d.v[np + i] = vy;
+                d.v[2 * np + i] = vz;
+            }
+            const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
+            if (ENERGY) {  // observables are due at step + 1 (the host only enables ENERGY then)
+                const double e = warp_sum(real ? Ep : 0.0);
+                if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
+                obs_position_partials(d, group, real, m, x, y, z, lane);
+                if (r.kind != 2) obs_velocity_partials(d, group, real, m, x, y, z, vx, vy, vz, lane);
+            }
+            if (r.kind == 2) {
+                const double ke2 = warp_sum(real ? m * (vx * vx + vy * vy + vz * vz) : 0.0);
+                if (lane == 0) d.ke_grp[group] = ke2;
+            } else if (!last && real) {
+                const int cl = it.cl;
+                begin_step<PREC>(d, r, i, cl, i - it.j0, step + 1, (double)Fx, (double)Fy, (double)Fz);
+            }
+        }
+    }
+    cluster.sync();
+}
+
+// ------------------------------------------------------------ per-atom kernels
+// One 32-thread CTA per 32-atom group; the group's cluster comes from a table.
+template <int PREC> __global__ void k_start(const Dev d, int k_local) {
+    const int g = blockIdx.x, lane = threadIdx.x, i = g * 32 + lane;
+    const int cl = d.cl_of_group[g];
+    const int a = i - d.poff[cl];
+    if (a >= d.nreal[cl]) return;
+    const Run r = *d.run;
+    double fx, fy, fz;
+    load_force<PREC>(d, i, fx, fy, fz);
+    begin_step<PREC>(d, r, i, cl, a, *d.step_base + k_local, fx, fy, fz);
+}
+
+template <int PREC> __global__ void k_berendsen(const Dev d, int k_local, int last) {
+    const int g = blockIdx.x, lane = threadIdx.x, i = g * 32 + lane;
+    const int cl = d.cl_of_group[g];
+    const int g0 = d.poff[cl] >> 5, g1 = d.poff[cl + 1] >> 5;
+    double ke2 = 0.0;
+    for (int k = g0 + lane; k < g1; k += 32) ke2 += d.ke_grp[k];
+    ke2 = warp_sum(ke2);
+    const Run r = *d.run;
+    const int64_t step = *d.step_base + k_local;  // completed step -> step + 1
+    const int n = d.nreal[cl];
+    const double T_inst = ke2 / (d.conv * 3.0 * n * r.kb);
+    const double Tt = ramp_T(r, step);
+    const double lam = T_inst > 0.0 ? sqrt(1.0 + r.dt_over_tau * (Tt / T_inst - 1.0)) : 1.0;
+    const int a = i - d.poff[cl];
+    const bool real = a < n;
+    const int np = d.npad;
+    double vx = 0.0, vy = 0.0, vz = 0.0, m = 0.0;
+    if (real) {
+        m = d.mass[i];
+        vx = d.v[i] * lam;
+        vy = d.v[np + i] * lam;
+        vz = d.v[2 * np + i] * lam;
+        d.v[i] = vx;
+        d.v[np + i] = vy;
+        d.v[2 * np + i] = vz;
+    }
+    const int64_t next = step + 1;
+    if (r.obs_every > 0 && next % r.obs_every == 0) {
+        const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
+        obs_velocity_partials(d, g, real, m, x, y, z, vx, vy, vz, lane);
+    }
+    if (!last && real) {
+        double fx, fy, fz;
+        load_force<PREC>(d, i, fx, fy, fz);
+        begin_step<PREC>(d, r, i, cl, a, next, fx, fy, fz);
+    }
+}
+
+// Mirror of the current positions relative to the cluster origins.
+template <int PREC> __global__ void k_mirror(const Dev d) {
+    const int g = blockIdx.x, lane = threadIdx.x, i = g * 32 + lane;
+    const int cl = d.cl_of_group[g];
+    if (i - d.poff[cl] >= d.nreal[cl]) return;
+    store_mirror<PREC>(d, i, cl, d.x[i], d.x[d.npad + i], d.x[2 * d.npad + i]);
+}
+
+// Origin of each cluster = its centre of mass (one CTA of 32 threads per cluster).
+__global__ void k_origin(const Dev d) {
+    const int cl = blockIdx.x, lane = threadIdx.x;
+    const int b = d.poff[cl], n = d.nreal[cl], np = d.npad;
+    double sx = 0.0, sy = 0.0, sz = 0.0, sm = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double m = d.mass[b + k];
+        sx += m * d.x[b + k];
+        sy += m * d.x[np + b + k];
+        sz += m * d.x[2 * np + b + k];
+        sm += m;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    sz = warp_sum(sz);
+    sm = warp_sum(sm);
+    if (lane == 0) {
+        d.origin[3 * cl] = sm > 0.0 ? sx / sm : 0.0;
+        d.origin[3 * cl + 1] = sm > 0.0 ? sy / sm : 0.0;
+        d.origin[3 * cl + 2] = sm > 0.0 ? sz / sm : 0.0;
+    }
+}
+
+// Observables of every cluster from the group partials (one CTA of 32 threads per cluster).
+// slot_mode 0: the "current" slot (index hist_cap); 1: ring slot of step base + k_local + 1.
+__global__ void k_obs_reduce(const Dev d, int k_local, int slot_mode) {
+    const int cl = blockIdx.x, lane = threadIdx.x;
+    const int g0 = d.poff[cl] >> 5, g1 = d.poff[cl + 1] >> 5;
+    double s[kObsFields];
+#pragma unroll
+    for (int f = 0; f < kObsFields; ++f) s[f] = 0.0;
+    for (int g = g0 + lane; g < g1; g += 32) {
+        const double* p = d.part + (size_t)g * kObsFields;
+#pragma unroll
+        for (int f = 0; f < 13; ++f) s[f] += p[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 13; ++f) s[f] = warp_sum(s[f]);
+    if (lane != 0) return;
+    const Run r = *d.run;
+    const int64_t step = *d.step_base + k_local + (slot_mode ? 1 : 0);
+    const int slot = slot_mode ? (int)((step / r.obs_every) % r.hist_cap) : r.hist_cap;
+    double* h = d.hist + ((size_t)slot * d.B + cl) * kHistFields;
+    const int n = d.nreal[cl];
+    const double epot = s[OF_EEMB] + d.pot.ecoef * s[OF_EPAIR];
+    const double ekin = 0.5 * s[OF_KE2] / d.conv;
+    const double M = s[OF_MASS];
+    double com[3];
+    for (int k = 0; k < 3; ++k) com[k] = M > 0.0 ? s[OF_MX + k] / M : 0.0;
+    const double* P = s + OF_P;
+    h[0] = epot;
+    h[1] = ekin;
+    h[2] = epot + ekin;
+    h[3] = n > 0 ? 2.0 * ekin / (3.0 * n * r.kb) : 0.0;
+    h[4] = com[0];
+    h[5] = com[1];
+    h[6] = com[2];
+    h[7] = P[0];
+    h[8] = P[1];
+    h[9] = P[2];
+    h[10] = s[OF_L] - (com[1] * P[2] - com[2] * P[1]);
+    h[11] = s[OF_L + 1] - (com[2] * P[0] - com[0] * P[2]);
+    h[12] = s[OF_L + 2] - (com[0] * P[1] - com[1] * P[0]);
+    h[13] = (double)step;
+    h[14] = 0.0;  // time is filled in by the host from the step
+    const bool bad = !isfinite(h[2]) || ((*d.status) & 1);
+    h[15] = bad ? 1.0 : 0.0;
+}
+
+__global__ void k_advance(const Dev d, int n) { *d.step_base += n; }
+
+__global__ void k_philox(const uint32_t* in, uint32_t* out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t c[4] = {in[6 * k], in[6 * k + 1], in[6 * k + 2], in[6 * k + 3]};
+    philox4x32_10(c, in[6 * k + 4], in[6 * k + 5]);
+    for (int w = 0; w < 4; ++w) out[4 * k + w] = c[w];
+}
+
+__global__ void k_normals(uint64_t seed, uint32_t cl, int64_t step, int n, int prec, double* out) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    if (prec == 1) {
+        float z[3];
+        normals_f32(seed, cl, step, (uint32_t)a, z);
+        for (int c = 0; c < 3; ++c) out[3 * a + c] = (double)z[c];
+    } else {
+        double z[3];
+        normals_f64(seed, cl, step, (uint32_t)a, z);
+        for (int c = 0; c < 3; ++c) out[3 * a + c] = z[c];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+size_t pass_smem_bytes(int prec, Shape sh) {
+    const size_t v4 = prec == 1 ? sizeof(float4) : sizeof(dbl4);
+    const size_t r = prec == 1 ? sizeof(float) : sizeof(double);
+    const size_t BI = 32 * (size_t)sh.ipt, W = sh.warps;
+    const size_t tiles = W * 32 * v4;
+    const size_t dens = (W + 1) * BI * sizeof(double);
+    const size_t force = (W + 1) * BI * sizeof(double) + (W + 1) * BI * 3 * r;
+    return tiles + (dens > force ? dens : force);
+}
+
+template <class K, class... Args>
+static cudaError_t launch_cluster(K kernel, int grid, int threads, size_t smem, int C, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int PREC, int IPT, int SPECIAL, int CUT>
+static cudaError_t density_t(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s) {
+    return launch_cluster(k_density<PREC, IPT, SPECIAL, CUT>, nitems * sh.cluster, sh.warps * 32,
+                          pass_smem_bytes(PREC, sh), sh.cluster, s, d, items, sh.cluster, obs);
+}
+template <int PREC, int IPT, int SPECIAL, int CUT, int ENERGY>
+static cudaError_t force_t(const Dev& d, const Item* items, int nitems, Shape sh, int mode, int k_local, int last,
+                           cudaStream_t s) {
+    return launch_cluster(k_force<PREC, IPT, SPECIAL, CUT, ENERGY>, nitems * sh.cluster, sh.warps * 32,
+                          pass_smem_bytes(PREC, sh), sh.cluster, s, d, items, sh.cluster, mode, k_local, last);
+}
+
+template <int PREC, int IPT>
+static cudaError_t density_p(const Dev& d, const Item* it, int n, Shape sh, int obs, cudaStream_t s) {
+    const bool sp = d.pot.special != 0, cut = d.pot.rcut > 0.0;
+    if (sp && !cut) return density_t<PREC, IPT, 1, 0>(d, it, n, sh, obs, s);
+    if (sp && cut) return density_t<PREC, IPT, 1, 1>(d, it, n, sh, obs, s);
+    if (!sp && !cut) return density_t<PREC, IPT, 0, 0>(d, it, n, sh, obs, s);
+    return density_t<PREC, IPT, 0, 1>(d, it, n, sh, obs, s);
+}
+template <int PREC, int IPT, int ENERGY>
+static cudaError_t force_p(const Dev& d, const Item* it, int n, Shape sh, int mode, int k, int last, cudaStream_t s) {
+    const bool sp = d.pot.special != 0, cut = d.pot.rcut > 0.0;
+    if (sp && !cut) return force_t<PREC, IPT, 1, 0, ENERGY>(d, it, n, sh, mode, k, last, s);
+    if (sp && cut) return force_t<PREC, IPT, 1, 1, ENERGY>(d, it, n, sh, mode, k, last, s);
+    if (!sp && !cut) return force_t<PREC, IPT, 0, 0, ENERGY>(d, it, n, sh, mode, k, last, s);
+    return force_t<PREC, IPT, 0, 1, ENERGY>(d, it, n, sh, mode, k, last, s);
+}
+
+cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (d.prec == 1)
+        return sh.ipt == 2 ? density_p<1, 2>(d, items, nitems, sh, obs, s) : density_p<1, 1>(d, items, nitems, sh, obs, s);
+    return sh.ipt == 2 ? density_p<0, 2>(d, items, nitems, sh, obs, s) : density_p<0, 1>(d, items, nitems, sh, obs, s);
+}
+
+cudaError_t launch_force(const Dev& d, const Item* items, int nitems, Shape sh, int mode, int k_local, int flags,
+                         cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    // ENERGY (pair-energy accumulation in the inner loop) is compiled in for fresh
+    // evaluations (mode 1) and for MD steps whose end is an observation (flag bit 1).
+    const bool energy = (mode == 1) || (mode == 2 && (flags & 2));
+    const int lst = flags & 1;
+    if (d.prec == 1) {
+        if (sh.ipt == 2)
+            return energy ? force_p<1, 2, 1>(d, items, nitems, sh, mode, k_local, lst, s)
+                          : force_p<1, 2, 0>(d, items, nitems, sh, mode, k_local, lst, s);
+        return energy ? force_p<1, 1, 1>(d, items, nitems, sh, mode, k_local, lst, s)
+                      : force_p<1, 1, 0>(d, items, nitems, sh, mode, k_local, lst, s);
+    }
+    if (sh.ipt == 2)
+        return energy ? force_p<0, 2, 1>(d, items, nitems, sh, mode, k_local, lst, s)
+                      : force_p<0, 2, 0>(d, items, nitems, sh, mode, k_local, lst, s);
+    return energy ? force_p<0, 1, 1>(d, items, nitems, sh, mode, k_local, lst, s)
+                  : force_p<0, 1, 0>(d, items, nitems, sh, mode, k_local, lst, s);
+}
+
+cudaError_t launch_start(const Dev& d, int k_local, cudaStream_t s) {
+    if (d.prec == 1)
+        k_start<1><<<d.ngroups, 32, 0, s>>>(d, k_local);
+    else
+        k_start<0><<<d.ngroups, 32, 0, s>>>(d, k_local);
+    return cudaGetLastError();
+}
+cudaError_t launch_berendsen(const Dev& d, int k_local, int last, cudaStream_t s) {
+    if (d.prec == 1)
+        k_berendsen<1><<<d.ngroups, 32, 0, s>>>(d, k_local, last);
+    else
+        k_berendsen<0><<<d.ngroups, 32, 0, s>>>(d, k_local, last);
+    return cudaGetLastError();
+}
+cudaError_t launch_mirror(const Dev& d, cudaStream_t s) {
+    if (d.prec == 1)
+        k_mirror<1><<<d.ngroups, 32, 0, s>>>(d);
+    else
+        k_mirror<0><<<d.ngroups, 32, 0, s>>>(d);
+    return cudaGetLastError();
+}
+cudaError_t launch_origin(const Dev& d, cudaStream_t s) {
+    k_origin<<<d.B, 32, 0, s>>>(d);
+    return cudaGetLastError();
+}
+cudaError_t launch_obs_reduce(const Dev& d, int k_local, int slot_mode, cudaStream_t s) {
+    k_obs_reduce<<<d.B, 32, 0, s>>>(d, k_local, slot_mode);
+    return cudaGetLastError();
+}
+cudaError_t launch_advance(const Dev& d, int n, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(d, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_philox<<<(n + 127) / 128, 128, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_normals(uint64_t seed, uint32_t cl, int64_t step, int n, int prec, double* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_normals<<<(n + 127) / 128, 128, 0, s>>>(seed, cl, step, n, prec, out);
+    return cudaGetLastError();
+}
+
+template <class K> static cudaError_t allow_smem(K k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+}
+template <int PREC, int IPT, int SP, int CUT> static cudaError_t cfg_one() {
+    cudaError_t e = allow_smem(k_density<PREC, IPT, SP, CUT>);
+    if (e == cudaSuccess) e = allow_smem(k_force<PREC, IPT, SP, CUT, 0>);
+    if (e == cudaSuccess) e = allow_smem(k_force<PREC, IPT, SP, CUT, 1>);
+    return e;
+}
+template <int PREC, int IPT> static cudaError_t cfg_ipt() {
+    cudaError_t e = cfg_one<PREC, IPT, 1, 0>();
+    if (e == cudaSuccess) e = cfg_one<PREC, IPT, 1, 1>();
+    if (e == cudaSuccess) e = cfg_one<PREC, IPT, 0, 0>();
+    if (e == cudaSuccess) e = cfg_one<PREC, IPT, 0, 1>();
+    return e;
+}
+cudaError_t configure_kernels() {
+    cudaError_t e = cfg_ipt<1, 1>();
+    if (e == cudaSuccess) e = cfg_ipt<1, 2>();
+    if (e == cudaSuccess) e = cfg_ipt<0, 1>();
+    if (e == cudaSuccess) e = cfg_ipt<0, 2>();
+    return e;
+}
+
+}  // namespace scmd
