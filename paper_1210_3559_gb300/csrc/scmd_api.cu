@@ -60,7 +60,9 @@ struct md_ctx {
     // device buffers
     int32_t *d_poff = nullptr, *d_nreal = nullptr, *d_clg = nullptr, *d_status = nullptr;
     double *d_x = nullptr, *d_v = nullptr, *d_mass = nullptr, *d_rho = nullptr, *d_origin = nullptr;
-    double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr;
+    double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr, *d_qs = nullptr;
+    float* d_qi = nullptr;
+    std::vector<int> qexp;  // fixed-point exponent per cluster (MIXED mirror grid 2^-q)
     void *d_f = nullptr, *d_mirror = nullptr, *d_posg = nullptr;
     int64_t* d_step = nullptr;
     Run* d_run = nullptr;
@@ -130,6 +132,8 @@ void fill_dev(md_ctx* c) {
     d.posg = c->d_posg;
     d.rho = c->d_rho;
     d.origin = c->d_origin;
+    d.qscale = c->d_qs;
+    d.qinv = c->d_qi;
     d.part = c->d_part;
     d.ke_grp = c->d_ke;
     d.hist = c->d_hist;
@@ -289,7 +293,7 @@ void free_all(md_ctx* c) {
     drop_graphs(c);
     void* ptrs[] = {c->d_poff, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
-                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1]};
+                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_qs, c->d_qi};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -529,6 +533,28 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_mass, sizeof(double) * np));
     CKC(cudaMalloc(&c->d_rho, sizeof(double) * np));
     CKC(cudaMalloc(&c->d_origin, sizeof(double) * 3 * n_clusters));
+    CKC(cudaMalloc(&c->d_qs, sizeof(double) * n_clusters));
+    CKC(cudaMalloc(&c->d_qi, sizeof(float) * n_clusters));
+    {
+        // Fixed-point grid of the MIXED mirror: |x - origin| < W = 2^(24 - q) keeps every
+        // coordinate exact. W is chosen from the cluster size alone (so that a context
+        // rebuilt from a checkpoint picks the same grid): the radius of a compact FCC
+        // cluster of N atoms with lattice constant a, plus 5 % and 4 A of margin.
+        std::vector<double> qs(n_clusters);
+        std::vector<float> qi(n_clusters);
+        c->qexp.resize(n_clusters);
+        for (int b = 0; b < n_clusters; ++b) {
+            const double R = std::cbrt(3.0 * sizes[b] * prm->a_A * prm->a_A * prm->a_A / (16.0 * M_PI));
+            const double W = 1.05 * R + 4.0;
+            int q = 24 - (int)std::ceil(std::log2(W));
+            q = std::max(0, std::min(q, 20));
+            c->qexp[b] = q;
+            qs[b] = std::ldexp(1.0, q);
+            qi[b] = std::ldexp(1.0f, -q);
+        }
+        CKC(cudaMemcpy(c->d_qs, qs.data(), sizeof(double) * n_clusters, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_qi, qi.data(), sizeof(float) * n_clusters, cudaMemcpyHostToDevice));
+    }
     CKC(cudaMalloc(&c->d_part, sizeof(double) * kObsFields * c->ngroups));
     CKC(cudaMalloc(&c->d_ke, sizeof(double) * c->ngroups));
     CKC(cudaMalloc(&c->d_hist, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
@@ -541,7 +567,7 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
         CKC(cudaMemcpy(c->items_d[k], c->items_h[k].data(), sizeof(Item) * c->items_h[k].size(), cudaMemcpyHostToDevice));
     }
-    c->h_stage_n = std::max<size_t>(4 * np, 16);
+    c->h_stage_n = std::max<size_t>(6 * np, 16);
     CKC(cudaMallocHost(&c->h_stage, sizeof(double) * c->h_stage_n));
     CKC(cudaMallocHost(&c->h_run, sizeof(Run)));
     CKC(cudaMallocHost(&c->h_step, sizeof(int64_t)));
@@ -602,6 +628,7 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     c->h_run->obs_every = c->cfg.obs_every;
     CKC(cudaMemcpyAsync(c->d_run, c->h_run, sizeof(Run), cudaMemcpyHostToDevice, c->stream));
     st = reset_origin_and_forces(c);
+    if (st == MD_OK) st = check_status(c);
     if (st != MD_OK) return bail(st);
     if (cfg->tune == 1) {
         st = md_autotune(c, 10);

@@ -7,9 +7,12 @@
 //   * FP64 state (positions x, velocities v) in structure-of-arrays form
 //     x[3][Npad], v[3][Npad]; masses m[Npad];
 //   * forces F[3][Npad] in the pass precision (float for MIXED, double for FP64);
-//   * "mirror": the positions the density pass reads, relative to a per-cluster
-//     origin (the cluster's centre of mass at the start of a graph chunk), as
-//     float4(x, y, z, 0) or, in FP64 mode, double4;
+//   * "mirror": the positions the density pass reads. MIXED: a fixed-point
+//     image of x on the grid 2^-q (q per cluster, from its size), relative to an
+//     integer origin near the cluster's centre of mass, stored exactly as
+//     float4(x, y, z, 0); pair differences of two such values are exact and do
+//     not depend on the origin, so forces are a pure function of x (bitwise
+//     checkpoint/resume). FP64: the absolute positions as double4;
 //   * "posg": what the force pass reads, (x, y, z, B6 * rho^-1/2) per atom,
 //     written by the density pass;
 //   * rho[Npad] (FP64) and per-32-atom-group observable partials.
@@ -92,7 +95,9 @@ struct Dev {
     void* mirror;        // float4 / double4 [npad]
     void* posg;          // float4 / double4 [npad]
     double* rho;         // [npad]
-    double* origin;      // [B][3]
+    double* origin;      // [B][3] MIXED: integer origin on the 2^-q grid; FP64: unused
+    const double* qscale;// [B] 2^q
+    const float* qinv;   // [B] 2^-q
     double* part;        // [ngroups][kObsFields]
     double* ke_grp;      // [ngroups] sum m v^2 (Berendsen)
     double* hist;        // ring [cap][B][kHistFields]

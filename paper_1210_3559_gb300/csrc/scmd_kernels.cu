@@ -20,7 +20,8 @@
 //     the CTAs of the cluster through distributed shared memory, in a fixed
 //     order (results are run-to-run deterministic); the cluster's rank-0 CTA
 //     owns the epilogue.
-// Precision (MIXED): pair terms in FP32 on COM-relative FP32 coordinates; each
+// Precision (MIXED): pair terms in FP32 on fixed-point FP32 coordinates (see
+// store_mirror: exact pair differences, independent of the origin); each
 // 32-pair tile is summed in FP32, tiles are summed in FP32 spans of 4 tiles,
 // spans are folded into FP64 (density, energy) or into FP32 running sums
 // (forces); reductions over warps/CTAs are FP64 (density, energy) or FP32
@@ -144,13 +145,23 @@ __device__ __forceinline__ double ramp_T(const Run& r, int64_t step) {
     return r.T0 + (r.T1 - r.T0) * k / (double)r.nsteps;
 }
 
+// MIXED: k = rint(x 2^q) - o (an integer in FP64, exact), stored as (float)k * 2^-q,
+// exact while |k| < 2^24. FP64: the position itself.
 template <int PREC> __device__ __forceinline__ void store_mirror(const Dev& d, int i, int cl, double x, double y, double z) {
     using V4 = typename Tr<PREC>::V4;
-    const double* o = d.origin + 3 * cl;
     V4 p;
-    p.x = (typename Tr<PREC>::R)(x - o[0]);
-    p.y = (typename Tr<PREC>::R)(y - o[1]);
-    p.z = (typename Tr<PREC>::R)(z - o[2]);
+    if (PREC == 1) {
+        const double* o = d.origin + 3 * cl;
+        const double qs = d.qscale[cl];
+        const float qi = d.qinv[cl];
+        p.x = (float)(rint(x * qs) - o[0]) * qi;
+        p.y = (float)(rint(y * qs) - o[1]) * qi;
+        p.z = (float)(rint(z * qs) - o[2]) * qi;
+    } else {
+        p.x = x;
+        p.y = y;
+        p.z = z;
+    }
     p.w = 0;
     reinterpret_cast<V4*>(d.mirror)[i] = p;
 }
@@ -642,7 +653,7 @@ template <int PREC> __global__ void k_mirror(const Dev d) {
     store_mirror<PREC>(d, i, cl, d.x[i], d.x[d.npad + i], d.x[2 * d.npad + i]);
 }
 
-// Origin of each cluster = its centre of mass (one CTA of 32 threads per cluster).
+// Mirror origin of each cluster from its centre of mass (one CTA of 32 threads per cluster).
 __global__ void k_origin(const Dev d) {
     const int cl = blockIdx.x, lane = threadIdx.x;
     const int b = d.poff[cl], n = d.nreal[cl], np = d.npad;
@@ -659,9 +670,11 @@ __global__ void k_origin(const Dev d) {
     sz = warp_sum(sz);
     sm = warp_sum(sm);
     if (lane == 0) {
-        d.origin[3 * cl] = sm > 0.0 ? sx / sm : 0.0;
-        d.origin[3 * cl + 1] = sm > 0.0 ? sy / sm : 0.0;
-        d.origin[3 * cl + 2] = sm > 0.0 ? sz / sm : 0.0;
+        // integer origin on the 2^-q grid nearest the centre of mass (MIXED); 0 for FP64
+        const double qs = d.prec == 1 ? d.qscale[cl] : 0.0;
+        d.origin[3 * cl] = sm > 0.0 ? rint(sx / sm * qs) : 0.0;
+        d.origin[3 * cl + 1] = sm > 0.0 ? rint(sy / sm * qs) : 0.0;
+        d.origin[3 * cl + 2] = sm > 0.0 ? rint(sz / sm * qs) : 0.0;
     }
 }
 

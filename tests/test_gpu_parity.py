@@ -263,15 +263,22 @@ def test_observables_and_history(scmd):
 
 
 def test_nonfinite_detected_without_trap(scmd):
-    # two atoms 0.05 A apart with a large step: forces overflow; the library reports it, the GPU survives
-    pos = np.array([[0, 0, 0], [0.05, 0, 0], [2.5, 0, 0]], float)
-    ctx = make(scmd, [3], pos, prec=MIXED)
+    """A run that blows up is reported as MD_ERR_NONFINITE; the GPU and the context stay usable."""
+    pos = inputs.fcc_sphere(13)
+    ctx = make(scmd, [13], pos, prec=MIXED)
+    # an absurd bath temperature gives velocities ~1e148 A/fs: FP32 coordinates overflow
+    th = scmd.thermostat(scmd.MD_LANGEVIN, 1e300, 1e300, gamma_per_ps=10.0, seed=1)
     with pytest.raises(scmd.ScmdError) as e:
-        scmd.md_step(ctx, 20, 50.0)
+        scmd.md_step(ctx, 3, 1.0, th)
     assert e.value.status == scmd.MD_ERR_NONFINITE
-    # the context and the GPU still work: restore a sane state and continue
-    good = inputs.fcc_sphere(3)
-    scmd.md_set_state(ctx, good, np.zeros((3, 3)), 0)
+    # two atoms 1e-4 A apart: FP32 forces overflow at evaluation time
+    bad = pos.copy()
+    bad[1] = bad[0] + np.array([1e-4, 0, 0])
+    with pytest.raises(scmd.ScmdError) as e:
+        scmd.md_set_state(ctx, bad, np.zeros((13, 3)), 0)
+    assert e.value.status == scmd.MD_ERR_NONFINITE
+    # restore a sane state and continue on the same context
+    scmd.md_set_state(ctx, pos, np.zeros((13, 3)), 0)
     scmd.md_step(ctx, 5, 1.0)
     E, F = scmd.md_energy_forces(ctx)
     assert np.isfinite(E).all() and np.isfinite(F).all()
