@@ -536,18 +536,20 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_qs, sizeof(double) * n_clusters));
     CKC(cudaMalloc(&c->d_qi, sizeof(float) * n_clusters));
     {
-        // Fixed-point grid of the MIXED mirror: |x - origin| < W = 2^(24 - q) keeps every
-        // coordinate exact. W is chosen from the cluster size alone (so that a context
-        // rebuilt from a checkpoint picks the same grid): the radius of a compact FCC
-        // cluster of N atoms with lattice constant a, plus 5 % and 4 A of margin.
+        // Fixed-point grid of the MIXED mirror: coordinates are exact while
+        // |x - origin| < W = 2^(24 - q). W is chosen from the cluster size alone (so
+        // that a context rebuilt from a checkpoint picks the same grid): the radius
+        // of a compact FCC cluster of N atoms with lattice constant a, plus 2 % and
+        // 0.25 A, rounded up to a power of two. Atoms beyond W stay correct to FP32
+        // rounding of their offset from the origin.
         std::vector<double> qs(n_clusters);
         std::vector<float> qi(n_clusters);
         c->qexp.resize(n_clusters);
         for (int b = 0; b < n_clusters; ++b) {
             const double R = std::cbrt(3.0 * sizes[b] * prm->a_A * prm->a_A * prm->a_A / (16.0 * M_PI));
-            const double W = 1.05 * R + 4.0;
+            const double W = 1.02 * R + 0.25;
             int q = 24 - (int)std::ceil(std::log2(W));
-            q = std::max(0, std::min(q, 20));
+            q = std::max(8, std::min(q, 23));
             c->qexp[b] = q;
             qs[b] = std::ldexp(1.0, q);
             qi[b] = std::ldexp(1.0f, -q);
