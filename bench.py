@@ -1,0 +1,410 @@
+"""Benchmark: Sutton-Chen Ni cluster MD on one GB300 per rank (replicas), one JSON line.
+
+Default workload (Ni~2000 cooling run): fcc_sphere(2000) (a = 3.52 A), Maxwell-Boltzmann
+velocities at 2000 K (seed 2), melted with Langevin at 2000 K for 20 ps (1e4 steps of
+2 fs, gamma = 1/ps; untimed set-up), then the linear Langevin cooling 2000 -> 300 K over
+2e5 steps of 2 fs (gamma = 1/ps), MIXED precision (FP32 pair terms, FP64 rho, energy and
+integration). One timed iteration ("step" of this benchmark) is one md_step call of
+--md-steps MD steps (default 500) of that schedule, issued as CUDA-graph replays; the
+default --steps 400 covers the whole 2e5-step cooling schedule. L2 is flushed (a 256 MB
+write) before every timed iteration and that flush is outside the timed events.
+
+value  : atom-timesteps/s over all ranks (sum of atoms x MD steps / max rank time).
+e2e    : the same metric through the C ABI with host buffers every iteration
+         (md_set_state from pinned host arrays, md_step, md_get_state back to the host).
+roofline: the force pass (dominant kernel), FP32-pipe lane operations per launch
+         (16 per ordered pair) over its mean launch time, timed with CUDA events on the
+         library's stream right after the timed region, against 152 SMs x 128 FP32
+         lanes x the maximum SM clock.
+cpu_baseline: the FP64 oracle (plain C + OpenMP) on the host cores, on a bounded sample
+         of the same workload (rank 0 only).
+--impl reference: times that oracle alone as the reference arm.
+Multi-GPU (torchrun): independent replicas, one per rank ("replicas only": clusters are
+independent), no data-path collective; value sums the ranks' work.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "atom-timesteps/s & pair-evals/s vs FP32 peak; mixed vs FP64 at stated drift"
+UNIT = "atom-timesteps/s"
+FP32_LANES_PER_SM = 128
+FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n,m) = (9,6)
+DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
+
+
+# ------------------------------------------------------------------ workloads
+def workload(name: str, rank: int):
+    from paper_1210_3559_gb300 import inputs
+    seed_off = 1000 * rank  # independent replica per rank
+    if name == "ni2000":
+        pos = inputs.fcc_sphere(2000)
+        m = inputs.masses(2000)
+        vel = inputs.maxwell_boltzmann(pos, m, 2000.0, seed=2 + seed_off, dof="3N")
+        return dict(sizes=[2000], pos=pos, vel=vel, mass=m, prec="mixed", dt=2.0, melt_steps=10000,
+                    melt_T=2000.0, schedule=(2000.0, 300.0, 200000), gamma=1.0, seed=2 + seed_off,
+                    desc="Ni~2000 FCC sphere, melt 2000 K, Langevin cooling 2000->300 K over 2e5 steps dt=2 fs")
+    if name in ("ni6000", "ni20000"):
+        n = int(name[2:])
+        pos = inputs.fcc_sphere(n)
+        m = inputs.masses(n)
+        vel = inputs.maxwell_boltzmann(pos, m, 2000.0, seed=(3 if n == 6000 else 4) + seed_off, dof="3N")
+        return dict(sizes=[n], pos=pos, vel=vel, mass=m, prec="mixed", dt=2.0, melt_steps=2000, melt_T=2000.0,
+                    schedule=(2000.0, 300.0, 200000), gamma=1.0, seed=3 + seed_off,
+                    desc=f"Ni~{n} FCC sphere, Langevin cooling 2000->300 K over 2e5 steps dt=2 fs")
+    if name == "ni147":
+        pos = inputs.mackay_icosahedron(3, 2.49)
+        m = inputs.masses(147)
+        vel = inputs.maxwell_boltzmann(pos, m, 1500.0, seed=1 + seed_off)
+        return dict(sizes=[147], pos=pos, vel=vel, mass=m, prec="fp64", dt=1.0, melt_steps=0, melt_T=0.0,
+                    schedule=None, gamma=0.0, seed=1 + seed_off,
+                    desc="Ni147 Mackay icosahedron, 1500 K, NVE dt=1 fs, FP64")
+    if name == "batched512":
+        sizes = inputs.batched_sizes(512, 55, 2000, seed=5 + seed_off)
+        parts, vels = [], []
+        for b, n in enumerate(sizes):
+            p = inputs.fcc_sphere(int(n))
+            parts.append(p)
+            vels.append(inputs.maxwell_boltzmann(p, inputs.masses(int(n)), 2000.0, seed=1000 + b + seed_off, dof="3N"))
+        pos = np.concatenate(parts)
+        return dict(sizes=sizes, pos=pos, vel=np.concatenate(vels), mass=inputs.masses(len(pos)), prec="mixed",
+                    dt=2.0, melt_steps=10000, melt_T=2000.0, schedule=(900.0, 900.0, 250000), gamma=1.0,
+                    seed=5 + seed_off,
+                    desc="512 clusters N~U{55..2000}, melt 2000 K, Langevin quench at 900 K dt=2 fs")
+    raise SystemExit(f"unknown config {name}")
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.out.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]) if f[3] not in ("[N/A]", "") else 0.0,
+                                 hw=f[5], hwt=f[6], swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 0.25 * max(x["power"] for x in rows)] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "samples": len(load), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ oracle baseline
+def cpu_baseline(w, budget_s: float):
+    """Time the FP64 oracle on a bounded sample of the workload (same thermostat and dt)."""
+    import oracle
+    cores = oracle.num_threads(os.cpu_count() or 1)
+    sizes = list(map(int, w["sizes"]))
+    if len(sizes) > 8:  # batched: a fixed subset of clusters, scaled by atoms
+        sizes = sizes[:8]
+    n = sum(sizes)
+    pos, vel, mass = w["pos"][:n], w["vel"][:n], w["mass"][:n]
+    b = oracle.Batch(sizes, pos, vel, mass)
+    th = oracle.thermostat(oracle.LANGEVIN if w["gamma"] > 0 else oracle.NVE,
+                           w["melt_T"] or 0.0, None, gamma_ps=w["gamma"] or 1.0, seed=w["seed"])
+    t0 = time.perf_counter()
+    b.run(1, w["dt"], th)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(2000, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    b.run(steps, w["dt"], th)
+    el = time.perf_counter() - t0
+    return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} MD steps (FP64, all pairs) of {len(sizes)} cluster(s), {n} atoms, "
+                      f"dt={w['dt']} fs, same thermostat", "s_per_step": el / steps}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args.config, 0)
+    import oracle
+    cores = oracle.num_threads(os.cpu_count() or 1)
+    sizes = list(map(int, w["sizes"]))[:8]
+    n = sum(sizes)
+    b = oracle.Batch(sizes, w["pos"][:n], w["vel"][:n], w["mass"][:n])
+    th = oracle.thermostat(oracle.LANGEVIN if w["gamma"] > 0 else oracle.NVE, w["melt_T"] or 0.0, None,
+                           gamma_ps=w["gamma"] or 1.0, seed=w["seed"])
+    for _ in range(args.warmup):
+        b.run(1, w["dt"], th)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run(1, w["dt"], th)
+    el = time.perf_counter() - t0
+    val = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["desc"], "sample_atoms": n, "md_steps_per_step": 1},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step = 1 MD step of {n} atoms (FP64 oracle, all pairs)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="ni2000", choices=["ni2000", "ni6000", "ni20000", "ni147", "batched512"])
+    ap.add_argument("--md-steps", type=int, default=500, help="MD steps per timed iteration")
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--melt-steps", type=int, default=None, help="override the untimed melt length")
+    ap.add_argument("--shapes", default=None, help="ipt,warps,cluster for the density and force passes (6 ints); skips tuning")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    torch.cuda.set_device(local)
+    from paper_1210_3559_gb300 import build as _build, scmd
+    _build.build()
+    w = workload(args.config, rank)
+    if args.melt_steps is not None:
+        w["melt_steps"] = args.melt_steps
+    prec = args.precision or w["prec"]
+    P = scmd.MD_PREC_MIXED if prec == "mixed" else scmd.MD_PREC_FP64
+    stream = torch.cuda.Stream()
+    cfg = scmd.config(precision=P, graph_chunk=min(args.md_steps, 512), tune=0 if args.no_tune else 1,
+                      stream=stream.cuda_stream)
+    sizes = np.asarray(w["sizes"], dtype=np.int32)
+    natoms = int(sizes.sum())
+    pairs_per_eval = float(np.sum(sizes.astype(np.float64) * (sizes - 1)))
+    if args.shapes:
+        cfg.tune = 0
+    ctx = scmd.md_create(cfg, sizes, w["pos"], w["vel"], w["mass"], scmd.sc_params())
+    if args.shapes:
+        v = [int(x) for x in args.shapes.split(",")]
+        scmd.md_set_launch(ctx, 0, *v[0:3])
+        scmd.md_set_launch(ctx, 1, *v[3:6])
+    dt = w["dt"]
+    # set-up: melt (untimed)
+    if w["melt_steps"]:
+        scmd.md_step(ctx, w["melt_steps"], dt, scmd.thermostat(scmd.MD_LANGEVIN, w["melt_T"], w["melt_T"],
+                                                               gamma_per_ps=w["gamma"], seed=w["seed"]))
+    M = args.md_steps
+
+    def therm(k):
+        if w["schedule"] is None:
+            return None
+        T0, T1, n = w["schedule"]
+        a, b = k * M, (k + 1) * M
+        return scmd.thermostat(scmd.MD_LANGEVIN, T0 + (T1 - T0) * min(a, n) / n, T0 + (T1 - T0) * min(b, n) / n,
+                               gamma_per_ps=w["gamma"], seed=w["seed"] + 17)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # warm-up iterations (not timed) advance the schedule like the timed ones
+    k_iter = 0
+    for _ in range(args.warmup):
+        scmd.md_step(ctx, M, dt, therm(k_iter))
+        k_iter += 1
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+        scmd.md_step(ctx, M, dt, therm(k_iter))
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+        k_iter += 1
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3  # seconds of timed device work
+    t_max = t_dev
+    if dist:
+        t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    md_steps_total = args.steps * M
+    value = natoms * md_steps_total * world / t_max
+    pair_rate = pairs_per_eval * md_steps_total * world / t_max
+
+    # pass timings with CUDA events on the library's stream (same state, same launch shapes)
+    ms_d, ms_f, pairs = scmd.md_time_passes(ctx, 50)
+    peak_clock = (clocks or {}).get("sm_max_mhz", 2070.0)
+    peak_ops = 152 * FP32_LANES_PER_SM * peak_clock * 1e6
+    achieved = FORCE_OPS_PER_PAIR * pairs / (ms_f * 1e-3)
+    shapes = {"density": scmd.md_get_launch(ctx, 0), "force": scmd.md_get_launch(ctx, 1)}
+    per_step, per_chunk = scmd.md_launch_counts(ctx)
+    chunk = min(M, 512)
+    launches = args.steps * (M * per_step + math.ceil(M / chunk) * per_chunk)
+
+    # force error of the final state against the FP64 oracle (rank 0, first cluster)
+    force_err = None
+    pos_f, vel_f, step_f = scmd.md_get_state(ctx)
+    if rank == 0:
+        import oracle
+        E, F = scmd.md_energy_forces(ctx)
+        n0 = int(sizes[0])
+        _, Fr, _, _ = oracle.energy_forces(pos_f[:n0])
+        force_err = float(np.linalg.norm(F[:n0] - Fr) / np.linalg.norm(Fr))
+
+    # e2e through the C ABI with host buffers: set_state (H2D) + md_step + get_state (D2H)
+    pos_h = torch.from_numpy(pos_f.copy()).pin_memory().numpy()
+    vel_h = torch.from_numpy(vel_f.copy()).pin_memory().numpy()
+    e2e_iters = max(3, min(args.steps, 20))
+    scmd.md_set_state(ctx, pos_h, vel_h, step_f)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s_now = step_f
+    for k in range(e2e_iters):
+        scmd.md_set_state(ctx, pos_h, vel_h, s_now)
+        scmd.md_step(ctx, M, dt, therm(k_iter + k))
+        p2, v2, s_now = scmd.md_get_state(ctx)
+        pos_h[:] = p2
+        vel_h[:] = v2
+    e2e_t = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = natoms * M * e2e_iters * world / e2e_t
+
+    # FP64-on-GPU form of the same workload, short sample (mixed vs FP64)
+    fp64 = None
+    if not args.skip_fp64 and prec == "mixed":
+        cfg64 = scmd.config(precision=scmd.MD_PREC_FP64, graph_chunk=min(M, 512), tune=0 if args.no_tune else 1,
+                            stream=stream.cuda_stream)
+        c64 = scmd.md_create(cfg64, sizes, pos_f, vel_f, w["mass"], scmd.sc_params())
+        m64 = max(10, M // 10)
+        scmd.md_step(c64, m64, dt, therm(0))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+        reps64 = 3
+        for _ in range(reps64):
+            scmd.md_step(c64, m64, dt, therm(0))
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": natoms * m64 * reps64 / t64, "unit": UNIT,
+                "pair_evals_per_s": pairs_per_eval * m64 * reps64 / t64,
+                "sample": f"{reps64} x {m64} MD steps, same state and thermostat, per GPU"}
+        scmd.md_destroy(c64)
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cpu = cpu_baseline(w, args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "atoms_per_gpu": natoms, "clusters_per_gpu": int(len(sizes)),
+                       "md_steps_per_step": M, "dt_fs": dt, "precision": prec,
+                       "l2": "flushed (256 MB write) before every timed iteration, outside the timed events",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "launch_shapes": {k: list(v) for k, v in shapes.items()},
+                       "wall_s_timed_region": t_wall},
+            "pair_evals_per_s": pair_rate,
+            "fp32_pipe_frac_force_pass": achieved / peak_ops,
+            "force_err_vs_oracle": force_err,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops, "traffic": None,
+                         "kernel": "k_force (force pass)", "ms_per_launch": ms_f,
+                         "density_pass_ms_per_launch": ms_d, "pairs_per_launch": pairs,
+                         "peak_basis": f"152 SMs x 128 FP32 lanes x {peak_clock:.0f} MHz (max SM clock)"},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * natoms * 3 * 8), "d2h_bytes_per_step": int(2 * natoms * 3 * 8),
+                    "iterations": e2e_iters},
+            "gpu_launches": int(launches),
+            "fp64_gpu": fp64,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    scmd.md_destroy(ctx)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

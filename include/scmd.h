@@ -184,6 +184,15 @@ md_status md_clear_history(md_ctx* ctx);
 md_status md_get_state(md_ctx* ctx, double* pos_A, double* vel_A_per_fs, int64_t* step);
 md_status md_set_state(md_ctx* ctx, const double* pos_A, const double* vel_A_per_fs, int64_t step);
 
+/* MIXED precision keeps pair coordinates in FP32 relative to one origin per
+ * cluster, set to the cluster's centre of mass when the context is created and
+ * kept fixed afterwards (so that forces depend on the positions alone and a
+ * checkpoint restored into this context, or into one created from the same
+ * initial positions, resumes bit for bit). md_recenter moves every origin to
+ * the current centre of mass (useful after md_set_state with a configuration
+ * far from the original one) and recomputes the forces. */
+md_status md_recenter(md_ctx* ctx);
+
 /* Forces of the current state as held by the context (host [Ntot][3]). */
 md_status md_get_forces(md_ctx* ctx, double* forces_eV_per_A);
 

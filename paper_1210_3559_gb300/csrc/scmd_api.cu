@@ -4,9 +4,9 @@
 // per MD step, the density pass and the force pass (whose epilogue integrates),
 // plus a Berendsen kernel when that thermostat is selected and an observables
 // reduction when a sample is due. md_step replays CUDA graphs that each hold
-// one chunk of steps (origin refresh, step start, 2-3 kernels per step, step
-// counter advance); graphs are cached by chunk length, the observation phase
-// of the chunk's first step, the thermostat kind and the launch shapes.
+// one chunk of steps (step start, 2-3 kernels per step, step counter advance);
+// graphs are cached by chunk length, the observation phase of the chunk's
+// first step, the thermostat kind and the launch shapes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,9 +60,8 @@ struct md_ctx {
     // device buffers
     int32_t *d_poff = nullptr, *d_nreal = nullptr, *d_clg = nullptr, *d_status = nullptr;
     double *d_x = nullptr, *d_v = nullptr, *d_mass = nullptr, *d_rho = nullptr, *d_origin = nullptr;
-    double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr, *d_qs = nullptr;
-    float* d_qi = nullptr;
-    std::vector<int> qexp;  // fixed-point exponent per cluster (MIXED mirror grid 2^-q)
+    double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr, *d_hs = nullptr;
+    float* d_sig0 = nullptr;
     void *d_f = nullptr, *d_mirror = nullptr, *d_posg = nullptr;
     int64_t* d_step = nullptr;
     Run* d_run = nullptr;
@@ -132,8 +131,8 @@ void fill_dev(md_ctx* c) {
     d.posg = c->d_posg;
     d.rho = c->d_rho;
     d.origin = c->d_origin;
-    d.qscale = c->d_qs;
-    d.qinv = c->d_qi;
+    d.hs = c->d_hs;
+    d.sig0 = c->d_sig0;
     d.part = c->d_part;
     d.ke_grp = c->d_ke;
     d.hist = c->d_hist;
@@ -215,8 +214,8 @@ md_status evaluate(md_ctx* c, bool observe) {
     return MD_OK;
 }
 
-md_status reset_origin_and_forces(md_ctx* c) {
-    CK(c, launch_origin(c->dev, c->stream));
+md_status recompute_forces(md_ctx* c, bool new_origin) {
+    if (new_origin) CK(c, launch_origin(c->dev, c->stream));
     md_status st = evaluate(c, false);
     if (st != MD_OK) return st;
     CK(c, cudaStreamSynchronize(c->stream));
@@ -230,7 +229,6 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
     const Item* i0 = items_for(c, c->shape[0], &n0);
     const Item* i1 = items_for(c, c->shape[1], &n1);
     const int oe = c->cfg.obs_every;
-    CK(c, launch_origin(d, c->stream));
     CK(c, launch_start(d, 0, c->stream));
     for (int k = 0; k < M; ++k) {
         const int64_t next = s0 + k + 1;
@@ -293,7 +291,7 @@ void free_all(md_ctx* c) {
     drop_graphs(c);
     void* ptrs[] = {c->d_poff, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
-                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_qs, c->d_qi};
+                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -533,30 +531,8 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_mass, sizeof(double) * np));
     CKC(cudaMalloc(&c->d_rho, sizeof(double) * np));
     CKC(cudaMalloc(&c->d_origin, sizeof(double) * 3 * n_clusters));
-    CKC(cudaMalloc(&c->d_qs, sizeof(double) * n_clusters));
-    CKC(cudaMalloc(&c->d_qi, sizeof(float) * n_clusters));
-    {
-        // Fixed-point grid of the MIXED mirror: coordinates are exact while
-        // |x - origin| < W = 2^(24 - q). W is chosen from the cluster size alone (so
-        // that a context rebuilt from a checkpoint picks the same grid): the radius
-        // of a compact FCC cluster of N atoms with lattice constant a, plus 2 % and
-        // 0.25 A, rounded up to a power of two. Atoms beyond W stay correct to FP32
-        // rounding of their offset from the origin.
-        std::vector<double> qs(n_clusters);
-        std::vector<float> qi(n_clusters);
-        c->qexp.resize(n_clusters);
-        for (int b = 0; b < n_clusters; ++b) {
-            const double R = std::cbrt(3.0 * sizes[b] * prm->a_A * prm->a_A * prm->a_A / (16.0 * M_PI));
-            const double W = 1.02 * R + 0.25;
-            int q = 24 - (int)std::ceil(std::log2(W));
-            q = std::max(8, std::min(q, 23));
-            c->qexp[b] = q;
-            qs[b] = std::ldexp(1.0, q);
-            qi[b] = std::ldexp(1.0f, -q);
-        }
-        CKC(cudaMemcpy(c->d_qs, qs.data(), sizeof(double) * n_clusters, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_qi, qi.data(), sizeof(float) * n_clusters, cudaMemcpyHostToDevice));
-    }
+    CKC(cudaMalloc(&c->d_hs, sizeof(double) * np));
+    CKC(cudaMalloc(&c->d_sig0, sizeof(float) * np));
     CKC(cudaMalloc(&c->d_part, sizeof(double) * kObsFields * c->ngroups));
     CKC(cudaMalloc(&c->d_ke, sizeof(double) * c->ngroups));
     CKC(cudaMalloc(&c->d_hist, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
@@ -629,7 +605,7 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     c->h_run->hist_cap = c->hist_cap;
     c->h_run->obs_every = c->cfg.obs_every;
     CKC(cudaMemcpyAsync(c->d_run, c->h_run, sizeof(Run), cudaMemcpyHostToDevice, c->stream));
-    st = reset_origin_and_forces(c);
+    st = recompute_forces(c, true);
     if (st == MD_OK) st = check_status(c);
     if (st != MD_OK) return bail(st);
     if (cfg->tune == 1) {
@@ -717,6 +693,7 @@ md_status md_step(md_ctx* c, int64_t nsteps, double dt, const md_thermostat* th)
     r.noise_k = t.kind == MD_LANGEVIN ? (1.0 - r.c1 * r.c1) * kKB * kConv : 0.0;
     r.T0 = t.T0_K;
     r.T1 = t.T1_K;
+    r.dT = (t.T1_K - t.T0_K) / (double)nsteps;
     r.dt_over_tau = t.kind == MD_BERENDSEN ? dt / (t.tau_ps * 1e3) : 0.0;
     r.kb = kKB;
     r.step0 = c->step;
@@ -726,6 +703,7 @@ md_status md_step(md_ctx* c, int64_t nsteps, double dt, const md_thermostat* th)
     r.obs_every = c->cfg.obs_every;
     r.hist_cap = c->hist_cap;
     CK(c, cudaMemcpyAsync(c->d_run, c->h_run, sizeof(Run), cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_prepare(c->dev, c->stream));
     md_status st = set_step_base(c, c->step);
     if (st != MD_OK) return st;
     const int chunk = c->cfg.graph_chunk;
@@ -815,7 +793,14 @@ md_status md_set_state(md_ctx* c, const double* pos, const double* vel, int64_t 
     if (st != MD_OK) return st;
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
     c->step = step;
-    st = reset_origin_and_forces(c);
+    st = recompute_forces(c, false);
+    if (st != MD_OK) return st;
+    return check_status(c);
+}
+
+md_status md_recenter(md_ctx* c) {
+    if (!c) return MD_ERR_INVALID;
+    md_status st = recompute_forces(c, true);
     if (st != MD_OK) return st;
     return check_status(c);
 }
@@ -945,7 +930,7 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
     if (per_step) *per_step = 2;
-    if (per_chunk) *per_chunk = 3;
+    if (per_chunk) *per_chunk = 2;
     return MD_OK;
 }
 

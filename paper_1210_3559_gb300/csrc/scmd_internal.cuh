@@ -7,12 +7,11 @@
 //   * FP64 state (positions x, velocities v) in structure-of-arrays form
 //     x[3][Npad], v[3][Npad]; masses m[Npad];
 //   * forces F[3][Npad] in the pass precision (float for MIXED, double for FP64);
-//   * "mirror": the positions the density pass reads. MIXED: a fixed-point
-//     image of x on the grid 2^-q (q per cluster, from its size), relative to an
-//     integer origin near the cluster's centre of mass, stored exactly as
-//     float4(x, y, z, 0); pair differences of two such values are exact and do
-//     not depend on the origin, so forces are a pure function of x (bitwise
-//     checkpoint/resume). FP64: the absolute positions as double4;
+//   * "mirror": the positions the density pass reads. MIXED: float4(x - o, 0)
+//     with o a per-cluster origin fixed when the context is created (the centre
+//     of mass of the initial positions; md_recenter moves it), so forces are a
+//     pure function of x for the life of the context (bitwise checkpoint/resume).
+//     FP64: the absolute positions as double4;
 //   * "posg": what the force pass reads, (x, y, z, B6 * rho^-1/2) per atom,
 //     written by the density pass;
 //   * rho[Npad] (FP64) and per-32-atom-group observable partials.
@@ -68,6 +67,7 @@ struct Run {
     double c1;               // Langevin exp(-gamma dt)
     double noise_k;          // (1 - c1^2) k_B * conv  (sigma_i^2 = noise_k * T / m_i)
     double T0, T1;           // ramp end points
+    double dT;               // (T1 - T0) / nsteps
     double dt_over_tau;      // Berendsen
     double kb;               // k_B
     int64_t step0;           // global step at the start of the call
@@ -95,9 +95,9 @@ struct Dev {
     void* mirror;        // float4 / double4 [npad]
     void* posg;          // float4 / double4 [npad]
     double* rho;         // [npad]
-    double* origin;      // [B][3] MIXED: integer origin on the 2^-q grid; FP64: unused
-    const double* qscale;// [B] 2^q
-    const float* qinv;   // [B] 2^-q
+    double* origin;      // [B][3] MIXED mirror origin; FP64: unused
+    const double* hs;    // [npad] half-step kick factor h * conv / m (per md_step call)
+    const float* sig0;   // [npad] sqrt((1 - c1^2) k_B conv / m) (Langevin, per md_step call)
     double* part;        // [ngroups][kObsFields]
     double* ke_grp;      // [ngroups] sum m v^2 (Berendsen)
     double* hist;        // ring [cap][B][kHistFields]
@@ -116,6 +116,7 @@ struct Shape { int ipt, warps, cluster; };
 // Kernels are launched through these wrappers (defined in scmd_kernels.cu).
 cudaError_t launch_mirror(const Dev& d, cudaStream_t s);
 cudaError_t launch_origin(const Dev& d, cudaStream_t s);
+cudaError_t launch_prepare(const Dev& d, cudaStream_t s);
 cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s);
 // mode: 0 = forces only (store F), 1 = forces + all observable partials (no integration),
 //       2 = MD step: finish the half kick, record observables if due, start the next step unless last.

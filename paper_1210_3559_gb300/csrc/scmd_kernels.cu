@@ -20,8 +20,8 @@
 //     the CTAs of the cluster through distributed shared memory, in a fixed
 //     order (results are run-to-run deterministic); the cluster's rank-0 CTA
 //     owns the epilogue.
-// Precision (MIXED): pair terms in FP32 on fixed-point FP32 coordinates (see
-// store_mirror: exact pair differences, independent of the origin); each
+// Precision (MIXED): pair terms in FP32 on FP32 coordinates relative to a fixed
+// per-cluster origin near the centre of mass; each
 // 32-pair tile is summed in FP32, tiles are summed in FP32 spans of 4 tiles,
 // spans are folded into FP64 (density, energy) or into FP32 running sums
 // (forces); reductions over warps/CTAs are FP64 (density, energy) or FP32
@@ -141,22 +141,18 @@ __device__ __forceinline__ void normals_f64(uint64_t seed, uint32_t cl, int64_t 
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ double ramp_T(const Run& r, int64_t step) {
-    const double k = (double)(step - r.step0);
-    return r.T0 + (r.T1 - r.T0) * k / (double)r.nsteps;
+    return r.T0 + r.dT * (double)(step - r.step0);
 }
 
-// MIXED: k = rint(x 2^q) - o (an integer in FP64, exact), stored as (float)k * 2^-q,
-// exact while |k| < 2^24. FP64: the position itself.
+// MIXED: float(x - o) with the cluster's fixed origin o. FP64: the position itself.
 template <int PREC> __device__ __forceinline__ void store_mirror(const Dev& d, int i, int cl, double x, double y, double z) {
     using V4 = typename Tr<PREC>::V4;
     V4 p;
     if (PREC == 1) {
         const double* o = d.origin + 3 * cl;
-        const double qs = d.qscale[cl];
-        const float qi = d.qinv[cl];
-        p.x = (float)(rint(x * qs) - o[0]) * qi;
-        p.y = (float)(rint(y * qs) - o[1]) * qi;
-        p.z = (float)(rint(z * qs) - o[2]) * qi;
+        p.x = (float)(x - o[0]);
+        p.y = (float)(y - o[1]);
+        p.z = (float)(z - o[2]);
     } else {
         p.x = x;
         p.y = y;
@@ -175,40 +171,42 @@ template <int PREC> __device__ __forceinline__ void load_force(const Dev& d, int
 }
 
 // Start of a step for one atom from (x, v, F): B, then A O A (Langevin) or A A (NVE, Berendsen).
+// Per-atom factors h conv / m and the Langevin noise scale come precomputed (k_prepare), so the
+// FP64 work here is multiply-adds only.
 template <int PREC>
 __device__ __forceinline__ void begin_step(const Dev& d, const Run& r, int i, int cl, int atom, int64_t step,
                                            double fx, double fy, double fz) {
     const int np = d.npad;
-    const double hs = r.h * d.conv / d.mass[i];
-    double vx = d.v[i] + hs * fx, vy = d.v[np + i] + hs * fy, vz = d.v[2 * np + i] + hs * fz;
+    const double hs = d.hs[i];
+    double vx = fma(hs, fx, d.v[i]), vy = fma(hs, fy, d.v[np + i]), vz = fma(hs, fz, d.v[2 * np + i]);
     double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
     if (r.kind == 1) {
-        x += r.h * vx;
-        y += r.h * vy;
-        z += r.h * vz;
-        const double T = ramp_T(r, step);
-        const double sig = sqrt(fmax(r.noise_k * T / d.mass[i], 0.0));
+        x = fma(r.h, vx, x);
+        y = fma(r.h, vy, y);
+        z = fma(r.h, vz, z);
+        const double T = fmax(ramp_T(r, step), 0.0);
         if (PREC == 1) {
             float zz[3];
             normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
-            const float sf = (float)sig;
-            vx = r.c1 * vx + (double)(sf * zz[0]);
-            vy = r.c1 * vy + (double)(sf * zz[1]);
-            vz = r.c1 * vz + (double)(sf * zz[2]);
+            const float sf = d.sig0[i] * sqrtf((float)T);
+            vx = fma(r.c1, vx, (double)(sf * zz[0]));
+            vy = fma(r.c1, vy, (double)(sf * zz[1]));
+            vz = fma(r.c1, vz, (double)(sf * zz[2]));
         } else {
             double zz[3];
             normals_f64(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
-            vx = r.c1 * vx + sig * zz[0];
-            vy = r.c1 * vy + sig * zz[1];
-            vz = r.c1 * vz + sig * zz[2];
+            const double sig = sqrt(r.noise_k * T / d.mass[i]);
+            vx = fma(r.c1, vx, sig * zz[0]);
+            vy = fma(r.c1, vy, sig * zz[1]);
+            vz = fma(r.c1, vz, sig * zz[2]);
         }
-        x += r.h * vx;
-        y += r.h * vy;
-        z += r.h * vz;
+        x = fma(r.h, vx, x);
+        y = fma(r.h, vy, y);
+        z = fma(r.h, vz, z);
     } else {
-        x += r.dt * vx;
-        y += r.dt * vy;
-        z += r.dt * vz;
+        x = fma(r.dt, vx, x);
+        y = fma(r.dt, vy, y);
+        z = fma(r.dt, vz, z);
     }
     d.v[i] = vx;
     d.v[np + i] = vy;
@@ -567,10 +565,10 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
             const int64_t step = *d.step_base + k_local;  // this pass completes step -> step + 1
             double vx = 0.0, vy = 0.0, vz = 0.0;
             if (real) {
-                const double hs = r.h * d.conv / m;
-                vx = d.v[i] + hs * (double)Fx;
-                vy = d.v[np + i] + hs * (double)Fy;
-                vz = d.v[2 * np + i] + hs * (double)Fz;
+                const double hs = d.hs[i];
+                vx = fma(hs, (double)Fx, d.v[i]);
+                vy = fma(hs, (double)Fy, d.v[np + i]);
+                vz = fma(hs, (double)Fz, d.v[2 * np + i]);
                 d.v[i] = vx;
                 d.v[np + i] = vy;
                 d.v[2 * np + i] = vz;
@@ -653,7 +651,7 @@ template <int PREC> __global__ void k_mirror(const Dev d) {
     store_mirror<PREC>(d, i, cl, d.x[i], d.x[d.npad + i], d.x[2 * d.npad + i]);
 }
 
-// Mirror origin of each cluster from its centre of mass (one CTA of 32 threads per cluster).
+// Mirror origin of each cluster = its centre of mass (one CTA of 32 threads per cluster).
 __global__ void k_origin(const Dev d) {
     const int cl = blockIdx.x, lane = threadIdx.x;
     const int b = d.poff[cl], n = d.nreal[cl], np = d.npad;
@@ -670,11 +668,9 @@ __global__ void k_origin(const Dev d) {
     sz = warp_sum(sz);
     sm = warp_sum(sm);
     if (lane == 0) {
-        // integer origin on the 2^-q grid nearest the centre of mass (MIXED); 0 for FP64
-        const double qs = d.prec == 1 ? d.qscale[cl] : 0.0;
-        d.origin[3 * cl] = sm > 0.0 ? rint(sx / sm * qs) : 0.0;
-        d.origin[3 * cl + 1] = sm > 0.0 ? rint(sy / sm * qs) : 0.0;
-        d.origin[3 * cl + 2] = sm > 0.0 ? rint(sz / sm * qs) : 0.0;
+        d.origin[3 * cl] = sm > 0.0 ? sx / sm : 0.0;
+        d.origin[3 * cl + 1] = sm > 0.0 ? sy / sm : 0.0;
+        d.origin[3 * cl + 2] = sm > 0.0 ? sz / sm : 0.0;
     }
 }
 
@@ -725,6 +721,16 @@ __global__ void k_obs_reduce(const Dev d, int k_local, int slot_mode) {
 }
 
 __global__ void k_advance(const Dev d, int n) { *d.step_base += n; }
+
+// Per-atom factors of the current md_step call: h conv / m and sqrt((1 - c1^2) k_B conv / m).
+__global__ void k_prepare(const Dev d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.npad) return;
+    const Run r = *d.run;
+    const double m = d.mass[i];
+    const_cast<double*>(d.hs)[i] = r.h * d.conv / m;
+    const_cast<float*>(d.sig0)[i] = (float)sqrt(r.noise_k / m);
+}
 
 __global__ void k_philox(const uint32_t* in, uint32_t* out, int n) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -856,6 +862,10 @@ cudaError_t launch_mirror(const Dev& d, cudaStream_t s) {
 }
 cudaError_t launch_origin(const Dev& d, cudaStream_t s) {
     k_origin<<<d.B, 32, 0, s>>>(d);
+    return cudaGetLastError();
+}
+cudaError_t launch_prepare(const Dev& d, cudaStream_t s) {
+    k_prepare<<<(d.npad + 255) / 256, 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 cudaError_t launch_obs_reduce(const Dev& d, int k_local, int slot_mode, cudaStream_t s) {

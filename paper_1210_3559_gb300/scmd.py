@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
                 "md_get_state": ([_VP, _DP, _DP, P(i64)], i32),
                 "md_set_state": ([_VP, _DP, _DP, i64], i32),
                 "md_get_forces": ([_VP, _DP], i32),
+                "md_recenter": ([_VP], i32),
                 "md_get_launch": ([_VP, i32, P(i32), P(i32), P(i32)], i32),
                 "md_set_launch": ([_VP, i32, i32, i32, i32], i32),
                 "md_autotune": ([_VP, i32], i32),
@@ -102,7 +103,7 @@ def lib() -> ctypes.CDLL:
 
 def exported_symbols():
     return ["md_abi_version", "md_create", "md_energy_forces", "md_get_density", "md_step", "md_observables",
-            "md_obs_history", "md_clear_history", "md_get_state", "md_set_state", "md_get_forces",
+            "md_obs_history", "md_clear_history", "md_get_state", "md_set_state", "md_get_forces", "md_recenter",
             "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts",
             "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals"]
 
@@ -253,6 +254,10 @@ def md_set_state(ctx: Context, pos, vel, step: int):
     pos = _arr(pos, ctx.ntot)
     vel = _arr(vel, ctx.ntot)
     _check(lib().md_set_state(ctx.handle, pos.ctypes.data_as(_DP), vel.ctypes.data_as(_DP), int(step)), ctx.handle)
+
+
+def md_recenter(ctx: Context):
+    _check(lib().md_recenter(ctx.handle), ctx.handle)
 
 
 def md_get_launch(ctx: Context, which: int):

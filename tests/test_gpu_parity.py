@@ -5,11 +5,12 @@ cluster, since a per-atom relative error is undefined where |F_i| ~ 0):
   FP64 mode  : e_F <= 1e-12, |dE|/|E| <= 1e-13, rho relative <= 1e-13
   MIXED mode : e_F <= 1e-5 (the stated bound for mixed-precision forces),
                |dE|/|E| <= 1e-6, rho relative <= 2e-5.
-The MIXED rho and energy bounds follow from the arithmetic: coordinates sit on a
-fixed-point grid 2^-q with q >= 18 for every size tested, so each coordinate is off
-by at most 2^-(q+1) <= 1.9e-6 A, a pair distance by at most 2 sqrt(3) of that, and a
-term r^-6 by 6 * 6.6e-6 / r >= 2.0 A -> 2e-5 relative in the worst case (typical
-errors are 10-50x smaller); FP32 arithmetic adds ~1e-7.
+The MIXED rho and energy bounds follow from the arithmetic: pair coordinates are
+FP32 offsets from a per-cluster origin at the centre of mass, so for clusters of
+radius R <= 32 A each coordinate is off by at most ulp(32)/2 = 1.9e-6 A, a pair
+distance by at most 2 sqrt(3) of that, and a term r^-6 by 6 * 6.6e-6 / r with
+r >= 2.0 A -> 2e-5 relative in the worst case (typical errors are 10-50x smaller);
+FP32 arithmetic adds ~1e-7.
 Integer work (Philox words) must be bit-exact.
 """
 import os
@@ -244,6 +245,17 @@ def test_checkpoint_resume_is_bitwise(scmd, prec):
     pc, vc, sc = scmd.md_get_state(c)
     assert sa == sc == 100
     assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+
+
+def test_recenter_keeps_forces(scmd):
+    pos = inputs.jitter(inputs.fcc_sphere(300), 0.1, 12)
+    ctx = make(scmd, [300], pos, prec=MIXED)
+    _, F0 = scmd.md_energy_forces(ctx)
+    far = pos + np.array([500.0, -300.0, 250.0])  # same cluster, far from the creation origin
+    scmd.md_set_state(ctx, far, np.zeros_like(far), 0)
+    scmd.md_recenter(ctx)
+    _, F1 = scmd.md_energy_forces(ctx)
+    assert rel_force_err(F1, F0) <= 1e-6
 
 
 def test_observables_and_history(scmd):
