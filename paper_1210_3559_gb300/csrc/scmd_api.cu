@@ -120,6 +120,7 @@ void fill_dev(md_ctx* c) {
     d.npad = c->npad;
     d.ngroups = c->ngroups;
     d.prec = c->cfg.precision;
+    d.single_n = c->B == 1 ? c->sizes[0] : 0;
     d.poff = c->d_poff;
     d.nreal = c->d_nreal;
     d.cl_of_group = c->d_clg;

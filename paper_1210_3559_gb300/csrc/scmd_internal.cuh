@@ -85,6 +85,7 @@ struct Dev {
     int32_t npad;        // padded atoms
     int32_t ngroups;     // npad / 32
     int32_t prec;        // md_precision
+    int32_t single_n;    // atoms of the only cluster when B == 1 (work items computed in place), else 0
     const int32_t* poff; // [B+1] padded offsets
     const int32_t* nreal;// [B] real atoms per cluster
     const int32_t* cl_of_group; // [ngroups] cluster of each 32-atom group

@@ -261,8 +261,34 @@ __device__ __forceinline__ void obs_position_partials(const Dev& d, int group, b
     }
 }
 
+// ------------------------------------------------------------- pass helpers
+// Programmatic dependent launch: let the next kernel in the stream be scheduled
+// early, and wait for the previous one before touching what it wrote.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Thread-block-cluster barrier in two halves (every thread of every CTA takes part).
+__device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// The work item of this CTA: a table entry, or (one cluster per context) computed in place.
+template <int BI> __device__ __forceinline__ Item load_item(const Dev& d, const Item* items, int C) {
+    const int k = blockIdx.x / C;
+    if (d.single_n > 0) {
+        Item it;
+        it.i0 = k * BI;
+        it.ni = min(BI, d.single_n - it.i0);
+        it.j0 = 0;
+        it.nj = d.single_n;
+        it.cl = 0;
+        it.pad = 0;
+        return it;
+    }
+    return items[k];
+}
+
 // ------------------------------------------------------------- density pass
-// Shared memory: tiles [W][32] V4 | red [W][32*IPT] double | cta [32*IPT] double
+// Shared memory: tiles [W][32] V4 | red [W][BI] double | inbox [C][BI] double (read on rank 0)
 template <int PREC, int IPT, int SPECIAL, int CUT>
 __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __restrict__ items, int C, int obs) {
     using R = typename Tr<PREC>::R;
@@ -270,19 +296,28 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
     constexpr int BI = 32 * IPT;
     extern __shared__ __align__(32) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
+    cluster_arrive_relaxed();  // "this CTA has started": waited for before any remote store
+    pdl_launch_dependents();
     const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rank = (int)cluster.block_rank();
-    const Item it = items[blockIdx.x / C];
+    const Item it = load_item<BI>(d, items, C);
     V4* tiles = reinterpret_cast<V4*>(smem);
     double* red = reinterpret_cast<double*>(smem + (size_t)W * 32 * sizeof(V4));
-    double* cta = red + W * BI;
+    double* inbox = red + W * BI;
     const V4* mir = reinterpret_cast<const V4*>(d.mirror);
     const R rc2 = (R)d.pot.rcut2;
     const int mexp = d.pot.m;
+    const int ntile = (it.nj + 31) >> 5;
+    const int Q = C * W, qi = rank * W + warp;
+    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
+    const int tdiag = (it.i0 - it.j0) >> 5;
+    pdl_wait();  // positions come from the previous kernel
 
     R xi[IPT], yi[IPT], zi[IPT];
     double racc[IPT];
     R sacc[IPT];
+    V4 nxt;
+    if (t_beg < t_end) nxt = mir[it.j0 + (t_beg << 5) + lane];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const V4 p = mir[it.i0 + lane + 32 * q];
@@ -292,59 +327,43 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
         racc[q] = 0.0;
         sacc[q] = R(0);
     }
-    const int ntile = (it.nj + 31) >> 5;
-    const int Q = C * W, qi = rank * W + warp;
-    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
-    const int tdiag = (it.i0 - it.j0) >> 5;
     V4* tile = tiles + warp * 32;
     int span = 0;
     for (int t = t_beg; t < t_end; ++t) {
         const int jb = it.j0 + (t << 5);
         __syncwarp();
-        tile[lane] = mir[jb + lane];
+        tile[lane] = nxt;
         __syncwarp();
+        if (t + 1 < t_end) nxt = mir[jb + 32 + lane];
         const int valid = min(32, it.nj - (t << 5));
         const bool diag = (t >= tdiag) && (t < tdiag + IPT);
         R tacc[IPT];
 #pragma unroll
         for (int q = 0; q < IPT; ++q) tacc[q] = R(0);
+#define SCMD_DENSITY_BODY(MASK)                                                \
+    {                                                                          \
+        const V4 p = tile[k];                                                  \
+        _Pragma("unroll") for (int q = 0; q < IPT; ++q) {                      \
+            const R dx = xi[q] - p.x, dy = yi[q] - p.y, dz = zi[q] - p.z;      \
+            R r2 = fma(dx, dx, fma(dy, dy, dz * dz));                          \
+            if (CUT) r2 = (r2 < rc2) ? r2 : big<R>();                          \
+            if (MASK && jb + k == it.i0 + lane + 32 * q) r2 = big<R>();        \
+            if (SPECIAL) {                                                     \
+                const R inv = inv_r2(r2);                                      \
+                tacc[q] = fma(inv * inv, inv, tacc[q]);                        \
+            } else {                                                           \
+                const R ir = inv_r(r2);                                        \
+                tacc[q] += rpow(ir * ir, ir, mexp);                            \
+            }                                                                  \
+        }                                                                      \
+    }
         if (!diag && valid == 32) {
 #pragma unroll 8
-            for (int k = 0; k < 32; ++k) {
-                const V4 p = tile[k];
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) {
-                    const R dx = xi[q] - p.x, dy = yi[q] - p.y, dz = zi[q] - p.z;
-                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    if (CUT) r2 = (r2 < rc2) ? r2 : big<R>();
-                    if (SPECIAL) {
-                        const R inv = inv_r2(r2);
-                        tacc[q] = fma(inv * inv, inv, tacc[q]);
-                    } else {
-                        const R ir = inv_r(r2);
-                        tacc[q] += rpow(ir * ir, ir, mexp);
-                    }
-                }
-            }
+            for (int k = 0; k < 32; ++k) SCMD_DENSITY_BODY(false)
         } else {
-            for (int k = 0; k < valid; ++k) {
-                const V4 p = tile[k];
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) {
-                    const R dx = xi[q] - p.x, dy = yi[q] - p.y, dz = zi[q] - p.z;
-                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    if (CUT) r2 = (r2 < rc2) ? r2 : big<R>();
-                    if (jb + k == it.i0 + lane + 32 * q) r2 = big<R>();
-                    if (SPECIAL) {
-                        const R inv = inv_r2(r2);
-                        tacc[q] = fma(inv * inv, inv, tacc[q]);
-                    } else {
-                        const R ir = inv_r(r2);
-                        tacc[q] += rpow(ir * ir, ir, mexp);
-                    }
-                }
-            }
+            for (int k = 0; k < valid; ++k) SCMD_DENSITY_BODY(true)
         }
+#undef SCMD_DENSITY_BODY
 #pragma unroll
         for (int q = 0; q < IPT; ++q) sacc[q] += tacc[q];
         if (++span == 4) {
@@ -359,68 +378,104 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
 #pragma unroll
     for (int q = 0; q < IPT; ++q) red[warp * BI + q * 32 + lane] = racc[q] + (double)sacc[q];
     __syncthreads();
+    cluster_wait();  // every CTA of the cluster has started: its shared memory may be written
     if (threadIdx.x < BI) {
         double s = 0.0;
         for (int w = 0; w < W; ++w) s += red[w * BI + threadIdx.x];
-        cta[threadIdx.x] = s;
+        *cluster.map_shared_rank(inbox + rank * BI + threadIdx.x, 0) = s;
     }
-    cluster.sync();
-    if (rank == 0 && threadIdx.x < BI) {
-        double tot = 0.0;
-        for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(cta + threadIdx.x, r);
-        const int t = threadIdx.x, i = it.i0 + t;
-        const bool real = t < it.ni;
-        const double rho = tot * d.pot.am;
-        V4 p = mir[i];
-        if (real) {
-            d.rho[i] = rho;
-            if (PREC == 1) {
-                const float rf = (float)rho;
-                float y = rsqrt_approx(rf);
-                y = y * (1.5f - 0.5f * rf * y * y);  // one Newton step
-                p.w = rho > 0.0 ? (float)d.pot.B6 * y : 0.0f;
-            } else {
-                p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
-            }
-            reinterpret_cast<V4*>(d.posg)[i] = p;
+    cluster_arrive_release();
+    cluster_wait();
+    if (rank != 0 || threadIdx.x >= BI) return;
+    double tot = 0.0;
+    for (int r = 0; r < C; ++r) tot += inbox[r * BI + threadIdx.x];
+    const int t = threadIdx.x, i = it.i0 + t;
+    const bool real = t < it.ni;
+    const double rho = tot * d.pot.am;
+    if (real) {
+        const int q = t >> 5;  // this thread's own atom is its q-th i-atom
+        V4 p;
+        p.x = (q == 0) ? xi[0] : xi[IPT - 1];
+        p.y = (q == 0) ? yi[0] : yi[IPT - 1];
+        p.z = (q == 0) ? zi[0] : zi[IPT - 1];
+        d.rho[i] = rho;
+        if (PREC == 1) {
+            const float rf = (float)rho;
+            float y = rsqrt_approx(rf);
+            y = y * (1.5f - 0.5f * rf * y * y);  // one Newton step
+            p.w = rho > 0.0 ? (float)d.pot.B6 * y : 0.0f;
+        } else {
+            p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
         }
-        if (obs) {
-            double e = real ? -d.pot.eps * d.pot.c * sqrt(rho) : 0.0;
-            e = warp_sum(e);
-            if (lane == 0) d.part[(size_t)(i >> 5) * kObsFields + OF_EEMB] = e;
-        }
+        reinterpret_cast<V4*>(d.posg)[i] = p;
     }
-    cluster.sync();
+    if (obs) {
+        double e = real ? -d.pot.eps * d.pot.c * sqrt(rho) : 0.0;
+        e = warp_sum(e);
+        if (lane == 0) d.part[(size_t)(i >> 5) * kObsFields + OF_EEMB] = e;
+    }
 }
 
 // --------------------------------------------------------------- force pass
-// Shared memory: tiles [W][32] V4 | redf [W][32*IPT][3] R | rede [W][32*IPT] double
-//                | ctaf [32*IPT][3] R | ctae [32*IPT] double
+// Shared memory: tiles [W][32] V4 | rede [W][BI] double | inboxe [C][BI] double
+//                | redf [W][BI][3] R | inboxf [C][BI][3] R
 template <int PREC, int IPT, int SPECIAL, int CUT, int ENERGY>
 __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __restrict__ items, int C, int mode, int k_local,
-                                               int last) {
+                                                  int last) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     constexpr int BI = 32 * IPT;
     extern __shared__ __align__(32) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
+    cluster_arrive_relaxed();
+    pdl_launch_dependents();
     const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rank = (int)cluster.block_rank();
-    const Item it = items[blockIdx.x / C];
+    const Item it = load_item<BI>(d, items, C);
     V4* tiles = reinterpret_cast<V4*>(smem);
     double* rede = reinterpret_cast<double*>(smem + (size_t)W * 32 * sizeof(V4));
-    double* ctae = rede + W * BI;
-    R* redf = reinterpret_cast<R*>(ctae + BI);
-    R* ctaf = redf + W * BI * 3;
+    double* inboxe = rede + W * BI;
+    R* redf = reinterpret_cast<R*>(inboxe + C * BI);
+    R* inboxf = redf + W * BI * 3;
     const V4* pg = reinterpret_cast<const V4*>(d.posg);
     const R A = (R)d.pot.A9;
     const R rc2 = (R)d.pot.rcut2;
     const int nexp = d.pot.n, mexp = d.pot.m;
+    const int ntile = (it.nj + 31) >> 5;
+    const int Q = C * W, qi = rank * W + warp;
+    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
+    const int tdiag = (it.i0 - it.j0) >> 5;
+    // epilogue owner: rank 0, thread t < BI owns atom i0 + t
+    const bool owner = rank == 0 && threadIdx.x < BI;
+    const bool oreal = owner && (int)threadIdx.x < it.ni;
+    const int io = it.i0 + threadIdx.x;
+    const Run* __restrict__ run = d.run;
+    float zz[3] = {0.f, 0.f, 0.f};
+    int64_t step = 0;
+    const bool integrate = mode == 2;
+    pdl_wait();  // posg comes from the density pass; x, v and the step counter from earlier kernels
+    // Fetch what the epilogue needs, and draw the thermostat noise (a function of seed,
+    // cluster, atom and step only), before the pair loop so that their latency is hidden.
+    if (integrate && oreal && !last && PREC == 1 && run->kind == 1) {
+        step = *d.step_base + k_local;
+        normals_f32(run->seed, (uint32_t)it.cl, step + 1, (uint32_t)(io - it.j0), zz);
+    }
+    double vx0 = 0, vy0 = 0, vz0 = 0, hs = 0, m = 0;
+    if (integrate && oreal) {
+        const int np = d.npad;
+        vx0 = d.v[io];
+        vy0 = d.v[np + io];
+        vz0 = d.v[2 * np + io];
+        hs = d.hs[io];
+        m = d.mass[io];
+    }
 
     R xi[IPT], yi[IPT], zi[IPT], gi[IPT];
     R fx[IPT], fy[IPT], fz[IPT], sx[IPT], sy[IPT], sz[IPT];
     R es[IPT];
     double ea[IPT];
+    V4 nxt;
+    if (t_beg < t_end) nxt = pg[it.j0 + (t_beg << 5) + lane];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const V4 p = pg[it.i0 + lane + 32 * q];
@@ -433,17 +488,14 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
         es[q] = R(0);
         ea[q] = 0.0;
     }
-    const int ntile = (it.nj + 31) >> 5;
-    const int Q = C * W, qi = rank * W + warp;
-    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
-    const int tdiag = (it.i0 - it.j0) >> 5;
     V4* tile = tiles + warp * 32;
     int span = 0;
     for (int t = t_beg; t < t_end; ++t) {
         const int jb = it.j0 + (t << 5);
         __syncwarp();
-        tile[lane] = pg[jb + lane];
+        tile[lane] = nxt;
         __syncwarp();
+        if (t + 1 < t_end) nxt = pg[jb + 32 + lane];
         const int valid = min(32, it.nj - (t << 5));
         const bool diag = (t >= tdiag) && (t < tdiag + IPT);
         R tx[IPT], ty[IPT], tz[IPT], te[IPT];
@@ -506,95 +558,147 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     }
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
-        const int s = warp * BI + q * 32 + lane;
-        redf[3 * s + 0] = fx[q] + sx[q];
-        redf[3 * s + 1] = fy[q] + sy[q];
-        redf[3 * s + 2] = fz[q] + sz[q];
-        if (ENERGY) rede[s] = ea[q] + (double)es[q];
+        const int sidx = warp * BI + q * 32 + lane;
+        redf[3 * sidx + 0] = fx[q] + sx[q];
+        redf[3 * sidx + 1] = fy[q] + sy[q];
+        redf[3 * sidx + 2] = fz[q] + sz[q];
+        if (ENERGY) rede[sidx] = ea[q] + (double)es[q];
     }
     __syncthreads();
+    cluster_wait();  // every CTA of the cluster has started
     if (threadIdx.x < BI) {
         R ax = R(0), ay = R(0), az = R(0);
         double ae = 0.0;
         for (int w = 0; w < W; ++w) {
-            const int s = w * BI + threadIdx.x;
-            ax += redf[3 * s];
-            ay += redf[3 * s + 1];
-            az += redf[3 * s + 2];
-            if (ENERGY) ae += rede[s];
+            const int sidx = w * BI + threadIdx.x;
+            ax += redf[3 * sidx];
+            ay += redf[3 * sidx + 1];
+            az += redf[3 * sidx + 2];
+            if (ENERGY) ae += rede[sidx];
         }
-        ctaf[3 * threadIdx.x] = ax;
-        ctaf[3 * threadIdx.x + 1] = ay;
-        ctaf[3 * threadIdx.x + 2] = az;
-        if (ENERGY) ctae[threadIdx.x] = ae;
+        R* dst = cluster.map_shared_rank(inboxf + 3 * (rank * BI + threadIdx.x), 0);
+        dst[0] = ax;
+        dst[1] = ay;
+        dst[2] = az;
+        if (ENERGY) *cluster.map_shared_rank(inboxe + rank * BI + threadIdx.x, 0) = ae;
     }
-    cluster.sync();
-    if (rank == 0 && threadIdx.x < BI) {
-        R Fx = R(0), Fy = R(0), Fz = R(0);
-        double Ep = 0.0;
-        for (int r = 0; r < C; ++r) {
-            const R* rf = cluster.map_shared_rank(ctaf, r);
-            Fx += rf[3 * threadIdx.x];
-            Fy += rf[3 * threadIdx.x + 1];
-            Fz += rf[3 * threadIdx.x + 2];
-            if (ENERGY) Ep += *cluster.map_shared_rank(ctae + threadIdx.x, r);
+    cluster_arrive_release();
+    cluster_wait();
+    if (!owner) return;
+    R Fx = R(0), Fy = R(0), Fz = R(0);
+    double Ep = 0.0;
+    for (int r = 0; r < C; ++r) {
+        const R* rf = inboxf + 3 * (r * BI + threadIdx.x);
+        Fx += rf[0];
+        Fy += rf[1];
+        Fz += rf[2];
+        if (ENERGY) Ep += inboxe[r * BI + threadIdx.x];
+    }
+    const int i = io, np = d.npad;
+    const bool real = oreal;
+    R* fo = reinterpret_cast<R*>(d.f);
+    if (real) {
+        fo[i] = Fx;
+        fo[np + i] = Fy;
+        fo[2 * np + i] = Fz;
+        if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+    }
+    const int group = i >> 5;
+    if (mode == 1) {
+        // fresh evaluation: all observable partials at the current (x, v)
+        const double mm = real ? d.mass[i] : 0.0;
+        if (ENERGY) {
+            const double e = warp_sum(real ? Ep : 0.0);
+            if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
         }
-        const int t = threadIdx.x, i = it.i0 + t, np = d.npad;
-        const bool real = t < it.ni;
-        R* fo = reinterpret_cast<R*>(d.f);
+        const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
+        const double vx = real ? d.v[i] : 0.0, vy = real ? d.v[np + i] : 0.0, vz = real ? d.v[2 * np + i] : 0.0;
+        obs_velocity_partials(d, group, real, mm, x, y, z, vx, vy, vz, lane);
+        obs_position_partials(d, group, real, mm, x, y, z, lane);
+    } else if (mode == 2) {
+        const Run r = *run;
+        step = *d.step_base + k_local;  // this pass completes step -> step + 1
+        double vx = 0.0, vy = 0.0, vz = 0.0;
         if (real) {
-            fo[i] = Fx;
-            fo[np + i] = Fy;
-            fo[2 * np + i] = Fz;
-            if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+            vx = fma(hs, (double)Fx, vx0);
+            vy = fma(hs, (double)Fy, vy0);
+            vz = fma(hs, (double)Fz, vz0);
         }
-        const int group = i >> 5;
-        const double m = real ? d.mass[i] : 0.0;
-        if (mode == 1) {
-            // fresh evaluation: all observable partials at the current (x, v)
-            if (ENERGY) {
-                const double e = warp_sum(real ? Ep : 0.0);
-                if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
-            }
-            const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
-            const double vx = real ? d.v[i] : 0.0, vy = real ? d.v[np + i] : 0.0, vz = real ? d.v[2 * np + i] : 0.0;
-            obs_velocity_partials(d, group, real, m, x, y, z, vx, vy, vz, lane);
+        double x = 0.0, y = 0.0, z = 0.0;
+        if (real) {
+            x = d.x[i];
+            y = d.x[np + i];
+            z = d.x[2 * np + i];
+        }
+        if (ENERGY) {  // observables are due at step + 1 (the host compiles ENERGY in only then)
+            const double e = warp_sum(real ? Ep : 0.0);
+            if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
             obs_position_partials(d, group, real, m, x, y, z, lane);
-        } else if (mode == 2) {
-            const Run r = *d.run;
-            const int64_t step = *d.step_base + k_local;  // this pass completes step -> step + 1
-            double vx = 0.0, vy = 0.0, vz = 0.0;
+            if (r.kind != 2) obs_velocity_partials(d, group, real, m, x, y, z, vx, vy, vz, lane);
+        }
+        if (r.kind == 2) {
             if (real) {
-                const double hs = d.hs[i];
-                vx = fma(hs, (double)Fx, d.v[i]);
-                vy = fma(hs, (double)Fy, d.v[np + i]);
-                vz = fma(hs, (double)Fz, d.v[2 * np + i]);
                 d.v[i] = vx;
                 d.v[np + i] = vy;
                 d.v[2 * np + i] = vz;
             }
-            const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
-            if (ENERGY) {  // observables are due at step + 1 (the host only enables ENERGY then)
-                const double e = warp_sum(real ? Ep : 0.0);
-                if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
-                obs_position_partials(d, group, real, m, x, y, z, lane);
-                if (r.kind != 2) obs_velocity_partials(d, group, real, m, x, y, z, vx, vy, vz, lane);
-            }
-            if (r.kind == 2) {
-                const double ke2 = warp_sum(real ? m * (vx * vx + vy * vy + vz * vz) : 0.0);
-                if (lane == 0) d.ke_grp[group] = ke2;
-            } else if (!last && real) {
-                const int cl = it.cl;
-                begin_step<PREC>(d, r, i, cl, i - it.j0, step + 1, (double)Fx, (double)Fy, (double)Fz);
+            const double ke2 = warp_sum(real ? m * (vx * vx + vy * vy + vz * vz) : 0.0);
+            if (lane == 0) d.ke_grp[group] = ke2;
+        } else if (real) {
+            if (last) {
+                d.v[i] = vx;
+                d.v[np + i] = vy;
+                d.v[2 * np + i] = vz;
+            } else {
+                // start of the next step: B (A O A | A A), new mirror
+                const int64_t s1 = step + 1;
+                vx = fma(hs, (double)Fx, vx);
+                vy = fma(hs, (double)Fy, vy);
+                vz = fma(hs, (double)Fz, vz);
+                if (r.kind == 1) {
+                    x = fma(r.h, vx, x);
+                    y = fma(r.h, vy, y);
+                    z = fma(r.h, vz, z);
+                    if (PREC == 1) {
+                        const float sf = d.sig0[i] * sqrtf((float)fmax(ramp_T(r, s1), 0.0));
+                        vx = fma(r.c1, vx, (double)(sf * zz[0]));
+                        vy = fma(r.c1, vy, (double)(sf * zz[1]));
+                        vz = fma(r.c1, vz, (double)(sf * zz[2]));
+                    } else {
+                        double z64[3];
+                        normals_f64(r.seed, (uint32_t)it.cl, s1, (uint32_t)(i - it.j0), z64);
+                        const double sig = sqrt(r.noise_k * fmax(ramp_T(r, s1), 0.0) / m);
+                        vx = fma(r.c1, vx, sig * z64[0]);
+                        vy = fma(r.c1, vy, sig * z64[1]);
+                        vz = fma(r.c1, vz, sig * z64[2]);
+                    }
+                    x = fma(r.h, vx, x);
+                    y = fma(r.h, vy, y);
+                    z = fma(r.h, vz, z);
+                } else {
+                    x = fma(r.dt, vx, x);
+                    y = fma(r.dt, vy, y);
+                    z = fma(r.dt, vz, z);
+                }
+                d.v[i] = vx;
+                d.v[np + i] = vy;
+                d.v[2 * np + i] = vz;
+                d.x[i] = x;
+                d.x[np + i] = y;
+                d.x[2 * np + i] = z;
+                if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+                    atomicOr(d.status, 1);
+                store_mirror<PREC>(d, i, it.cl, x, y, z);
             }
         }
     }
-    cluster.sync();
 }
 
 // ------------------------------------------------------------ per-atom kernels
 // One 32-thread CTA per 32-atom group; the group's cluster comes from a table.
 template <int PREC> __global__ void k_start(const Dev d, int k_local) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int g = blockIdx.x, lane = threadIdx.x, i = g * 32 + lane;
     const int cl = d.cl_of_group[g];
     const int a = i - d.poff[cl];
@@ -606,6 +710,8 @@ template <int PREC> __global__ void k_start(const Dev d, int k_local) {
 }
 
 template <int PREC> __global__ void k_berendsen(const Dev d, int k_local, int last) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int g = blockIdx.x, lane = threadIdx.x, i = g * 32 + lane;
     const int cl = d.cl_of_group[g];
     const int g0 = d.poff[cl] >> 5, g1 = d.poff[cl + 1] >> 5;
@@ -645,6 +751,8 @@ template <int PREC> __global__ void k_berendsen(const Dev d, int k_local, int la
 
 // Mirror of the current positions relative to the cluster origins.
 template <int PREC> __global__ void k_mirror(const Dev d) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int g = blockIdx.x, lane = threadIdx.x, i = g * 32 + lane;
     const int cl = d.cl_of_group[g];
     if (i - d.poff[cl] >= d.nreal[cl]) return;
@@ -653,6 +761,8 @@ template <int PREC> __global__ void k_mirror(const Dev d) {
 
 // Mirror origin of each cluster = its centre of mass (one CTA of 32 threads per cluster).
 __global__ void k_origin(const Dev d) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int cl = blockIdx.x, lane = threadIdx.x;
     const int b = d.poff[cl], n = d.nreal[cl], np = d.npad;
     double sx = 0.0, sy = 0.0, sz = 0.0, sm = 0.0;
@@ -677,6 +787,8 @@ __global__ void k_origin(const Dev d) {
 // Observables of every cluster from the group partials (one CTA of 32 threads per cluster).
 // slot_mode 0: the "current" slot (index hist_cap); 1: ring slot of step base + k_local + 1.
 __global__ void k_obs_reduce(const Dev d, int k_local, int slot_mode) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int cl = blockIdx.x, lane = threadIdx.x;
     const int g0 = d.poff[cl] >> 5, g1 = d.poff[cl + 1] >> 5;
     double s[kObsFields];
@@ -720,10 +832,16 @@ __global__ void k_obs_reduce(const Dev d, int k_local, int slot_mode) {
     h[15] = bad ? 1.0 : 0.0;
 }
 
-__global__ void k_advance(const Dev d, int n) { *d.step_base += n; }
+__global__ void k_advance(const Dev d, int n) {
+    pdl_launch_dependents();
+    pdl_wait();
+    *d.step_base += n;
+}
 
 // Per-atom factors of the current md_step call: h conv / m and sqrt((1 - c1^2) k_B conv / m).
 __global__ void k_prepare(const Dev d) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.npad) return;
     const Run r = *d.run;
@@ -758,28 +876,41 @@ __global__ void k_normals(uint64_t seed, uint32_t cl, int64_t step, int n, int p
 size_t pass_smem_bytes(int prec, Shape sh) {
     const size_t v4 = prec == 1 ? sizeof(float4) : sizeof(dbl4);
     const size_t r = prec == 1 ? sizeof(float) : sizeof(double);
-    const size_t BI = 32 * (size_t)sh.ipt, W = sh.warps;
+    const size_t BI = 32 * (size_t)sh.ipt, W = sh.warps, C = sh.cluster;
     const size_t tiles = W * 32 * v4;
-    const size_t dens = (W + 1) * BI * sizeof(double);
-    const size_t force = (W + 1) * BI * sizeof(double) + (W + 1) * BI * 3 * r;
+    const size_t dens = (W + C) * BI * sizeof(double);
+    const size_t force = (W + C) * BI * sizeof(double) + (W + C) * BI * 3 * r;
     return tiles + (dens > force ? dens : force);
 }
 
+// Every kernel is launched with programmatic stream serialization (it waits on its
+// predecessor with griddepcontrol.wait) and, when C > 0, as clusters of C CTAs.
 template <class K, class... Args>
-static cudaError_t launch_cluster(K kernel, int grid, int threads, size_t smem, int C, cudaStream_t s, Args... args) {
+static cudaError_t launch_ex(K kernel, int grid, int threads, size_t smem, int C, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+    if (C > 0) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = C;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <class K, class... Args>
+static cudaError_t launch_cluster(K kernel, int grid, int threads, size_t smem, int C, cudaStream_t s, Args... args) {
+    return launch_ex(kernel, grid, threads, smem, C, s, args...);
 }
 
 template <int PREC, int IPT, int SPECIAL, int CUT>
@@ -841,40 +972,30 @@ cudaError_t launch_force(const Dev& d, const Item* items, int nitems, Shape sh, 
 
 cudaError_t launch_start(const Dev& d, int k_local, cudaStream_t s) {
     if (d.prec == 1)
-        k_start<1><<<d.ngroups, 32, 0, s>>>(d, k_local);
-    else
-        k_start<0><<<d.ngroups, 32, 0, s>>>(d, k_local);
-    return cudaGetLastError();
+        return launch_ex(k_start<1>, d.ngroups, 32, 0, 0, s, d, k_local);
+    return launch_ex(k_start<0>, d.ngroups, 32, 0, 0, s, d, k_local);
 }
 cudaError_t launch_berendsen(const Dev& d, int k_local, int last, cudaStream_t s) {
     if (d.prec == 1)
-        k_berendsen<1><<<d.ngroups, 32, 0, s>>>(d, k_local, last);
-    else
-        k_berendsen<0><<<d.ngroups, 32, 0, s>>>(d, k_local, last);
-    return cudaGetLastError();
+        return launch_ex(k_berendsen<1>, d.ngroups, 32, 0, 0, s, d, k_local, last);
+    return launch_ex(k_berendsen<0>, d.ngroups, 32, 0, 0, s, d, k_local, last);
 }
 cudaError_t launch_mirror(const Dev& d, cudaStream_t s) {
     if (d.prec == 1)
-        k_mirror<1><<<d.ngroups, 32, 0, s>>>(d);
-    else
-        k_mirror<0><<<d.ngroups, 32, 0, s>>>(d);
-    return cudaGetLastError();
+        return launch_ex(k_mirror<1>, d.ngroups, 32, 0, 0, s, d);
+    return launch_ex(k_mirror<0>, d.ngroups, 32, 0, 0, s, d);
 }
 cudaError_t launch_origin(const Dev& d, cudaStream_t s) {
-    k_origin<<<d.B, 32, 0, s>>>(d);
-    return cudaGetLastError();
+    return launch_ex(k_origin, d.B, 32, 0, 0, s, d);
 }
 cudaError_t launch_prepare(const Dev& d, cudaStream_t s) {
-    k_prepare<<<(d.npad + 255) / 256, 256, 0, s>>>(d);
-    return cudaGetLastError();
+    return launch_ex(k_prepare, (d.npad + 255) / 256, 256, 0, 0, s, d);
 }
 cudaError_t launch_obs_reduce(const Dev& d, int k_local, int slot_mode, cudaStream_t s) {
-    k_obs_reduce<<<d.B, 32, 0, s>>>(d, k_local, slot_mode);
-    return cudaGetLastError();
+    return launch_ex(k_obs_reduce, d.B, 32, 0, 0, s, d, k_local, slot_mode);
 }
 cudaError_t launch_advance(const Dev& d, int n, cudaStream_t s) {
-    k_advance<<<1, 1, 0, s>>>(d, n);
-    return cudaGetLastError();
+    return launch_ex(k_advance, 1, 1, 0, 0, s, d, n);
 }
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
