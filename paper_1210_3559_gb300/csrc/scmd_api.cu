@@ -62,6 +62,8 @@ struct md_ctx {
     double *d_x = nullptr, *d_v = nullptr, *d_mass = nullptr, *d_rho = nullptr, *d_origin = nullptr;
     double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr, *d_hs = nullptr;
     float* d_sig0 = nullptr;
+    float4* d_noise = nullptr;
+    int noise_steps = 0;  // capacity of d_noise in steps (MIXED); chunks never exceed it
     void *d_f = nullptr, *d_mirror = nullptr, *d_posg = nullptr;
     int64_t* d_step = nullptr;
     Run* d_run = nullptr;
@@ -134,6 +136,7 @@ void fill_dev(md_ctx* c) {
     d.origin = c->d_origin;
     d.hs = c->d_hs;
     d.sig0 = c->d_sig0;
+    d.noise = c->d_noise;
     d.part = c->d_part;
     d.ke_grp = c->d_ke;
     d.hist = c->d_hist;
@@ -230,6 +233,7 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
     const Item* i0 = items_for(c, c->shape[0], &n0);
     const Item* i1 = items_for(c, c->shape[1], &n1);
     const int oe = c->cfg.obs_every;
+    if (kind == MD_LANGEVIN && c->cfg.precision == MD_PREC_MIXED) CK(c, launch_noise(d, M, c->stream));
     CK(c, launch_start(d, 0, c->stream));
     for (int k = 0; k < M; ++k) {
         const int64_t next = s0 + k + 1;
@@ -292,7 +296,7 @@ void free_all(md_ctx* c) {
     drop_graphs(c);
     void* ptrs[] = {c->d_poff, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
-                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0};
+                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -534,6 +538,13 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_origin, sizeof(double) * 3 * n_clusters));
     CKC(cudaMalloc(&c->d_hs, sizeof(double) * np));
     CKC(cudaMalloc(&c->d_sig0, sizeof(float) * np));
+    if (cfg->precision == MD_PREC_MIXED) {
+        // Langevin normals of a whole chunk are drawn ahead of it; the buffer holds at most
+        // 256 MB, which bounds the chunk length for very large batches.
+        const size_t per_step = sizeof(float4) * np;
+        c->noise_steps = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->cfg.graph_chunk, (256u << 20) / per_step));
+        CKC(cudaMalloc(&c->d_noise, per_step * c->noise_steps));
+    }
     CKC(cudaMalloc(&c->d_part, sizeof(double) * kObsFields * c->ngroups));
     CKC(cudaMalloc(&c->d_ke, sizeof(double) * c->ngroups));
     CKC(cudaMalloc(&c->d_hist, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
@@ -707,7 +718,8 @@ md_status md_step(md_ctx* c, int64_t nsteps, double dt, const md_thermostat* th)
     CK(c, launch_prepare(c->dev, c->stream));
     md_status st = set_step_base(c, c->step);
     if (st != MD_OK) return st;
-    const int chunk = c->cfg.graph_chunk;
+    const int chunk = c->cfg.precision == MD_PREC_MIXED ? std::min(c->cfg.graph_chunk, c->noise_steps)
+                                                        : c->cfg.graph_chunk;
     int64_t done = 0;
     const double t_call0 = c->time_fs;
     while (done < nsteps) {
@@ -931,7 +943,7 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
     if (per_step) *per_step = 2;
-    if (per_chunk) *per_chunk = 2;
+    if (per_chunk) *per_chunk = 3;
     return MD_OK;
 }
 

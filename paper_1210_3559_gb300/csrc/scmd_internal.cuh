@@ -99,6 +99,7 @@ struct Dev {
     double* origin;      // [B][3] MIXED mirror origin; FP64: unused
     const double* hs;    // [npad] half-step kick factor h * conv / m (per md_step call)
     const float* sig0;   // [npad] sqrt((1 - c1^2) k_B conv / m) (Langevin, per md_step call)
+    float4* noise;       // [noise_steps][npad] Langevin normals of the running chunk (MIXED)
     double* part;        // [ngroups][kObsFields]
     double* ke_grp;      // [ngroups] sum m v^2 (Berendsen)
     double* hist;        // ring [cap][B][kHistFields]
@@ -118,6 +119,7 @@ struct Shape { int ipt, warps, cluster; };
 cudaError_t launch_mirror(const Dev& d, cudaStream_t s);
 cudaError_t launch_origin(const Dev& d, cudaStream_t s);
 cudaError_t launch_prepare(const Dev& d, cudaStream_t s);
+cudaError_t launch_noise(const Dev& d, int M, cudaStream_t s);
 cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s);
 // mode: 0 = forces only (store F), 1 = forces + all observable partials (no integration),
 //       2 = MD step: finish the half kick, record observables if due, start the next step unless last.

@@ -175,7 +175,7 @@ template <int PREC> __device__ __forceinline__ void load_force(const Dev& d, int
 // FP64 work here is multiply-adds only.
 template <int PREC>
 __device__ __forceinline__ void begin_step(const Dev& d, const Run& r, int i, int cl, int atom, int64_t step,
-                                           double fx, double fy, double fz) {
+                                           double fx, double fy, double fz, int noise_slot) {
     const int np = d.npad;
     const double hs = d.hs[i];
     double vx = fma(hs, fx, d.v[i]), vy = fma(hs, fy, d.v[np + i]), vz = fma(hs, fz, d.v[2 * np + i]);
@@ -187,7 +187,14 @@ __device__ __forceinline__ void begin_step(const Dev& d, const Run& r, int i, in
         const double T = fmax(ramp_T(r, step), 0.0);
         if (PREC == 1) {
             float zz[3];
-            normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
+            if (noise_slot >= 0) {
+                const float4 nz = d.noise[(size_t)noise_slot * np + i];
+                zz[0] = nz.x;
+                zz[1] = nz.y;
+                zz[2] = nz.z;
+            } else {
+                normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
+            }
             const float sf = d.sig0[i] * sqrtf((float)T);
             vx = fma(r.c1, vx, (double)(sf * zz[0]));
             vy = fma(r.c1, vy, (double)(sf * zz[1]));
@@ -261,6 +268,41 @@ __device__ __forceinline__ void obs_position_partials(const Dev& d, int group, b
     }
 }
 
+// ------------------------------------------------------- double-float sums
+// An unevaluated sum hi + lo of two FP32 numbers, added with Knuth's error-free
+// TwoSum, carries ~2^-44 relative accuracy on the FP32 pipe; the FP64 pipe of this
+// part (1/64 of FP32, 64-cycle dependent latency) is kept off the reduction chain.
+struct f2sum {
+    float hi, lo;
+};
+__device__ __forceinline__ f2sum two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ f2sum f2_add(f2sum a, float b) {
+    const f2sum t = two_sum(a.hi, b);
+    const float lo = t.lo + a.lo;
+    const float hi = t.hi + lo;
+    return {hi, lo - (hi - t.hi)};
+}
+__device__ __forceinline__ f2sum f2_add(f2sum a, f2sum b) {
+    const f2sum t = two_sum(a.hi, b.hi);
+    const float lo = t.lo + (a.lo + b.lo);
+    const float hi = t.hi + lo;
+    return {hi, lo - (hi - t.hi)};
+}
+// Pin a loaded value in a register at this point: the load must complete here, so the
+// compiler cannot sink it to its use after the pair loop (where its latency would show).
+__device__ __forceinline__ void pin(double v) { asm volatile("" ::"d"(v)); }
+__device__ __forceinline__ void pin(float v) { asm volatile("" ::"f"(v)); }
+__device__ __forceinline__ void pin(long long v) { asm volatile("" ::"l"(v)); }
+// Exponent-field test on the integer pipe (IEEE double finite iff exponent != all ones).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
 // ------------------------------------------------------------- pass helpers
 // Programmatic dependent launch: let the next kernel in the stream be scheduled
 // early, and wait for the previous one before touching what it wrote.
@@ -302,8 +344,11 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
     const int rank = (int)cluster.block_rank();
     const Item it = load_item<BI>(d, items, C);
     V4* tiles = reinterpret_cast<V4*>(smem);
+    // MIXED: partials are double-float (2 floats); FP64: one double (same 8 bytes)
     double* red = reinterpret_cast<double*>(smem + (size_t)W * 32 * sizeof(V4));
     double* inbox = red + W * BI;
+    f2sum* red2 = reinterpret_cast<f2sum*>(red);
+    f2sum* inbox2 = reinterpret_cast<f2sum*>(inbox);
     const V4* mir = reinterpret_cast<const V4*>(d.mirror);
     const R rc2 = (R)d.pot.rcut2;
     const int mexp = d.pot.m;
@@ -315,6 +360,7 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
 
     R xi[IPT], yi[IPT], zi[IPT];
     double racc[IPT];
+    f2sum facc[IPT];
     R sacc[IPT];
     V4 nxt;
     if (t_beg < t_end) nxt = mir[it.j0 + (t_beg << 5) + lane];
@@ -325,6 +371,7 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
         yi[q] = p.y;
         zi[q] = p.z;
         racc[q] = 0.0;
+        facc[q] = {0.f, 0.f};
         sacc[q] = R(0);
     }
     V4* tile = tiles + warp * 32;
@@ -370,25 +417,46 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
             span = 0;
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
-                racc[q] += (double)sacc[q];
+                if (PREC == 1)
+                    facc[q] = f2_add(facc[q], (float)sacc[q]);
+                else
+                    racc[q] += (double)sacc[q];
                 sacc[q] = R(0);
             }
         }
     }
 #pragma unroll
-    for (int q = 0; q < IPT; ++q) red[warp * BI + q * 32 + lane] = racc[q] + (double)sacc[q];
+    for (int q = 0; q < IPT; ++q) {
+        if (PREC == 1)
+            red2[warp * BI + q * 32 + lane] = f2_add(facc[q], (float)sacc[q]);
+        else
+            red[warp * BI + q * 32 + lane] = racc[q] + (double)sacc[q];
+    }
     __syncthreads();
     cluster_wait();  // every CTA of the cluster has started: its shared memory may be written
     if (threadIdx.x < BI) {
-        double s = 0.0;
-        for (int w = 0; w < W; ++w) s += red[w * BI + threadIdx.x];
-        *cluster.map_shared_rank(inbox + rank * BI + threadIdx.x, 0) = s;
+        if (PREC == 1) {
+            f2sum s2 = red2[threadIdx.x];
+            for (int w = 1; w < W; ++w) s2 = f2_add(s2, red2[w * BI + threadIdx.x]);
+            *cluster.map_shared_rank(inbox2 + rank * BI + threadIdx.x, 0) = s2;
+        } else {
+            double s = 0.0;
+            for (int w = 0; w < W; ++w) s += red[w * BI + threadIdx.x];
+            *cluster.map_shared_rank(inbox + rank * BI + threadIdx.x, 0) = s;
+        }
     }
     cluster_arrive_release();
     cluster_wait();
     if (rank != 0 || threadIdx.x >= BI) return;
-    double tot = 0.0;
-    for (int r = 0; r < C; ++r) tot += inbox[r * BI + threadIdx.x];
+    double tot;
+    if (PREC == 1) {
+        f2sum t2 = inbox2[threadIdx.x];
+        for (int r = 1; r < C; ++r) t2 = f2_add(t2, inbox2[r * BI + threadIdx.x]);
+        tot = (double)t2.hi + (double)t2.lo;
+    } else {
+        tot = 0.0;
+        for (int r = 0; r < C; ++r) tot += inbox[r * BI + threadIdx.x];
+    }
     const int t = threadIdx.x, i = it.i0 + t;
     const bool real = t < it.ni;
     const double rho = tot * d.pot.am;
@@ -450,24 +518,47 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     const bool oreal = owner && (int)threadIdx.x < it.ni;
     const int io = it.i0 + threadIdx.x;
     const Run* __restrict__ run = d.run;
-    float zz[3] = {0.f, 0.f, 0.f};
-    int64_t step = 0;
     const bool integrate = mode == 2;
-    pdl_wait();  // posg comes from the density pass; x, v and the step counter from earlier kernels
-    // Fetch what the epilogue needs, and draw the thermostat noise (a function of seed,
-    // cluster, atom and step only), before the pair loop so that their latency is hidden.
-    if (integrate && oreal && !last && PREC == 1 && run->kind == 1) {
-        step = *d.step_base + k_local;
-        normals_f32(run->seed, (uint32_t)it.cl, step + 1, (uint32_t)(io - it.j0), zz);
+    pdl_wait();  // posg comes from the density pass; x, v and the noise from earlier kernels
+    // Everything the epilogue reads is fetched (and pinned in registers) before the pair loop.
+    double vx0 = 0, vy0 = 0, vz0 = 0, xx0 = 0, yy0 = 0, zz0 = 0, hs = 0, m = 0, ox = 0, oy = 0, oz = 0;
+    float4 nz = make_float4(0.f, 0.f, 0.f, 0.f);
+    float sf = 0.f;
+    double r_h = 0, r_dt = 0, r_c1 = 0;
+    long long step = 0;
+    int r_kind = 0;
+    if (integrate) {  // every lane of the owners' warps must agree on the thermostat branch
+        r_h = run->h;
+        r_dt = run->dt;
+        r_c1 = run->c1;
+        r_kind = run->kind;
+        step = *d.step_base + k_local;  // this pass completes step -> step + 1
     }
-    double vx0 = 0, vy0 = 0, vz0 = 0, hs = 0, m = 0;
     if (integrate && oreal) {
         const int np = d.npad;
         vx0 = d.v[io];
         vy0 = d.v[np + io];
         vz0 = d.v[2 * np + io];
+        xx0 = d.x[io];
+        yy0 = d.x[np + io];
+        zz0 = d.x[2 * np + io];
         hs = d.hs[io];
         m = d.mass[io];
+        if (PREC == 1) {
+            ox = d.origin[3 * it.cl];
+            oy = d.origin[3 * it.cl + 1];
+            oz = d.origin[3 * it.cl + 2];
+            if (!last && r_kind == 1) {
+                nz = d.noise[(size_t)(k_local + 1) * np + io];  // normals of step base + k_local + 1
+                const double T = fmax(fma(run->dT, (double)(step + 1 - run->step0), run->T0), 0.0);
+                sf = d.sig0[io] * sqrtf((float)T);
+            }
+        }
+    }
+    if (integrate) {
+        pin(vx0); pin(vy0); pin(vz0); pin(xx0); pin(yy0); pin(zz0); pin(hs); pin(m);
+        pin(ox); pin(oy); pin(oz); pin(nz.x); pin(nz.y); pin(nz.z); pin(sf);
+        pin(r_h); pin(r_dt); pin(r_c1); pin(step);
     }
 
     R xi[IPT], yi[IPT], zi[IPT], gi[IPT];
@@ -616,27 +707,16 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
         obs_velocity_partials(d, group, real, mm, x, y, z, vx, vy, vz, lane);
         obs_position_partials(d, group, real, mm, x, y, z, lane);
     } else if (mode == 2) {
-        const Run r = *run;
-        step = *d.step_base + k_local;  // this pass completes step -> step + 1
-        double vx = 0.0, vy = 0.0, vz = 0.0;
-        if (real) {
-            vx = fma(hs, (double)Fx, vx0);
-            vy = fma(hs, (double)Fy, vy0);
-            vz = fma(hs, (double)Fz, vz0);
-        }
-        double x = 0.0, y = 0.0, z = 0.0;
-        if (real) {
-            x = d.x[i];
-            y = d.x[np + i];
-            z = d.x[2 * np + i];
-        }
+        const double Fxd = (double)Fx, Fyd = (double)Fy, Fzd = (double)Fz;
+        // velocities at the end of this step (second half kick)
+        const double vx = fma(hs, Fxd, vx0), vy = fma(hs, Fyd, vy0), vz = fma(hs, Fzd, vz0);
         if (ENERGY) {  // observables are due at step + 1 (the host compiles ENERGY in only then)
             const double e = warp_sum(real ? Ep : 0.0);
             if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
-            obs_position_partials(d, group, real, m, x, y, z, lane);
-            if (r.kind != 2) obs_velocity_partials(d, group, real, m, x, y, z, vx, vy, vz, lane);
+            obs_position_partials(d, group, real, m, xx0, yy0, zz0, lane);
+            if (r_kind != 2) obs_velocity_partials(d, group, real, m, xx0, yy0, zz0, vx, vy, vz, lane);
         }
-        if (r.kind == 2) {
+        if (r_kind == 2) {
             if (real) {
                 d.v[i] = vx;
                 d.v[np + i] = vy;
@@ -650,45 +730,53 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
                 d.v[np + i] = vy;
                 d.v[2 * np + i] = vz;
             } else {
-                // start of the next step: B (A O A | A A), new mirror
-                const int64_t s1 = step + 1;
-                vx = fma(hs, (double)Fx, vx);
-                vy = fma(hs, (double)Fy, vy);
-                vz = fma(hs, (double)Fz, vz);
-                if (r.kind == 1) {
-                    x = fma(r.h, vx, x);
-                    y = fma(r.h, vy, y);
-                    z = fma(r.h, vz, z);
+                // next step: its first half kick (rounded separately, exactly as at a chunk start
+                // so that trajectories do not depend on where chunks begin), then A O A or A A
+                double ux = fma(hs, Fxd, vx), uy = fma(hs, Fyd, vy), uz = fma(hs, Fzd, vz);
+                double x, y, z;
+                if (r_kind == 1) {
+                    const double x1 = fma(r_h, ux, xx0), y1 = fma(r_h, uy, yy0), z1 = fma(r_h, uz, zz0);
                     if (PREC == 1) {
-                        const float sf = d.sig0[i] * sqrtf((float)fmax(ramp_T(r, s1), 0.0));
-                        vx = fma(r.c1, vx, (double)(sf * zz[0]));
-                        vy = fma(r.c1, vy, (double)(sf * zz[1]));
-                        vz = fma(r.c1, vz, (double)(sf * zz[2]));
+                        ux = fma(r_c1, ux, (double)(sf * nz.x));
+                        uy = fma(r_c1, uy, (double)(sf * nz.y));
+                        uz = fma(r_c1, uz, (double)(sf * nz.z));
                     } else {
+                        const Run r = *run;
                         double z64[3];
-                        normals_f64(r.seed, (uint32_t)it.cl, s1, (uint32_t)(i - it.j0), z64);
-                        const double sig = sqrt(r.noise_k * fmax(ramp_T(r, s1), 0.0) / m);
-                        vx = fma(r.c1, vx, sig * z64[0]);
-                        vy = fma(r.c1, vy, sig * z64[1]);
-                        vz = fma(r.c1, vz, sig * z64[2]);
+                        normals_f64(r.seed, (uint32_t)it.cl, step + 1, (uint32_t)(i - it.j0), z64);
+                        const double T = fmax(ramp_T(r, step + 1), 0.0);
+                        const double sig = sqrt(r.noise_k * T / m);
+                        ux = fma(r_c1, ux, sig * z64[0]);
+                        uy = fma(r_c1, uy, sig * z64[1]);
+                        uz = fma(r_c1, uz, sig * z64[2]);
                     }
-                    x = fma(r.h, vx, x);
-                    y = fma(r.h, vy, y);
-                    z = fma(r.h, vz, z);
+                    x = fma(r_h, ux, x1);
+                    y = fma(r_h, uy, y1);
+                    z = fma(r_h, uz, z1);
                 } else {
-                    x = fma(r.dt, vx, x);
-                    y = fma(r.dt, vy, y);
-                    z = fma(r.dt, vz, z);
+                    x = fma(r_dt, ux, xx0);
+                    y = fma(r_dt, uy, yy0);
+                    z = fma(r_dt, uz, zz0);
                 }
-                d.v[i] = vx;
-                d.v[np + i] = vy;
-                d.v[2 * np + i] = vz;
+                if (PREC == 1) {
+                    float4 p;
+                    p.x = (float)(x - ox);
+                    p.y = (float)(y - oy);
+                    p.z = (float)(z - oz);
+                    p.w = 0.f;
+                    reinterpret_cast<float4*>(d.mirror)[i] = p;
+                } else {
+                    store_mirror<PREC>(d, i, it.cl, x, y, z);
+                }
+                d.v[i] = ux;
+                d.v[np + i] = uy;
+                d.v[2 * np + i] = uz;
                 d.x[i] = x;
                 d.x[np + i] = y;
                 d.x[2 * np + i] = z;
-                if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+                if (!(finite_bits(x) && finite_bits(y) && finite_bits(z) && finite_bits(ux) && finite_bits(uy) &&
+                      finite_bits(uz)))
                     atomicOr(d.status, 1);
-                store_mirror<PREC>(d, i, it.cl, x, y, z);
             }
         }
     }
@@ -706,7 +794,7 @@ template <int PREC> __global__ void k_start(const Dev d, int k_local) {
     const Run r = *d.run;
     double fx, fy, fz;
     load_force<PREC>(d, i, fx, fy, fz);
-    begin_step<PREC>(d, r, i, cl, a, *d.step_base + k_local, fx, fy, fz);
+    begin_step<PREC>(d, r, i, cl, a, *d.step_base + k_local, fx, fy, fz, k_local);
 }
 
 template <int PREC> __global__ void k_berendsen(const Dev d, int k_local, int last) {
@@ -745,7 +833,7 @@ template <int PREC> __global__ void k_berendsen(const Dev d, int k_local, int la
     if (!last && real) {
         double fx, fy, fz;
         load_force<PREC>(d, i, fx, fy, fz);
-        begin_step<PREC>(d, r, i, cl, a, next, fx, fy, fz);
+        begin_step<PREC>(d, r, i, cl, a, next, fx, fy, fz, -1);
     }
 }
 
@@ -836,6 +924,26 @@ __global__ void k_advance(const Dev d, int n) {
     pdl_launch_dependents();
     pdl_wait();
     *d.step_base += n;
+}
+
+// Langevin normals of steps base .. base + M - 1 for every atom, ahead of the chunk
+// (MIXED): noise[m][i] = the three FP32 Box-Muller normals of step base + m.
+__global__ void k_noise(const Dev d, int M) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)M * d.npad) return;
+    const int m = (int)(idx / d.npad), i = (int)(idx - (long long)m * d.npad);
+    const int cl = d.cl_of_group[i >> 5];
+    const int a = i - d.poff[cl];
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a < d.nreal[cl]) {
+        const Run& r = *d.run;
+        float zz[3];
+        normals_f32(r.seed, (uint32_t)cl, *d.step_base + m, (uint32_t)a, zz);
+        out = make_float4(zz[0], zz[1], zz[2], 0.f);
+    }
+    d.noise[idx] = out;
 }
 
 // Per-atom factors of the current md_step call: h conv / m and sqrt((1 - c1^2) k_B conv / m).
@@ -987,6 +1095,10 @@ cudaError_t launch_mirror(const Dev& d, cudaStream_t s) {
 }
 cudaError_t launch_origin(const Dev& d, cudaStream_t s) {
     return launch_ex(k_origin, d.B, 32, 0, 0, s, d);
+}
+cudaError_t launch_noise(const Dev& d, int M, cudaStream_t s) {
+    const long long n = (long long)M * d.npad;
+    return launch_ex(k_noise, (int)((n + 255) / 256), 256, 0, 0, s, d, M);
 }
 cudaError_t launch_prepare(const Dev& d, cudaStream_t s) {
     return launch_ex(k_prepare, (d.npad + 255) / 256, 256, 0, 0, s, d);
