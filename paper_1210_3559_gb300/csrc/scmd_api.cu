@@ -702,6 +702,7 @@ md_status md_step(md_ctx* c, int64_t nsteps, double dt, const md_thermostat* th)
     r.dt = dt;
     r.h = 0.5 * dt;
     r.c1 = t.kind == MD_LANGEVIN ? std::exp(-t.gamma_per_ps * 1e-3 * dt) : 1.0;
+    r.hk = r.h * (1.0 + r.c1);
     r.noise_k = t.kind == MD_LANGEVIN ? (1.0 - r.c1 * r.c1) * kKB * kConv : 0.0;
     r.T0 = t.T0_K;
     r.T1 = t.T1_K;
@@ -888,8 +889,8 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     if (!c || reps < 1) return MD_ERR_INVALID;
     const Dev& d = c->dev;
     const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[4] = {1, 2, 4, 8};
-    Shape best[2] = {c->shape[0], c->shape[1]};
-    float best_t[2] = {1e30f, 1e30f};
+    // Phase 1: every shape of each pass timed alone (CUDA events over reps launches).
+    std::vector<std::pair<float, Shape>> timed[2];
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
@@ -907,11 +908,7 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
                                           : launch_force(d, it, n, s, 0, 0, 0, c->stream);
                     };
                     // feasibility: the cluster shape must be schedulable
-                    if (run() != cudaSuccess) {
-                        cudaGetLastError();
-                        continue;
-                    }
-                    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                    if (run() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
                         cudaGetLastError();
                         continue;
                     }
@@ -922,19 +919,76 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
                     CK(c, cudaEventSynchronize(e1));
                     float ms = 0;
                     cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best_t[which]) {
-                        best_t[which] = ms;
-                        best[which] = s;
-                    }
+                    timed[which].push_back({ms, s});
                 }
+    for (int which = 0; which < 2; ++which) {
+        if (timed[which].empty()) return fail(c, MD_ERR_CUDA, "autotune: no launch shape could run");
+        std::sort(timed[which].begin(), timed[which].end(),
+                  [](const std::pair<float, Shape>& a, const std::pair<float, Shape>& b) { return a.first < b.first; });
+    }
+    // Phase 2: the fastest shapes of each pass combined and timed where they run, inside the
+    // captured MD step graph (kernels of consecutive passes overlap through programmatic
+    // dependent launch, which depends on both shapes). The state is saved and restored.
+    const size_t nb = sizeof(double) * 3 * c->npad;
+    const size_t fb = (size_t)elem_size(c) * 3 * c->npad;
+    void *sx = nullptr, *sv = nullptr, *sf = nullptr;
+    CK(c, cudaMalloc(&sx, nb));
+    CK(c, cudaMalloc(&sv, nb));
+    CK(c, cudaMalloc(&sf, fb));
+    CK(c, cudaMemcpyAsync(sx, c->d_x, nb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(sv, c->d_v, nb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(sf, c->d_f, fb, cudaMemcpyDeviceToDevice, c->stream));
+    const int64_t step_saved = c->step;
+    const double time_saved = c->time_fs;
+    const int obs_saved = c->cfg.obs_every;
+    const auto samples_saved = c->samples;
+    c->cfg.obs_every = 0;
+    const int K = 6, M = 16;
+    Shape best[2] = {timed[0][0].second, timed[1][0].second};
+    float best_t = 1e30f;
+    md_status st = MD_OK;
+    md_thermostat nve{};
+    nve.kind = MD_NVE;
+    for (int a = 0; a < std::min<int>(K, (int)timed[0].size()) && st == MD_OK; ++a)
+        for (int b = 0; b < std::min<int>(K, (int)timed[1].size()) && st == MD_OK; ++b) {
+            c->shape[0] = timed[0][a].second;
+            c->shape[1] = timed[1][b].second;
+            drop_graphs(c);
+            st = md_step(c, M, 0.5, &nve);  // capture + warm-up
+            if (st != MD_OK) break;
+            cudaEventRecord(e0, c->stream);
+            for (int k = 0; k < 3 && st == MD_OK; ++k) st = md_step(c, M, 0.5, &nve);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = MD_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == MD_OK && ms < best_t) {
+                best_t = ms;
+                best[0] = c->shape[0];
+                best[1] = c->shape[1];
+            }
+        }
+    c->cfg.obs_every = obs_saved;
+    c->step = step_saved;
+    c->time_fs = time_saved;
+    c->samples = samples_saved;
+    CK(c, cudaMemcpyAsync(c->d_x, sx, nb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->d_v, sv, nb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->d_f, sf, fb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    cudaFree(sx);
+    cudaFree(sv);
+    cudaFree(sf);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st != MD_OK) return st;
     c->shape[0] = best[0];
     c->shape[1] = best[1];
     drop_graphs(c);
     cache_store(c->cfg.tune_cache, tune_key(c), c->shape);
-    // the forces must again belong to the current state
-    md_status st = evaluate(c, false);
+    // forces, densities and mirror of the restored state under the chosen shapes
+    st = evaluate(c, false);
     if (st != MD_OK) return st;
     CK(c, cudaStreamSynchronize(c->stream));
     return MD_OK;

@@ -64,6 +64,7 @@ struct Pot {
 // Integrator / thermostat parameters of the current md_step call (device resident).
 struct Run {
     double dt, h;            // step, half step (fs)
+    double hk;               // h (1 + c1): the BAOAB position update as one multiply-add
     double c1;               // Langevin exp(-gamma dt)
     double noise_k;          // (1 - c1^2) k_B * conv  (sigma_i^2 = noise_k * T / m_i)
     double T0, T1;           // ramp end points
@@ -99,7 +100,7 @@ struct Dev {
     double* origin;      // [B][3] MIXED mirror origin; FP64: unused
     const double* hs;    // [npad] half-step kick factor h * conv / m (per md_step call)
     const float* sig0;   // [npad] sqrt((1 - c1^2) k_B conv / m) (Langevin, per md_step call)
-    float4* noise;       // [noise_steps][npad] Langevin normals of the running chunk (MIXED)
+    float4* noise;       // [noise_steps][npad] Langevin normals of the running chunk times sqrt(T(step)) (MIXED)
     double* part;        // [ngroups][kObsFields]
     double* ke_grp;      // [ngroups] sum m v^2 (Berendsen)
     double* hist;        // ring [cap][B][kHistFields]

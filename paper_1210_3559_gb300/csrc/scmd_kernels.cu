@@ -140,6 +140,11 @@ __device__ __forceinline__ void normals_f64(uint64_t seed, uint32_t cl, int64_t 
 }
 
 // ------------------------------------------------------------------ helpers
+// Exponent-field test on the integer pipe (IEEE double finite iff exponent != all ones).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
 __device__ __forceinline__ double ramp_T(const Run& r, int64_t step) {
     return r.T0 + r.dT * (double)(step - r.step0);
 }
@@ -172,56 +177,59 @@ template <int PREC> __device__ __forceinline__ void load_force(const Dev& d, int
 
 // Start of a step for one atom from (x, v, F): B, then A O A (Langevin) or A A (NVE, Berendsen).
 // Per-atom factors h conv / m and the Langevin noise scale come precomputed (k_prepare), so the
-// FP64 work here is multiply-adds only.
+// FP64 work here is multiply-adds only. With u the velocity after B and n the O-step noise, BAOAB
+// gives v' = c1 u + n and x' = x + h u + h v' = x + h n + h (1 + c1) u, evaluated in that form
+// (shared with the force-pass epilogue, so that a step starting a chunk rounds like any other).
 template <int PREC>
 __device__ __forceinline__ void begin_step(const Dev& d, const Run& r, int i, int cl, int atom, int64_t step,
                                            double fx, double fy, double fz, int noise_slot) {
     const int np = d.npad;
     const double hs = d.hs[i];
-    double vx = fma(hs, fx, d.v[i]), vy = fma(hs, fy, d.v[np + i]), vz = fma(hs, fz, d.v[2 * np + i]);
-    double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
+    double ux = fma(hs, fx, d.v[i]), uy = fma(hs, fy, d.v[np + i]), uz = fma(hs, fz, d.v[2 * np + i]);
+    const double x0 = d.x[i], y0 = d.x[np + i], z0 = d.x[2 * np + i];
+    double x, y, z;
     if (r.kind == 1) {
-        x = fma(r.h, vx, x);
-        y = fma(r.h, vy, y);
-        z = fma(r.h, vz, z);
-        const double T = fmax(ramp_T(r, step), 0.0);
+        double nx, ny, nz;
         if (PREC == 1) {
-            float zz[3];
+            float4 zz;
             if (noise_slot >= 0) {
-                const float4 nz = d.noise[(size_t)noise_slot * np + i];
-                zz[0] = nz.x;
-                zz[1] = nz.y;
-                zz[2] = nz.z;
+                zz = d.noise[(size_t)noise_slot * np + i];  // already times sqrt(T(step))
             } else {
-                normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
+                float w[3];
+                normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)atom, w);
+                const float sT = sqrtf((float)fmax(ramp_T(r, step), 0.0));
+                zz = make_float4(w[0] * sT, w[1] * sT, w[2] * sT, 0.f);
             }
-            const float sf = d.sig0[i] * sqrtf((float)T);
-            vx = fma(r.c1, vx, (double)(sf * zz[0]));
-            vy = fma(r.c1, vy, (double)(sf * zz[1]));
-            vz = fma(r.c1, vz, (double)(sf * zz[2]));
+            const float sg = d.sig0[i];
+            nx = (double)(sg * zz.x);
+            ny = (double)(sg * zz.y);
+            nz = (double)(sg * zz.z);
         } else {
-            double zz[3];
-            normals_f64(r.seed, (uint32_t)cl, step, (uint32_t)atom, zz);
-            const double sig = sqrt(r.noise_k * T / d.mass[i]);
-            vx = fma(r.c1, vx, sig * zz[0]);
-            vy = fma(r.c1, vy, sig * zz[1]);
-            vz = fma(r.c1, vz, sig * zz[2]);
+            double w[3];
+            normals_f64(r.seed, (uint32_t)cl, step, (uint32_t)atom, w);
+            const double sig = sqrt(r.noise_k * fmax(ramp_T(r, step), 0.0) / d.mass[i]);
+            nx = sig * w[0];
+            ny = sig * w[1];
+            nz = sig * w[2];
         }
-        x = fma(r.h, vx, x);
-        y = fma(r.h, vy, y);
-        z = fma(r.h, vz, z);
+        x = fma(r.hk, ux, fma(r.h, nx, x0));
+        y = fma(r.hk, uy, fma(r.h, ny, y0));
+        z = fma(r.hk, uz, fma(r.h, nz, z0));
+        ux = fma(r.c1, ux, nx);
+        uy = fma(r.c1, uy, ny);
+        uz = fma(r.c1, uz, nz);
     } else {
-        x = fma(r.dt, vx, x);
-        y = fma(r.dt, vy, y);
-        z = fma(r.dt, vz, z);
+        x = fma(r.dt, ux, x0);
+        y = fma(r.dt, uy, y0);
+        z = fma(r.dt, uz, z0);
     }
-    d.v[i] = vx;
-    d.v[np + i] = vy;
-    d.v[2 * np + i] = vz;
+    d.v[i] = ux;
+    d.v[np + i] = uy;
+    d.v[2 * np + i] = uz;
     d.x[i] = x;
     d.x[np + i] = y;
     d.x[2 * np + i] = z;
-    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+    if (!(finite_bits(x) && finite_bits(y) && finite_bits(z) && finite_bits(ux) && finite_bits(uy) && finite_bits(uz)))
         atomicOr(d.status, 1);
     store_mirror<PREC>(d, i, cl, x, y, z);
 }
@@ -298,10 +306,26 @@ __device__ __forceinline__ f2sum f2_add(f2sum a, f2sum b) {
 __device__ __forceinline__ void pin(double v) { asm volatile("" ::"d"(v)); }
 __device__ __forceinline__ void pin(float v) { asm volatile("" ::"f"(v)); }
 __device__ __forceinline__ void pin(long long v) { asm volatile("" ::"l"(v)); }
-// Exponent-field test on the integer pipe (IEEE double finite iff exponent != all ones).
-__device__ __forceinline__ bool finite_bits(double v) {
-    return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+
+// Asynchronous global -> shared copies (cp.async) for the force epilogue's inputs.
+struct __align__(16) EpiSlot {
+    float4 nz;       // Langevin noise of the next step (times sqrt(T))
+    double v[3], x[3], hs, m, o[3];
+    float sig0;
+    float pad[3];
+};
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ------------------------------------------------------------- pass helpers
 // Programmatic dependent launch: let the next kernel in the stream be scheduled
@@ -520,45 +544,30 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     const Run* __restrict__ run = d.run;
     const bool integrate = mode == 2;
     pdl_wait();  // posg comes from the density pass; x, v and the noise from earlier kernels
-    // Everything the epilogue reads is fetched (and pinned in registers) before the pair loop.
-    double vx0 = 0, vy0 = 0, vz0 = 0, xx0 = 0, yy0 = 0, zz0 = 0, hs = 0, m = 0, ox = 0, oy = 0, oz = 0;
-    float4 nz = make_float4(0.f, 0.f, 0.f, 0.f);
-    float sf = 0.f;
-    double r_h = 0, r_dt = 0, r_c1 = 0;
-    long long step = 0;
-    int r_kind = 0;
-    if (integrate) {  // every lane of the owners' warps must agree on the thermostat branch
-        r_h = run->h;
-        r_dt = run->dt;
-        r_c1 = run->c1;
-        r_kind = run->kind;
-        step = *d.step_base + k_local;  // this pass completes step -> step + 1
-    }
+    // The epilogue's inputs are copied into this owner's shared-memory slot with cp.async
+    // before the pair loop (no register, no stall) and waited for only after it.
+    const uintptr_t slot0 = (reinterpret_cast<uintptr_t>(inboxf + C * BI * 3) + 15) & ~uintptr_t(15);
+    EpiSlot* slot = reinterpret_cast<EpiSlot*>(slot0) + (owner ? threadIdx.x : 0);
     if (integrate && oreal) {
         const int np = d.npad;
-        vx0 = d.v[io];
-        vy0 = d.v[np + io];
-        vz0 = d.v[2 * np + io];
-        xx0 = d.x[io];
-        yy0 = d.x[np + io];
-        zz0 = d.x[2 * np + io];
-        hs = d.hs[io];
-        m = d.mass[io];
+        cp_async8(&slot->v[0], d.v + io);
+        cp_async8(&slot->v[1], d.v + np + io);
+        cp_async8(&slot->v[2], d.v + 2 * np + io);
+        cp_async8(&slot->x[0], d.x + io);
+        cp_async8(&slot->x[1], d.x + np + io);
+        cp_async8(&slot->x[2], d.x + 2 * np + io);
+        cp_async8(&slot->hs, d.hs + io);
+        cp_async8(&slot->m, d.mass + io);
         if (PREC == 1) {
-            ox = d.origin[3 * it.cl];
-            oy = d.origin[3 * it.cl + 1];
-            oz = d.origin[3 * it.cl + 2];
-            if (!last && r_kind == 1) {
-                nz = d.noise[(size_t)(k_local + 1) * np + io];  // normals of step base + k_local + 1
-                const double T = fmax(fma(run->dT, (double)(step + 1 - run->step0), run->T0), 0.0);
-                sf = d.sig0[io] * sqrtf((float)T);
+            cp_async8(&slot->o[0], d.origin + 3 * it.cl);
+            cp_async8(&slot->o[1], d.origin + 3 * it.cl + 1);
+            cp_async8(&slot->o[2], d.origin + 3 * it.cl + 2);
+            if (!last) {
+                cp_async16(&slot->nz, d.noise + (size_t)(k_local + 1) * np + io);  // step base + k_local + 1
+                cp_async4(&slot->sig0, d.sig0 + io);
             }
         }
-    }
-    if (integrate) {
-        pin(vx0); pin(vy0); pin(vz0); pin(xx0); pin(yy0); pin(zz0); pin(hs); pin(m);
-        pin(ox); pin(oy); pin(oz); pin(nz.x); pin(nz.y); pin(nz.z); pin(sf);
-        pin(r_h); pin(r_dt); pin(r_c1); pin(step);
+        cp_async_commit();
     }
 
     R xi[IPT], yi[IPT], zi[IPT], gi[IPT];
@@ -707,6 +716,12 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
         obs_velocity_partials(d, group, real, mm, x, y, z, vx, vy, vz, lane);
         obs_position_partials(d, group, real, mm, x, y, z, lane);
     } else if (mode == 2) {
+        const Run* rr = run;
+        const int r_kind = rr->kind;
+        cp_async_wait_all();
+        const double vx0 = slot->v[0], vy0 = slot->v[1], vz0 = slot->v[2];
+        const double xx0 = slot->x[0], yy0 = slot->x[1], zz0 = slot->x[2];
+        const double hs = slot->hs, m = real ? slot->m : 0.0;
         const double Fxd = (double)Fx, Fyd = (double)Fy, Fzd = (double)Fz;
         // velocities at the end of this step (second half kick)
         const double vx = fma(hs, Fxd, vx0), vy = fma(hs, Fyd, vy0), vz = fma(hs, Fzd, vz0);
@@ -730,39 +745,45 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
                 d.v[np + i] = vy;
                 d.v[2 * np + i] = vz;
             } else {
-                // next step: its first half kick (rounded separately, exactly as at a chunk start
-                // so that trajectories do not depend on where chunks begin), then A O A or A A
+                // next step (same arithmetic as begin_step): first half kick, then A O A or A A
                 double ux = fma(hs, Fxd, vx), uy = fma(hs, Fyd, vy), uz = fma(hs, Fzd, vz);
                 double x, y, z;
                 if (r_kind == 1) {
-                    const double x1 = fma(r_h, ux, xx0), y1 = fma(r_h, uy, yy0), z1 = fma(r_h, uz, zz0);
+                    const double h = rr->h, hk = rr->hk, c1 = rr->c1;
+                    double nx, ny, nz;
                     if (PREC == 1) {
-                        ux = fma(r_c1, ux, (double)(sf * nz.x));
-                        uy = fma(r_c1, uy, (double)(sf * nz.y));
-                        uz = fma(r_c1, uz, (double)(sf * nz.z));
+                        const float sg = slot->sig0;
+                        const float4 w = slot->nz;
+                        nx = (double)(sg * w.x);
+                        ny = (double)(sg * w.y);
+                        nz = (double)(sg * w.z);
                     } else {
-                        const Run r = *run;
-                        double z64[3];
-                        normals_f64(r.seed, (uint32_t)it.cl, step + 1, (uint32_t)(i - it.j0), z64);
-                        const double T = fmax(ramp_T(r, step + 1), 0.0);
-                        const double sig = sqrt(r.noise_k * T / m);
-                        ux = fma(r_c1, ux, sig * z64[0]);
-                        uy = fma(r_c1, uy, sig * z64[1]);
-                        uz = fma(r_c1, uz, sig * z64[2]);
+                        const Run r = *rr;
+                        const int64_t s1 = *d.step_base + k_local + 1;
+                        double w[3];
+                        normals_f64(r.seed, (uint32_t)it.cl, s1, (uint32_t)(i - it.j0), w);
+                        const double sig = sqrt(r.noise_k * fmax(ramp_T(r, s1), 0.0) / m);
+                        nx = sig * w[0];
+                        ny = sig * w[1];
+                        nz = sig * w[2];
                     }
-                    x = fma(r_h, ux, x1);
-                    y = fma(r_h, uy, y1);
-                    z = fma(r_h, uz, z1);
+                    x = fma(hk, ux, fma(h, nx, xx0));
+                    y = fma(hk, uy, fma(h, ny, yy0));
+                    z = fma(hk, uz, fma(h, nz, zz0));
+                    ux = fma(c1, ux, nx);
+                    uy = fma(c1, uy, ny);
+                    uz = fma(c1, uz, nz);
                 } else {
-                    x = fma(r_dt, ux, xx0);
-                    y = fma(r_dt, uy, yy0);
-                    z = fma(r_dt, uz, zz0);
+                    const double dt = rr->dt;
+                    x = fma(dt, ux, xx0);
+                    y = fma(dt, uy, yy0);
+                    z = fma(dt, uz, zz0);
                 }
                 if (PREC == 1) {
                     float4 p;
-                    p.x = (float)(x - ox);
-                    p.y = (float)(y - oy);
-                    p.z = (float)(z - oz);
+                    p.x = (float)(x - slot->o[0]);
+                    p.y = (float)(y - slot->o[1]);
+                    p.z = (float)(z - slot->o[2]);
                     p.w = 0.f;
                     reinterpret_cast<float4*>(d.mirror)[i] = p;
                 } else {
@@ -927,7 +948,8 @@ __global__ void k_advance(const Dev d, int n) {
 }
 
 // Langevin normals of steps base .. base + M - 1 for every atom, ahead of the chunk
-// (MIXED): noise[m][i] = the three FP32 Box-Muller normals of step base + m.
+// (MIXED): noise[m][i] = the three FP32 Box-Muller normals of step base + m, times
+// sqrt(T) of that step's target temperature (the per-atom factor sig0 is applied later).
 __global__ void k_noise(const Dev d, int M) {
     pdl_launch_dependents();
     pdl_wait();
@@ -940,8 +962,10 @@ __global__ void k_noise(const Dev d, int M) {
     if (a < d.nreal[cl]) {
         const Run& r = *d.run;
         float zz[3];
-        normals_f32(r.seed, (uint32_t)cl, *d.step_base + m, (uint32_t)a, zz);
-        out = make_float4(zz[0], zz[1], zz[2], 0.f);
+        const int64_t step = *d.step_base + m;
+        normals_f32(r.seed, (uint32_t)cl, step, (uint32_t)a, zz);
+        const float sT = sqrtf((float)fmax(ramp_T(r, step), 0.0));
+        out = make_float4(zz[0] * sT, zz[1] * sT, zz[2] * sT, 0.f);
     }
     d.noise[idx] = out;
 }
@@ -988,7 +1012,9 @@ size_t pass_smem_bytes(int prec, Shape sh) {
     const size_t tiles = W * 32 * v4;
     const size_t dens = (W + C) * BI * sizeof(double);
     const size_t force = (W + C) * BI * sizeof(double) + (W + C) * BI * 3 * r;
-    return tiles + (dens > force ? dens : force);
+    // force pass: the epilogue slots follow the reduction buffers, 16-byte aligned
+    const size_t force_slots = ((tiles + force + 15) / 16) * 16 - tiles + BI * sizeof(EpiSlot);
+    return tiles + (dens > force_slots ? dens : force_slots);
 }
 
 // Every kernel is launched with programmatic stream serialization (it waits on its
