@@ -249,6 +249,31 @@ md_status md_philox4x32_10(const uint32_t* in, uint32_t* out, int32_t count);
 md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int32_t n_atoms,
                               int32_t precision, double* out);
 
+/*
+ * Energy and forces of one cluster with no device allocation. The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory, such
+ * as a host framework whose own allocator owns all of the GPU's memory, or a
+ * time-critical loop that must never enter the CUDA allocator.
+ *   pos_dev[n_atoms][3]     positions (Angstrom), device memory, read only
+ *   forces_dev[n_atoms][3]  forces (eV/A), device memory, written
+ *   epot_dev[1]             potential energy of Eq. 1 (eV), device memory, written
+ *   stream                  cudaStream_t on which the work is queued (0 = default stream)
+ * The caller owns all three buffers. The arithmetic is that of md_energy_forces
+ * in MIXED precision (FP32 pair terms, FP64 rho and energy), all pairs, or the
+ * strict cutoff when params->rcut_A > 0. The call queues its kernels and returns;
+ * synchronise the stream before reading the outputs. Working data lives in one
+ * fixed array compiled into the library (kept by every GPU that loads it until the
+ * process exits), so n_atoms is limited to 1..16384: anything else returns
+ * MD_ERR_INVALID with a message in md_last_error(NULL), as does a bad argument.
+ * Every call on a device shares that array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. The first call on each device looks up the
+ * array's device address (with that device current); make that first call before
+ * starting any stream capture.
+ */
+md_status md_energy_forces_noalloc(const double* pos_dev, int32_t n_atoms, const md_sc_params* params,
+                                   double* forces_dev, double* epot_dev, uint64_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,8 @@ struct GraphKey {
 
 }  // namespace
 
+void scmd::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 struct md_ctx {
     md_config cfg{};
     Pot pot{};

@@ -135,6 +135,8 @@ cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t
 cudaError_t launch_normals(uint64_t seed, uint32_t cluster, int64_t step, int n, int prec, double* out,
                            cudaStream_t s);
 size_t pass_smem_bytes(int prec, Shape sh);
+// The calling thread's error message returned by md_last_error(NULL) (defined in scmd_api.cu).
+void set_thread_error(const char* msg);
 cudaError_t configure_kernels();
 
 }  // namespace scmd

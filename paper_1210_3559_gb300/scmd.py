@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
                 "md_destroy": ([_VP], None),
                 "md_philox4x32_10": ([P(u32), P(u32), i32], i32),
                 "md_langevin_normals": ([u64, u32, i64, i32, i32, _DP], i32),
+                "md_energy_forces_noalloc": ([_VP, i32, P(md_sc_params), _VP, _VP, u64], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -105,7 +106,8 @@ def exported_symbols():
     return ["md_abi_version", "md_create", "md_energy_forces", "md_get_density", "md_step", "md_observables",
             "md_obs_history", "md_clear_history", "md_get_state", "md_set_state", "md_get_forces", "md_recenter",
             "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts",
-            "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals"]
+            "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals",
+            "md_energy_forces_noalloc"]
 
 
 def md_abi_version() -> int:
@@ -301,3 +303,13 @@ def md_langevin_normals(seed: int, cluster: int, step: int, n_atoms: int, precis
     _check(lib().md_langevin_normals(int(seed), int(cluster), int(step), int(n_atoms), int(precision),
                                      out.ctypes.data_as(_DP)))
     return out
+
+
+def md_energy_forces_noalloc(pos_ptr: int, n_atoms: int, params: md_sc_params | None, forces_ptr: int,
+                             epot_ptr: int, stream: int = 0):
+    """Energy and forces of one cluster from caller-owned device buffers (raw device addresses),
+    for callers that cannot allocate device memory; the library allocates nothing either.
+    Queued on `stream`: synchronise it before reading the outputs."""
+    params = params or sc_params()
+    _check(lib().md_energy_forces_noalloc(int(pos_ptr), int(n_atoms), ctypes.byref(params), int(forces_ptr),
+                                          int(epot_ptr), int(stream)))
