@@ -9,6 +9,9 @@ integration). One timed iteration ("step" of this benchmark) is one md_step call
 default --steps 400 covers the whole 2e5-step cooling schedule. L2 is flushed (a 256 MB
 write) before every timed iteration and that flush is outside the timed events.
 
+Other configs (--config): ni6000, ni20000 (all pairs, MIXED), ni50000 (rcut = 8.8 A on the
+cell list, MIXED), ni147 (FP64 NVE), batched512 (512 clusters of 55..2000 atoms).
+
 value  : atom-timesteps/s over all ranks (sum of atoms x MD steps / max rank time).
 e2e    : the same metric through the C ABI with host buffers every iteration
          (md_set_state from pinned host arrays, md_step, md_get_state back to the host).
@@ -44,6 +47,9 @@ METRIC = "atom-timesteps/s & pair-evals/s vs FP32 peak; mixed vs FP64 at stated 
 UNIT = "atom-timesteps/s"
 FP32_LANES_PER_SM = 128
 FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n,m) = (9,6)
+# DRAM bytes (read + write) of one force-pass launch at the default workload, from the ncu
+# capture summarised in profiles/k_force_ni2000_mixed.md (cold caches; None when stale).
+FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 234496}
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
 
 
@@ -66,6 +72,14 @@ def workload(name: str, rank: int):
         return dict(sizes=[n], pos=pos, vel=vel, mass=m, prec="mixed", dt=2.0, melt_steps=2000, melt_T=2000.0,
                     schedule=(2000.0, 300.0, 200000), gamma=1.0, seed=3 + seed_off,
                     desc=f"Ni~{n} FCC sphere, Langevin cooling 2000->300 K over 2e5 steps dt=2 fs")
+    if name == "ni50000":
+        pos = inputs.fcc_sphere(50000)
+        m = inputs.masses(50000)
+        vel = inputs.maxwell_boltzmann(pos, m, 2000.0, seed=6 + seed_off, dof="3N")
+        return dict(sizes=[50000], pos=pos, vel=vel, mass=m, prec="mixed", dt=2.0, melt_steps=2000, melt_T=2000.0,
+                    schedule=(2000.0, 300.0, 200000), gamma=1.0, seed=6 + seed_off, rcut=8.8,
+                    desc="Ni~50000 FCC sphere, rcut 8.8 A (2.5 a) on the cell list, Langevin cooling "
+                         "2000->300 K over 2e5 steps dt=2 fs")
     if name == "ni147":
         pos = inputs.mackay_icosahedron(3, 2.49)
         m = inputs.masses(147)
@@ -152,7 +166,7 @@ def cpu_baseline(w, budget_s: float):
         sizes = sizes[:8]
     n = sum(sizes)
     pos, vel, mass = w["pos"][:n], w["vel"][:n], w["mass"][:n]
-    b = oracle.Batch(sizes, pos, vel, mass)
+    b = oracle.Batch(sizes, pos, vel, mass, oracle.params(rcut=w.get("rcut", 0.0)))
     th = oracle.thermostat(oracle.LANGEVIN if w["gamma"] > 0 else oracle.NVE,
                            w["melt_T"] or 0.0, None, gamma_ps=w["gamma"] or 1.0, seed=w["seed"])
     t0 = time.perf_counter()
@@ -163,8 +177,12 @@ def cpu_baseline(w, budget_s: float):
     b.run(steps, w["dt"], th)
     el = time.perf_counter() - t0
     return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} MD steps (FP64, all pairs) of {len(sizes)} cluster(s), {n} atoms, "
+            "sample": f"{steps} MD steps (FP64, all pairs{cut_note(w)}) of {len(sizes)} cluster(s), {n} atoms, "
                       f"dt={w['dt']} fs, same thermostat", "s_per_step": el / steps}
+
+
+def cut_note(w):
+    return f", cutoff {w['rcut']} A tested on every pair" if w.get("rcut") else ""
 
 
 def run_reference(args, rank, world):
@@ -175,7 +193,7 @@ def run_reference(args, rank, world):
     cores = oracle.num_threads(os.cpu_count() or 1)
     sizes = list(map(int, w["sizes"]))[:8]
     n = sum(sizes)
-    b = oracle.Batch(sizes, w["pos"][:n], w["vel"][:n], w["mass"][:n])
+    b = oracle.Batch(sizes, w["pos"][:n], w["vel"][:n], w["mass"][:n], oracle.params(rcut=w.get("rcut", 0.0)))
     th = oracle.thermostat(oracle.LANGEVIN if w["gamma"] > 0 else oracle.NVE, w["melt_T"] or 0.0, None,
                            gamma_ps=w["gamma"] or 1.0, seed=w["seed"])
     for _ in range(args.warmup):
@@ -190,7 +208,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w["desc"], "sample_atoms": n, "md_steps_per_step": 1},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step = 1 MD step of {n} atoms (FP64 oracle, all pairs)"},
+                             "sample": f"each step = 1 MD step of {n} atoms (FP64 oracle, all pairs{cut_note(w)})"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -202,7 +220,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="ni2000", choices=["ni2000", "ni6000", "ni20000", "ni147", "batched512"])
+    ap.add_argument("--config", default="ni2000", choices=["ni2000", "ni6000", "ni20000", "ni50000", "ni147", "batched512"])
     ap.add_argument("--md-steps", type=int, default=500, help="MD steps per timed iteration")
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
     ap.add_argument("--no-tune", action="store_true")
@@ -245,7 +263,9 @@ def main():
     pairs_per_eval = float(np.sum(sizes.astype(np.float64) * (sizes - 1)))
     if args.shapes:
         cfg.tune = 0
-    ctx = scmd.md_create(cfg, sizes, w["pos"], w["vel"], w["mass"], scmd.sc_params())
+    rcut = w.get("rcut", 0.0)
+    ctx = scmd.md_create(cfg, sizes, w["pos"], w["vel"], w["mass"], scmd.sc_params(rcut=rcut))
+    cells = scmd.md_launch_counts(ctx)[0] == 5
     if args.shapes:
         v = [int(x) for x in args.shapes.split(",")]
         scmd.md_set_launch(ctx, 0, *v[0:3])
@@ -301,10 +321,12 @@ def main():
         t_max = float(t.item())
     md_steps_total = args.steps * M
     value = natoms * md_steps_total * world / t_max
-    pair_rate = pairs_per_eval * md_steps_total * world / t_max
 
     # pass timings with CUDA events on the library's stream (same state, same launch shapes)
     ms_d, ms_f, pairs = scmd.md_time_passes(ctx, 50)
+    if cells:  # pairs tested by the cell list at the final state (27 neighbour cells per atom)
+        pairs_per_eval = pairs
+    pair_rate = pairs_per_eval * md_steps_total * world / t_max
     peak_clock = (clocks or {}).get("sm_max_mhz", 2070.0)
     peak_ops = 152 * FP32_LANES_PER_SM * peak_clock * 1e6
     achieved = FORCE_OPS_PER_PAIR * pairs / (ms_f * 1e-3)
@@ -320,7 +342,7 @@ def main():
         import oracle
         E, F = scmd.md_energy_forces(ctx)
         n0 = int(sizes[0])
-        _, Fr, _, _ = oracle.energy_forces(pos_f[:n0])
+        _, Fr, _, _ = oracle.energy_forces(pos_f[:n0], oracle.params(rcut=rcut))
         force_err = float(np.linalg.norm(F[:n0] - Fr) / np.linalg.norm(Fr))
 
     # e2e through the C ABI with host buffers: set_state (H2D) + md_step + get_state (D2H)
@@ -349,7 +371,7 @@ def main():
     if not args.skip_fp64 and prec == "mixed":
         cfg64 = scmd.config(precision=scmd.MD_PREC_FP64, graph_chunk=min(M, 512), tune=0 if args.no_tune else 1,
                             stream=stream.cuda_stream)
-        c64 = scmd.md_create(cfg64, sizes, pos_f, vel_f, w["mass"], scmd.sc_params())
+        c64 = scmd.md_create(cfg64, sizes, pos_f, vel_f, w["mass"], scmd.sc_params(rcut=rcut))
         m64 = max(10, M // 10)
         scmd.md_step(c64, m64, dt, therm(0))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -381,14 +403,17 @@ def main():
                        "md_steps_per_step": M, "dt_fs": dt, "precision": prec,
                        "l2": "flushed (256 MB write) before every timed iteration, outside the timed events",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "launch_shapes": {k: list(v) for k, v in shapes.items()},
+                       "launch_shapes": {k: list(v) for k, v in shapes.items()} if not cells else "cell list",
+                       "rcut_A": rcut or None, "path": "cells" if cells else "all pairs",
                        "wall_s_timed_region": t_wall},
             "pair_evals_per_s": pair_rate,
             "fp32_pipe_frac_force_pass": achieved / peak_ops,
             "force_err_vs_oracle": force_err,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops, "traffic": None,
-                         "kernel": "k_force (force pass)", "ms_per_launch": ms_f,
+                         "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
+                         "traffic": FORCE_DRAM_BYTES_PER_LAUNCH.get(args.config) if prec == "mixed" else None,
+                         "kernel": "k_cell_force (force pass, cell list)" if cells else "k_force (force pass)",
+                         "ms_per_launch": ms_f,
                          "density_pass_ms_per_launch": ms_d, "pairs_per_launch": pairs,
                          "peak_basis": f"152 SMs x 128 FP32 lanes x {peak_clock:.0f} MHz (max SM clock)"},
             "e2e": {"value": e2e_value, "unit": UNIT,

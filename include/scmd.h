@@ -65,10 +65,21 @@ typedef enum {
 } md_precision;
 
 typedef enum {
-    MD_PATH_AUTO = 0,     /* all pairs, or the cell list when rcut_A > 0                */
+    MD_PATH_AUTO = 0,     /* cells when rcut_A > 0 and the largest cluster has >= 8192
+                             atoms, else all pairs                                       */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
     MD_PATH_CELLS = 2     /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
 } md_path;
+
+/* The cell path (not in the paper, which sums every pair and leaves cutoffs to
+ * later work, Sec. II) gives each cluster a fixed cubic grid of G^3 cells of side
+ * h >= rcut_A around its centre of mass at creation, with a margin beyond the
+ * cluster's radius; atoms outside the grid are counted in its border cells, which
+ * keeps the result exact. Each step bins the atoms (a cell holds at most 256;
+ * md_create refuses an rcut_A whose cells would exceed that at the fcc density
+ * 4 / a^3, and a step that overflows a cell returns MD_ERR_STATE) and sums each
+ * atom over the 27 cells around its own. Pair terms, masks and the integrator are
+ * those of the all-pairs path with the cutoff, so both agree to rounding order. */
 
 /* Sutton-Chen parameters (Eq. 1, Eq. 2). Paper's Ni set (Sec. II A):
  * eps_eV = 1.5707e-2, a_A = 3.52, c = 39.432, n = 9, m = 6.
@@ -208,7 +219,8 @@ md_status md_set_launch(md_ctx* ctx, int32_t which, int32_t ipt, int32_t warps, 
 
 /*
  * Autotuner: time every launch shape of both passes on the context's own
- * clusters (CUDA events, reps launches each) and keep the fastest. With
+ * clusters (CUDA events, reps launches each) and keep the fastest (the cell
+ * path has a single launch shape: nothing to tune, returns MD_OK). With
  * cfg.tune_cache set, results are stored in (and later read from) that JSON
  * file, keyed by GPU name, SM count, precision, path and workload shape.
  */
@@ -218,13 +230,16 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
  * Mean device time (ms) of one launch of the density pass and of the force
  * pass, timed alone with CUDA events on the context's stream over reps
  * launches after warm-up. Pair-evaluation counts per launch are returned in
- * *pairs (ordered pairs visited per pass). Any output may be NULL.
+ * *pairs (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for
+ * the cell path, every atom times the atoms of its 27 neighbour cells, self
+ * included, as binned at the current positions). Any output may be NULL.
  */
 md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* ms_force,
                          double* pairs);
 
-/* Number of GPU kernels issued per md_step step and per graph replay
- * overhead (launches per chunk), for launch accounting. */
+/* Number of GPU kernels issued per md_step step (all pairs: 2, cells: 5, plus
+ * one Berendsen kernel, two with cells, and the observable kernels of recorded
+ * steps) and per graph replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);
 
 /* Last error message of ctx, or of the calling thread's last failed md_create when ctx is NULL. */

@@ -33,6 +33,11 @@ constexpr double kKB = 8.617333262e-5;
 
 thread_local std::string g_create_error;
 
+// MD_PATH_AUTO with a cutoff takes the cell list once the largest cluster has this many atoms:
+// below it the 27 cells of side >= rcut around an atom hold most of the cluster anyway.
+constexpr int kAutoCellsMinAtoms = 8192;
+constexpr double kPi = 3.14159265358979323846;
+
 struct GraphKey {
     int M, phase, kind, obs_every;
     int dens[3], force[3];
@@ -69,6 +74,14 @@ struct md_ctx {
     void *d_f = nullptr, *d_mirror = nullptr, *d_posg = nullptr;
     int64_t* d_step = nullptr;
     Run* d_run = nullptr;
+    // cell-list path
+    int path = 0;  // 0: all pairs, 1: cells
+    int n_cells = 0;
+    std::vector<CellGrid> grids;
+    CellGrid* d_grid = nullptr;
+    int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr;
+    void *d_cpos = nullptr, *d_cposg = nullptr;
+    double *d_eatom = nullptr, *d_obs_x = nullptr, *d_obs_v = nullptr;
     // pinned staging
     double* h_stage = nullptr;
     size_t h_stage_n = 0;
@@ -147,6 +160,63 @@ void fill_dev(md_ctx* c) {
     d.run = c->d_run;
     d.pot = c->pot;
     d.conv = kConv;
+    d.path = c->path;
+    d.n_cells = c->n_cells;
+    d.grid = c->d_grid;
+    d.cell_cl = c->d_cell_cl;
+    d.cell_count = c->d_cell_count;
+    d.cell_atoms = c->d_cell_atoms;
+    d.cpos = c->d_cpos;
+    d.cposg = c->d_cposg;
+    d.eatom = c->d_eatom;
+    d.obs_x = c->d_obs_x;
+    d.obs_v = c->d_obs_v;
+}
+
+// Cell grid of every cluster (cell-list path). The cube [-E, E)^3 around the origin covers the
+// cluster with a margin: E = max(1.3 R_fcc, 1.1 R_now) + rcut, R_fcc the radius of N atoms at
+// the fcc density 4 / a^3 and R_now the largest distance of an atom from the centre of mass
+// (clamped to 3 R_fcc so that a few far atoms cannot blow up the grid; those sit in border
+// cells). G = floor(2E / rcut) cells per axis (at most 128), side h = 2E / G >= rcut, rounded
+// up to a binary32 value (E is then G h / 2) so that offsets between cell centres are exact in FP32.
+// Returns false when a cell at the fcc density would not fit kCellCap atoms.
+bool make_grids(md_ctx* c, const double* pos, const double* mass) {
+    const double rc = c->pot.rcut, a = c->pot.a;
+    c->grids.resize(c->B);
+    int off = 0;
+    for (int b = 0; b < c->B; ++b) {
+        const int n = c->sizes[b];
+        const double* x = pos + 3 * (size_t)c->off[b];
+        const double* m = mass + c->off[b];
+        double com[3] = {0, 0, 0}, M = 0;
+        for (int k = 0; k < n; ++k) {
+            for (int q = 0; q < 3; ++q) com[q] += m[k] * x[3 * k + q];
+            M += m[k];
+        }
+        for (int q = 0; q < 3; ++q) com[q] /= M;
+        double r2max = 0;
+        for (int k = 0; k < n; ++k) {
+            double r2 = 0;
+            for (int q = 0; q < 3; ++q) r2 += (x[3 * k + q] - com[q]) * (x[3 * k + q] - com[q]);
+            r2max = std::max(r2max, r2);
+        }
+        const double r_fcc = a * std::cbrt(3.0 * n / (16.0 * kPi));
+        const double r_now = std::min(std::sqrt(r2max), 3.0 * r_fcc);
+        const double E = std::max(1.3 * r_fcc, 1.1 * r_now) + rc;
+        const int G = std::max(1, std::min(128, (int)std::floor(2.0 * E / rc)));
+        CellGrid g{};
+        g.G = G;
+        g.off = off;
+        float hf = (float)(2.0 * E / G);
+        if ((double)hf < 2.0 * E / G) hf = std::nextafter(hf, 1e30f);
+        g.h = (double)hf;
+        g.E = 0.5 * G * g.h;
+        if (1.25 * 4.0 * g.h * g.h * g.h / (a * a * a) > kCellCap) return false;
+        c->grids[b] = g;
+        off += G * G * G;
+    }
+    c->n_cells = off;
+    return true;
 }
 
 Shape default_shape(const md_ctx* c, int which) {
@@ -214,8 +284,15 @@ md_status evaluate(md_ctx* c, bool observe) {
     const Item* i0 = items_for(c, c->shape[0], &n0);
     const Item* i1 = items_for(c, c->shape[1], &n1);
     CK(c, launch_mirror(d, c->stream));
-    CK(c, launch_density(d, i0, n0, c->shape[0], observe ? 1 : 0, c->stream));
-    CK(c, launch_force(d, i1, n1, c->shape[1], observe ? 1 : 0, 0, 0, c->stream));
+    if (c->path == 1) {
+        CK(c, launch_cell_build(d, c->stream));
+        CK(c, launch_cell_density(d, observe ? 1 : 0, c->stream));
+        CK(c, launch_cell_force(d, observe ? 1 : 0, 0, 0, c->stream));
+        if (observe) CK(c, launch_cell_obs(d, 1, 1, c->stream));
+    } else {
+        CK(c, launch_density(d, i0, n0, c->shape[0], observe ? 1 : 0, c->stream));
+        CK(c, launch_force(d, i1, n1, c->shape[1], observe ? 1 : 0, 0, 0, c->stream));
+    }
     if (observe) CK(c, launch_obs_reduce(d, 0, 0, c->stream));
     return MD_OK;
 }
@@ -241,8 +318,18 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
         const int64_t next = s0 + k + 1;
         const bool obs = oe > 0 && next % oe == 0;
         const bool last = k == M - 1;
-        CK(c, launch_density(d, i0, n0, c->shape[0], obs ? 1 : 0, c->stream));
-        CK(c, launch_force(d, i1, n1, c->shape[1], 2, k, (last ? 1 : 0) | (obs ? 2 : 0), c->stream));
+        const int flags = (last ? 1 : 0) | (obs ? 2 : 0);
+        if (c->path == 1) {
+            CK(c, launch_cell_build(d, c->stream));
+            CK(c, launch_cell_density(d, obs ? 1 : 0, c->stream));
+            CK(c, launch_cell_force(d, 2, k, flags, c->stream));
+            // Berendsen: positions now, velocities after the rescale (in k_berendsen)
+            if (obs) CK(c, launch_cell_obs(d, kind == MD_BERENDSEN ? 1 : 0, kind == MD_BERENDSEN ? 0 : 1, c->stream));
+            if (kind == MD_BERENDSEN) CK(c, launch_cell_ke(d, c->stream));
+        } else {
+            CK(c, launch_density(d, i0, n0, c->shape[0], obs ? 1 : 0, c->stream));
+            CK(c, launch_force(d, i1, n1, c->shape[1], 2, k, flags, c->stream));
+        }
         if (kind == MD_BERENDSEN) CK(c, launch_berendsen(d, k, last ? 1 : 0, c->stream));
         if (obs) CK(c, launch_obs_reduce(d, k, 1, c->stream));
     }
@@ -298,7 +385,9 @@ void free_all(md_ctx* c) {
     drop_graphs(c);
     void* ptrs[] = {c->d_poff, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
-                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise};
+                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
+                    c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
+                    c->d_cpos, c->d_cposg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -329,6 +418,9 @@ md_status check_status(md_ctx* c) {
     CK(c, cudaMemcpyAsync(&s, c->d_status, sizeof s, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (s & 1) return fail(c, MD_ERR_NONFINITE, "a force, position or velocity became non-finite");
+    if (s & 2)
+        return fail(c, MD_ERR_STATE, "a cell of the cell grid overflowed (more than %d atoms); forces are invalid",
+                    kCellCap);
     return MD_OK;
 }
 
@@ -424,8 +516,10 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     if (n_clusters < 1) return fail(nullptr, MD_ERR_INVALID, "n_clusters must be >= 1");
     if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED)
         return fail(nullptr, MD_ERR_INVALID, "unknown precision %d", cfg->precision);
-    if (cfg->path != MD_PATH_AUTO && cfg->path != MD_PATH_ALLPAIRS)
-        return fail(nullptr, MD_ERR_INVALID, "path %d is not available in this build", cfg->path);
+    if (cfg->path != MD_PATH_AUTO && cfg->path != MD_PATH_ALLPAIRS && cfg->path != MD_PATH_CELLS)
+        return fail(nullptr, MD_ERR_INVALID, "unknown path %d", cfg->path);
+    if (cfg->path == MD_PATH_CELLS && !(prm->rcut_A > 0))
+        return fail(nullptr, MD_ERR_INVALID, "the cell path needs a cutoff (rcut_A > 0)");
     if (cfg->obs_every < 0 || cfg->graph_chunk < 0 || cfg->obs_capacity < 0)
         return fail(nullptr, MD_ERR_INVALID, "negative obs_every, graph_chunk or obs_capacity");
     if (!(std::isfinite(prm->eps_eV) && std::isfinite(prm->c) && std::isfinite(prm->a_A) && prm->a_A > 0 &&
@@ -504,6 +598,19 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     P.A9f = (float)P.A9;
     P.rcut2f = (float)P.rcut2;
     P.special = (P.n == 9 && P.m == 6) ? 1 : 0;
+    {
+        int maxn = 0;
+        for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
+        const bool cells = cfg->path == MD_PATH_CELLS ||
+                           (cfg->path == MD_PATH_AUTO && P.rcut > 0 && maxn >= kAutoCellsMinAtoms);
+        c->path = cells ? 1 : 0;
+        if (cells && !make_grids(c, pos, mass)) {
+            delete c;
+            return fail(nullptr, MD_ERR_INVALID,
+                        "rcut_A = %g is too large for the cell path (a cell would exceed %d atoms); "
+                        "use MD_PATH_ALLPAIRS", P.rcut, kCellCap);
+        }
+    }
 
     auto bail = [&](md_status st) {
         free_all(c);
@@ -555,6 +662,26 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_posg, (size_t)vec4_size(c) * np));
     CKC(cudaMalloc(&c->d_step, sizeof(int64_t)));
     CKC(cudaMalloc(&c->d_run, sizeof(Run)));
+    if (c->path == 1) {
+        std::vector<int32_t> cell_cl(c->n_cells);
+        for (int b = 0; b < n_clusters; ++b)
+            for (int k = 0; k < c->grids[b].G * c->grids[b].G * c->grids[b].G; ++k) cell_cl[c->grids[b].off + k] = b;
+        CKC(cudaMalloc(&c->d_grid, sizeof(CellGrid) * n_clusters));
+        CKC(cudaMalloc(&c->d_cell_cl, sizeof(int32_t) * c->n_cells));
+        CKC(cudaMalloc(&c->d_cell_count, sizeof(int32_t) * c->n_cells));
+        CKC(cudaMalloc(&c->d_cell_atoms, sizeof(int32_t) * kCellCap * (size_t)c->n_cells));
+        CKC(cudaMalloc(&c->d_cpos, (size_t)vec4_size(c) * kCellCap * c->n_cells));
+        CKC(cudaMalloc(&c->d_cposg, (size_t)vec4_size(c) * kCellCap * c->n_cells));
+        CKC(cudaMalloc(&c->d_eatom, sizeof(double) * 2 * np));
+        CKC(cudaMalloc(&c->d_obs_x, sizeof(double) * 3 * np));
+        CKC(cudaMalloc(&c->d_obs_v, sizeof(double) * 3 * np));
+        CKC(cudaMemcpy(c->d_grid, c->grids.data(), sizeof(CellGrid) * n_clusters, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_cell_cl, cell_cl.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice));
+        CKC(cudaMemset(c->d_cell_count, 0, sizeof(int32_t) * c->n_cells));
+        CKC(cudaMemset(c->d_eatom, 0, sizeof(double) * 2 * np));
+        CKC(cudaMemset(c->d_obs_x, 0, sizeof(double) * 3 * np));
+        CKC(cudaMemset(c->d_obs_v, 0, sizeof(double) * 3 * np));
+    }
     for (int k = 0; k < 2; ++k) {
         CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
         CKC(cudaMemcpy(c->items_d[k], c->items_h[k].data(), sizeof(Item) * c->items_h[k].size(), cudaMemcpyHostToDevice));
@@ -844,10 +971,14 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     int n0, n1;
     const Item* i0 = items_for(c, c->shape[0], &n0);
     const Item* i1 = items_for(c, c->shape[1], &n1);
+    const bool cells = c->path == 1;
+    auto density = [&]() { return cells ? launch_cell_density(d, 0, c->stream) : launch_density(d, i0, n0, c->shape[0], 0, c->stream); };
+    auto force = [&]() { return cells ? launch_cell_force(d, 0, 0, 0, c->stream) : launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream); };
     CK(c, launch_mirror(d, c->stream));
+    if (cells) CK(c, launch_cell_build(d, c->stream));
     for (int w = 0; w < 3; ++w) {
-        CK(c, launch_density(d, i0, n0, c->shape[0], 0, c->stream));
-        CK(c, launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream));
+        CK(c, density());
+        CK(c, force());
     }
     std::vector<cudaEvent_t> ev(2 * reps + 2);
     for (auto& e : ev) CK(c, cudaEventCreate(&e));
@@ -855,7 +986,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     md_status st = MD_OK;
     for (int k = 0; k < reps && st == MD_OK; ++k) {
         cudaEventRecord(ev[2 * k], c->stream);
-        if (launch_density(d, i0, n0, c->shape[0], 0, c->stream) != cudaSuccess) st = MD_ERR_CUDA;
+        if (density() != cudaSuccess) st = MD_ERR_CUDA;
         cudaEventRecord(ev[2 * k + 1], c->stream);
     }
     cudaStreamSynchronize(c->stream);
@@ -866,7 +997,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     }
     for (int k = 0; k < reps && st == MD_OK; ++k) {
         cudaEventRecord(ev[2 * k], c->stream);
-        if (launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream) != cudaSuccess) st = MD_ERR_CUDA;
+        if (force() != cudaSuccess) st = MD_ERR_CUDA;
         cudaEventRecord(ev[2 * k + 1], c->stream);
     }
     cudaStreamSynchronize(c->stream);
@@ -879,9 +1010,33 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
     if (ms_d) *ms_d = td / reps;
     if (ms_f) *ms_f = tf / reps;
-    if (pairs) {
+    if (pairs && !cells) {
         double p = 0;
         for (int s : c->sizes) p += (double)s * (double)(s - 1);
+        *pairs = p;
+    } else if (pairs) {
+        // pairs tested: every atom against every atom of its 27 neighbour cells (self included)
+        std::vector<int32_t> cnt(c->n_cells);
+        CK(c, cudaMemcpyAsync(cnt.data(), c->d_cell_count, sizeof(int32_t) * c->n_cells, cudaMemcpyDeviceToHost,
+                              c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        double p = 0;
+        for (const CellGrid& g : c->grids)
+            for (int z = 0; z < g.G; ++z)
+                for (int y = 0; y < g.G; ++y)
+                    for (int x = 0; x < g.G; ++x) {
+                        const int hc = std::min(cnt[g.off + (z * g.G + y) * g.G + x], kCellCap);
+                        if (hc == 0) continue;
+                        int64_t nbr = 0;
+                        for (int dz = -1; dz <= 1; ++dz)
+                            for (int dy = -1; dy <= 1; ++dy)
+                                for (int dx = -1; dx <= 1; ++dx) {
+                                    const int X = x + dx, Y = y + dy, Z = z + dz;
+                                    if (X < 0 || Y < 0 || Z < 0 || X >= g.G || Y >= g.G || Z >= g.G) continue;
+                                    nbr += std::min(cnt[g.off + (Z * g.G + Y) * g.G + X], kCellCap);
+                                }
+                        p += (double)hc * (double)nbr;
+                    }
         *pairs = p;
     }
     return MD_OK;
@@ -889,6 +1044,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
 
 md_status md_autotune(md_ctx* c, int32_t reps) {
     if (!c || reps < 1) return MD_ERR_INVALID;
+    if (c->path == 1) return MD_OK;  // the cell kernels have one launch shape
     const Dev& d = c->dev;
     const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[4] = {1, 2, 4, 8};
     // Phase 1: every shape of each pass timed alone (CUDA events over reps launches).
@@ -998,7 +1154,7 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
 
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
-    if (per_step) *per_step = 2;
+    if (per_step) *per_step = c->path == 1 ? 5 : 2;
     if (per_chunk) *per_chunk = 3;
     return MD_OK;
 }

@@ -26,6 +26,7 @@ constexpr int kGroup = 32;      // atoms per observable partial record (one warp
 constexpr int kObsFields = 16;  // doubles per observable partial record
 constexpr int kMaxWarps = 16;
 constexpr int kMaxCluster = 8;
+constexpr int kCellCap = 256;   // atoms a cell of the cell-list path can hold
 
 // Fields of an observable partial record (per 32-atom group).
 enum ObsField {
@@ -47,6 +48,15 @@ struct Item {
     int32_t nj;   // real atoms in the cluster
     int32_t cl;   // cluster index
     int32_t pad;
+};
+
+// Cell grid of one cluster (cell-list path): G^3 cubic cells of side h >= rcut covering
+// the cube [-E, E)^3 around the cluster's origin; cells off .. off + G^3 - 1 of the context.
+// h is a binary32 value and E = G h / 2, so the offset between two cell centres, (k - l) h
+// with |k - l| <= 1 per axis, is exact in FP32.
+struct CellGrid {
+    int32_t G, off;
+    double h, E;
 };
 
 // Derived potential constants.
@@ -105,10 +115,22 @@ struct Dev {
     double* ke_grp;      // [ngroups] sum m v^2 (Berendsen)
     double* hist;        // ring [cap][B][kHistFields]
     int64_t* step_base;  // [1] global step of local step 0 of the running chunk
-    int32_t* status;     // [1] bit 0: non-finite value
+    int32_t* status;     // [1] bit 0: non-finite value; bit 1: a cell overflowed
     Run* run;            // device copy of Run
     Pot pot;
     double conv;         // (eV/amu) in (A/fs)^2
+    // cell-list path (path == 1); unused by the all-pairs path
+    int32_t path;        // 0: all pairs, 1: cell list
+    int32_t n_cells;     // cells of all clusters
+    const CellGrid* grid;// [B]
+    const int32_t* cell_cl;  // [n_cells] cluster of each cell
+    int32_t* cell_count; // [n_cells] atoms binned into each cell (may exceed kCellCap: overflow)
+    int32_t* cell_atoms; // [n_cells][kCellCap] padded atom indices, ascending within a cell
+    void* cpos;          // [n_cells][kCellCap] V4 (x - cell centre, 0) in the pass precision
+    void* cposg;         // [n_cells][kCellCap] V4 (x - cell centre, B6 rho^-1/2), density pass
+    double* eatom;       // [npad][2] per-atom -eps c sqrt(rho_i) and sum_j r_ij^-n
+    double* obs_x;       // [npad][3] positions at an observation (end of the step)
+    double* obs_v;       // [npad][3] velocities at an observation
 };
 
 constexpr int kHistFields = 20;  // doubles per history record (see md_obs packing in the API)
@@ -135,6 +157,14 @@ cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t
 cudaError_t launch_normals(uint64_t seed, uint32_t cluster, int64_t step, int n, int prec, double* out,
                            cudaStream_t s);
 size_t pass_smem_bytes(int prec, Shape sh);
+// Cell-list path (defined in scmd_cells.cu).
+cudaError_t launch_cell_build(const Dev& d, cudaStream_t s);  // clear, bin, sort
+cudaError_t launch_cell_density(const Dev& d, int obs, cudaStream_t s);
+cudaError_t launch_cell_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
+// Observable partials of every 32-atom group from the per-atom data (from_state: read x, v;
+// else the snapshot obs_x, obs_v); with_velocity 0 leaves the velocity fields alone.
+cudaError_t launch_cell_obs(const Dev& d, int from_state, int with_velocity, cudaStream_t s);
+cudaError_t launch_cell_ke(const Dev& d, cudaStream_t s);
 // The calling thread's error message returned by md_last_error(NULL) (defined in scmd_api.cu).
 void set_thread_error(const char* msg);
 cudaError_t configure_kernels();
