@@ -176,9 +176,20 @@ def cpu_baseline(w, budget_s: float):
     t0 = time.perf_counter()
     b.run(steps, w["dt"], th)
     el = time.perf_counter() - t0
-    return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} MD steps (FP64, all pairs{cut_note(w)}) of {len(sizes)} cluster(s), {n} atoms, "
-                      f"dt={w['dt']} fs, same thermostat", "s_per_step": el / steps}
+    out = {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{steps} MD steps (FP64, all pairs{cut_note(w)}) of {len(sizes)} cluster(s), {n} atoms, "
+                     f"dt={w['dt']} fs, same thermostat", "s_per_step": el / steps}
+    # the same oracle on one core (the paper compares against one CPU core), when it fits the budget
+    if t1 * cores <= budget_s:
+        oracle.num_threads(1)
+        steps1 = max(1, min(200, int(0.5 * budget_s / (t1 * cores))))
+        t0 = time.perf_counter()
+        b.run(steps1, w["dt"], th)
+        el1 = time.perf_counter() - t0
+        oracle.num_threads(cores)
+        out["value_1core"] = n * steps1 / el1
+        out["sample_1core"] = f"{steps1} MD steps, same sample, 1 thread"
+    return out
 
 
 def cut_note(w):
@@ -229,6 +240,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--melt-steps", type=int, default=None, help="override the untimed melt length")
     ap.add_argument("--shapes", default=None, help="ipt,warps,cluster for the density and force passes (6 ints); skips tuning")
+    ap.add_argument("--snapshots", type=int, default=None, help="states kept during the timed run for e_F (default 10)")
+    ap.add_argument("--drift-steps", type=int, default=None, help="NVE steps of the drift runs (default: automatic)")
+    ap.add_argument("--skip-analysis", action="store_true", help="no snapshots, drift runs or structure analysis")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -275,6 +289,7 @@ def main():
     if w["melt_steps"]:
         scmd.md_step(ctx, w["melt_steps"], dt, scmd.thermostat(scmd.MD_LANGEVIN, w["melt_T"], w["melt_T"],
                                                                gamma_per_ps=w["gamma"], seed=w["seed"]))
+    melt_pos, melt_vel, _ = scmd.md_get_state(ctx)  # start of the NVE drift runs
     M = args.md_steps
 
     def therm(k):
@@ -292,6 +307,12 @@ def main():
     for _ in range(args.warmup):
         scmd.md_step(ctx, M, dt, therm(k_iter))
         k_iter += 1
+    n0 = int(sizes[0])
+    analysis_on = not args.skip_analysis
+    n_snap = 0 if not analysis_on else (args.snapshots if args.snapshots is not None else (10 if natoms <= 20000 else 3))
+    snap_every = max(1, args.steps // max(n_snap, 1))
+    snaps = []
+    obs_start = scmd.md_observables(ctx) if analysis_on else None
     sampler = ClockSampler(local)
     torch.cuda.synchronize()
     if dist:
@@ -307,6 +328,8 @@ def main():
         with torch.cuda.stream(stream):
             ev[k][1].record(stream)
         k_iter += 1
+        if len(snaps) < n_snap and (k + 1) % snap_every == 0:  # outside the events: a D2H copy of x
+            snaps.append(scmd.md_get_state(ctx)[0][:n0].copy())
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     if dist:
@@ -338,12 +361,33 @@ def main():
     # force error of the final state against the FP64 oracle (rank 0, first cluster)
     force_err = None
     pos_f, vel_f, step_f = scmd.md_get_state(ctx)
+    snap_err = []
     if rank == 0:
         import oracle
         E, F = scmd.md_energy_forces(ctx)
-        n0 = int(sizes[0])
         _, Fr, _, _ = oracle.energy_forces(pos_f[:n0], oracle.params(rcut=rcut))
         force_err = float(np.linalg.norm(F[:n0] - Fr) / np.linalg.norm(Fr))
+        # the snapshots of the timed run: first cluster, fresh context of the same precision and path
+        for sp in snaps:
+            cs = scmd.md_create(scmd.config(precision=P, path=scmd.MD_PATH_AUTO), [n0], sp, None, w["mass"][:n0],
+                                scmd.sc_params(rcut=rcut))
+            _, Fs = scmd.md_energy_forces(cs)
+            scmd.md_destroy(cs)
+            _, Fr, _, _ = oracle.energy_forces(sp, oracle.params(rcut=rcut))
+            snap_err.append(float(np.linalg.norm(Fs - Fr) / np.linalg.norm(Fr)))
+    structure = None
+    if rank == 0 and analysis_on:
+        from paper_1210_3559_gb300 import analysis
+        obs_end = scmd.md_observables(ctx)
+        structure = {"cluster": 0, "atoms": n0,
+                     "epot_per_atom_start_eV": obs_start[0]["epot"] / n0, "epot_per_atom_end_eV": obs_end[0]["epot"] / n0,
+                     "T_start_K": obs_start[0]["T"], "T_end_K": obs_end[0]["T"],
+                     "crystalline_fraction_end": analysis.crystalline_fraction(pos_f[:n0], 3.52),
+                     "crystalline_fraction_start_of_schedule": analysis.crystalline_fraction(melt_pos[:n0], 3.52)}
+    useful_pairs = None
+    if rank == 0 and cells:  # ordered pairs closer than rcut at the final state (each visited in both passes)
+        from scipy.spatial import cKDTree
+        useful_pairs = 2.0 * len(cKDTree(pos_f).query_pairs(rcut, output_type="ndarray"))
 
     # e2e through the C ABI with host buffers: set_state (H2D) + md_step + get_state (D2H)
     pos_h = torch.from_numpy(pos_f.copy()).pin_memory().numpy()
@@ -389,6 +433,32 @@ def main():
                 "sample": f"{reps64} x {m64} MD steps, same state and thermostat, per GPU"}
         scmd.md_destroy(c64)
 
+    # NVE energy drift from the melted state, MIXED and FP64 on the GPU (first cluster, or the first 8)
+    drift = None
+    if rank == 0 and analysis_on:
+        from paper_1210_3559_gb300 import analysis
+        nb = 1 if len(sizes) == 1 else min(8, len(sizes))
+        sz = sizes[:nb]
+        na = int(sz.sum())
+        rate64 = (fp64 or {}).get("value") or 2.0e6
+        steps_d = args.drift_steps or int(min(20000, max(1000, 10.0 * rate64 / na)))
+        oe = max(1, steps_d // 200)
+        drift = {"start": "state after the untimed melt" if w["melt_steps"] else "initial state",
+                 "clusters": int(nb), "atoms": na, "steps": steps_d, "dt_fs": dt}
+        for name, pr in (("mixed", scmd.MD_PREC_MIXED), ("fp64", scmd.MD_PREC_FP64)):
+            if pr == scmd.MD_PREC_FP64 and args.skip_fp64:
+                continue
+            cd = scmd.md_create(scmd.config(precision=pr, obs_every=oe, obs_capacity=steps_d // oe + 2,
+                                            graph_chunk=min(512, steps_d), stream=stream.cuda_stream),
+                                sz, melt_pos[:na], melt_vel[:na], w["mass"][:na], scmd.sc_params(rcut=rcut))
+            e0 = scmd.md_observables(cd)
+            scmd.md_step(cd, steps_d, dt)
+            hist = scmd.md_obs_history(cd)
+            scmd.md_destroy(cd)
+            t = np.array([0.0] + [h[0]["time_fs"] for h in hist])
+            et = np.array([sum(o["etot"] for o in e0)] + [sum(o["etot"] for o in h) for h in hist])
+            drift[name] = analysis.energy_drift(t, et, na)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cpu = cpu_baseline(w, args.cpu_budget)
@@ -406,9 +476,13 @@ def main():
                        "launch_shapes": {k: list(v) for k, v in shapes.items()} if not cells else "cell list",
                        "rcut_A": rcut or None, "path": "cells" if cells else "all pairs",
                        "wall_s_timed_region": t_wall},
-            "pair_evals_per_s": pair_rate,
+            "pair_evals_per_s": pair_rate if not cells else useful_pairs * md_steps_total * world / t_max,
+            "candidate_pairs_per_s": pair_rate if cells else None,
             "fp32_pipe_frac_force_pass": achieved / peak_ops,
             "force_err_vs_oracle": force_err,
+            "force_err_snapshots": snap_err or None,
+            "nve_drift": drift,
+            "structure": structure,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": FORCE_DRAM_BYTES_PER_LAUNCH.get(args.config) if prec == "mixed" else None,

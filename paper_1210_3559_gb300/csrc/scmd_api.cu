@@ -79,7 +79,7 @@ struct md_ctx {
     int n_cells = 0;
     std::vector<CellGrid> grids;
     CellGrid* d_grid = nullptr;
-    int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr;
+    int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr, *d_cell_order = nullptr;
     void *d_cpos = nullptr, *d_cposg = nullptr;
     double *d_eatom = nullptr, *d_obs_x = nullptr, *d_obs_v = nullptr;
     // pinned staging
@@ -164,6 +164,7 @@ void fill_dev(md_ctx* c) {
     d.n_cells = c->n_cells;
     d.grid = c->d_grid;
     d.cell_cl = c->d_cell_cl;
+    d.cell_order = c->d_cell_order;
     d.cell_count = c->d_cell_count;
     d.cell_atoms = c->d_cell_atoms;
     d.cpos = c->d_cpos;
@@ -387,7 +388,7 @@ void free_all(md_ctx* c) {
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
-                    c->d_cpos, c->d_cposg};
+                    c->d_cpos, c->d_cposg, c->d_cell_order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -663,11 +664,26 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_step, sizeof(int64_t)));
     CKC(cudaMalloc(&c->d_run, sizeof(Run)));
     if (c->path == 1) {
-        std::vector<int32_t> cell_cl(c->n_cells);
-        for (int b = 0; b < n_clusters; ++b)
-            for (int k = 0; k < c->grids[b].G * c->grids[b].G * c->grids[b].G; ++k) cell_cl[c->grids[b].off + k] = b;
+        std::vector<int32_t> cell_cl(c->n_cells), order(c->n_cells);
+        std::vector<double> depth(c->n_cells);
+        for (int b = 0; b < n_clusters; ++b) {
+            const CellGrid& g = c->grids[b];
+            for (int k = 0; k < g.G * g.G * g.G; ++k) {
+                cell_cl[g.off + k] = b;
+                // distance of the cell centre from the grid centre, in units of the cluster radius
+                const double x = (k % g.G + 0.5) * g.h - g.E, y = ((k / g.G) % g.G + 0.5) * g.h - g.E;
+                const double z = (k / (g.G * g.G) + 0.5) * g.h - g.E;
+                depth[g.off + k] = std::sqrt(x * x + y * y + z * z) / std::max(g.E - c->pot.rcut, 1e-9);
+            }
+        }
+        // interior (fullest) cells are launched first, so that the light surface cells and the empty
+        // ones fill the tail of the pass instead of extending it
+        for (int k = 0; k < c->n_cells; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return depth[a] < depth[b]; });
         CKC(cudaMalloc(&c->d_grid, sizeof(CellGrid) * n_clusters));
         CKC(cudaMalloc(&c->d_cell_cl, sizeof(int32_t) * c->n_cells));
+        CKC(cudaMalloc(&c->d_cell_order, sizeof(int32_t) * c->n_cells));
+        CKC(cudaMemcpy(c->d_cell_order, order.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice));
         CKC(cudaMalloc(&c->d_cell_count, sizeof(int32_t) * c->n_cells));
         CKC(cudaMalloc(&c->d_cell_atoms, sizeof(int32_t) * kCellCap * (size_t)c->n_cells));
         CKC(cudaMalloc(&c->d_cpos, (size_t)vec4_size(c) * kCellCap * c->n_cells));

@@ -21,17 +21,19 @@
 // (h is a binary32 value). In MIXED mode a coordinate is then off by at most about
 // ulp(1.5 h) ~ 5e-7 A whatever the cluster's size, where offsets from one origin per cluster
 // would carry ulp(R) (about 2e-6 A at R = 50 A).
-// One CTA per home cell. The atoms of the 27 neighbour cells are gathered into shared memory in
-// chunks; the home cell's nb atoms (nb <= 256) take nb i-slots and J = 256 / nb j-groups split
-// each chunk, so a warp reads one or two staged atoms per step for up to 32 i-atoms. A pair is
-// masked (r2 := inf) when r2 >= rcut^2 or when it is the atom itself (recognised by its place in
-// the staged list), like the all-pairs cutoff variant, so every tested pair takes the same
-// arithmetic as there.
+// One CTA per home cell, launched interior cells first (the fullest cells start early and the
+// light surface cells fill the tail). The atoms of the 27 neighbour cells are gathered into shared
+// memory in chunks; the home cell's nb atoms (nb <= 256) take nb i-slots and J = 256 / nb j-groups,
+// each walking a contiguous share of every chunk, so a warp reads one or two staged atoms per step
+// for up to 32 i-atoms. A pair is masked (r2 := inf) when r2 >= rcut^2 or when it is the atom itself
+// (recognised by its place in the staged list), like the all-pairs cutoff variant, so every tested
+// pair takes the same arithmetic as there.
 #include "scmd_device.cuh"
 
 namespace scmd {
 
 constexpr int kCellThreads = 256;
+constexpr int kSpan = 128;  // pair terms summed in the pass precision before folding into the wider sums
 template <int PREC> struct CellChunk;
 template <> struct CellChunk<1> { static constexpr int TJ = 2048; };  // 32 KB of float4
 template <> struct CellChunk<0> { static constexpr int TJ = 1024; };  // 32 KB of double4
@@ -153,7 +155,7 @@ __device__ __forceinline__ void gather(const V4* __restrict__ src, const int* sc
 
 // ------------------------------------------------------------- density pass
 template <int PREC, int SPECIAL>
-__global__ void __launch_bounds__(kCellThreads) k_cell_density(const Dev d, int obs) {
+__global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_density(const Dev d, int obs) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     constexpr int TJ = CellChunk<PREC>::TJ;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_density(const Dev d, int 
     __shared__ double part[kCellThreads];
     pdl_launch_dependents();
     pdl_wait();
-    const int c = blockIdx.x;
+    const int c = d.cell_order[blockIdx.x];
     const int hc = min(d.cell_count[c], kCellCap);
     if (hc == 0) return;
     const int cl = d.cell_cl[c];
@@ -180,42 +182,39 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_density(const Dev d, int 
         const V4 pi = cp[(size_t)c * kCellCap + r0 + is];
         f2sum facc = {0.f, 0.f};
         double racc = 0.0;
-        R tacc = R(0);
-        int span = 0;
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
             gather(cp, scell, pref, h, e0, ne, spos);
             __syncthreads();
             if (!act) continue;
-            for (int e = jg; e < ne; e += J) {
-                const V4 p = spos[e];
-                const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
-                R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                r2 = (r2 < rc2 && e0 + e != self) ? r2 : big<R>();
-                if (SPECIAL) {
-                    const R inv = inv_r2(r2);
-                    tacc = fma(inv * inv, inv, tacc);
-                } else {
-                    const R ir = inv_r(r2);
-                    tacc += rpow(ir * ir, ir, mexp);
+            // this j-group's contiguous share of the chunk, summed in spans of kSpan terms
+            const int per = (ne + J - 1) / J, lo = min(ne, jg * per), hi = min(ne, lo + per);
+            const int selfl = self - e0;
+            for (int b = lo; b < hi; b += kSpan) {
+                const int stop = min(hi, b + kSpan);
+                R tacc = R(0);
+#pragma unroll 4
+                for (int e = b; e < stop; ++e) {
+                    const V4 p = spos[e];
+                    const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
+                    if (SPECIAL) {
+                        const R inv = inv_r2(r2);
+                        tacc = fma(inv * inv, inv, tacc);
+                    } else {
+                        const R ir = inv_r(r2);
+                        tacc += rpow(ir * ir, ir, mexp);
+                    }
                 }
-                if (++span == 128) {
-                    if (PREC == 1)
-                        facc = f2_add(facc, (float)tacc);
-                    else
-                        racc += (double)tacc;
-                    tacc = R(0);
-                    span = 0;
-                }
+                if (PREC == 1)
+                    facc = f2_add(facc, (float)tacc);
+                else
+                    racc += (double)tacc;
             }
         }
-        if (PREC == 1) {
-            facc = f2_add(facc, (float)tacc);
-            racc = (double)facc.hi + (double)facc.lo;
-        } else {
-            racc += (double)tacc;
-        }
+        if (PREC == 1) racc = (double)facc.hi + (double)facc.lo;
         part[t] = racc;
         __syncthreads();
         if (jg == 0) {
@@ -244,7 +243,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_density(const Dev d, int 
 // step unless this is the chunk's last step or the thermostat is Berendsen (whose kernel
 // rescales and starts the next step).
 template <int PREC, int SPECIAL, int ENERGY>
-__global__ void __launch_bounds__(kCellThreads) k_cell_force(const Dev d, int mode, int k_local, int last) {
+__global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_force(const Dev d, int mode, int k_local, int last) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     constexpr int TJ = CellChunk<PREC>::TJ;
@@ -254,7 +253,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_force(const Dev d, int mo
     __shared__ double parte[ENERGY ? kCellThreads : 1];
     pdl_launch_dependents();
     pdl_wait();
-    const int c = blockIdx.x;
+    const int c = d.cell_order[blockIdx.x];
     const int hc = min(d.cell_count[c], kCellCap);
     if (hc == 0) return;
     const int cl = d.cell_cl[c];
@@ -271,53 +270,52 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_force(const Dev d, int mo
         const int i = home[r0 + is];
         const int self = pref[13] + r0 + is;
         const V4 pi = pg[(size_t)c * kCellCap + r0 + is];
-        R fx = R(0), fy = R(0), fz = R(0), sx = R(0), sy = R(0), sz = R(0), se = R(0);
+        R fx = R(0), fy = R(0), fz = R(0);
         double ea = 0.0;
-        int span = 0;
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
             gather(pg, scell, pref, h, e0, ne, spos);
             __syncthreads();
             if (!act) continue;
-            for (int e = jg; e < ne; e += J) {
-                const V4 p = spos[e];
-                const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
-                R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                r2 = (r2 < rc2 && e0 + e != self) ? r2 : big<R>();
-                const R ir = inv_r(r2);
-                const R inv = ir * ir;
-                R coef, rn;
-                if (SPECIAL) {
-                    const R inv2 = inv * inv, inv4 = inv2 * inv2;
-                    coef = inv4 * fma(A, inv * ir, -(pi.w + p.w));
-                    rn = inv4 * ir;
-                } else {
-                    rn = rpow(inv, ir, nexp);
-                    const R rm = rpow(inv, ir, mexp);
-                    coef = inv * (A * rn - (pi.w + p.w) * rm);
-                }
-                sx = fma(coef, dx, sx);
-                sy = fma(coef, dy, sy);
-                sz = fma(coef, dz, sz);
-                if (ENERGY) se += rn;
-                if (++span == 128) {
-                    fx += sx;
-                    fy += sy;
-                    fz += sz;
-                    sx = sy = sz = R(0);
-                    if (ENERGY) {
-                        ea += (double)se;
-                        se = R(0);
+            const int per = (ne + J - 1) / J, lo = min(ne, jg * per), hi = min(ne, lo + per);
+            const int selfl = self - e0;
+            for (int b = lo; b < hi; b += kSpan) {
+                const int stop = min(hi, b + kSpan);
+                R sx = R(0), sy = R(0), sz = R(0), se = R(0);
+#pragma unroll 4
+                for (int e = b; e < stop; ++e) {
+                    const V4 p = spos[e];
+                    const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
+                    const R ir = inv_r(r2);
+                    const R inv = ir * ir;
+                    R coef, rn;
+                    if (SPECIAL) {
+                        const R inv2 = inv * inv, inv4 = inv2 * inv2;
+                        coef = inv4 * fma(A, inv * ir, -(pi.w + p.w));
+                        rn = inv4 * ir;
+                    } else {
+                        rn = rpow(inv, ir, nexp);
+                        const R rm = rpow(inv, ir, mexp);
+                        coef = inv * (A * rn - (pi.w + p.w) * rm);
                     }
-                    span = 0;
+                    sx = fma(coef, dx, sx);
+                    sy = fma(coef, dy, sy);
+                    sz = fma(coef, dz, sz);
+                    if (ENERGY) se += rn;
                 }
+                fx += sx;
+                fy += sy;
+                fz += sz;
+                if (ENERGY) ea += (double)se;
             }
         }
-        partf[t][0] = fx + sx;
-        partf[t][1] = fy + sy;
-        partf[t][2] = fz + sz;
-        if (ENERGY) parte[t] = ea + (double)se;
+        partf[t][0] = fx;
+        partf[t][1] = fy;
+        partf[t][2] = fz;
+        if (ENERGY) parte[t] = ea;
         __syncthreads();
         if (jg != 0) continue;
         R Fx = partf[is][0], Fy = partf[is][1], Fz = partf[is][2];

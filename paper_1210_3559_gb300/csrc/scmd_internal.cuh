@@ -124,6 +124,7 @@ struct Dev {
     int32_t n_cells;     // cells of all clusters
     const CellGrid* grid;// [B]
     const int32_t* cell_cl;  // [n_cells] cluster of each cell
+    const int32_t* cell_order; // [n_cells] pair-pass launch order: cells nearest their cluster's centre first
     int32_t* cell_count; // [n_cells] atoms binned into each cell (may exceed kCellCap: overflow)
     int32_t* cell_atoms; // [n_cells][kCellCap] padded atom indices, ascending within a cell
     void* cpos;          // [n_cells][kCellCap] V4 (x - cell centre, 0) in the pass precision
