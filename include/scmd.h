@@ -78,7 +78,7 @@ typedef enum {
  * keeps the result exact. Each step bins the atoms (a cell holds at most 256;
  * md_create refuses an rcut_A whose cells would exceed that at the fcc density
  * 4 / a^3, and a step that overflows a cell returns MD_ERR_STATE) and sums each
- * atom over the 27 cells around its own. Pair terms, masks and the integrator are
+ * atom over the 5 x 5 x 5 cell octants (side h/2) around its own. Pair terms, masks and the integrator are
  * those of the all-pairs path with the cutoff, so both agree to rounding order. */
 
 /* Sutton-Chen parameters (Eq. 1, Eq. 2). Paper's Ni set (Sec. II A):
@@ -231,8 +231,8 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
  * pass, timed alone with CUDA events on the context's stream over reps
  * launches after warm-up. Pair-evaluation counts per launch are returned in
  * *pairs (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for
- * the cell path, every atom times the atoms of its 27 neighbour cells, self
- * included, as binned at the current positions). Any output may be NULL.
+ * the cell path, every atom times the atoms of the 5 x 5 x 5 cell octants around
+ * its own, self included, as binned at the current positions). Any output may be NULL.
  */
 md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* ms_force,
                          double* pairs);

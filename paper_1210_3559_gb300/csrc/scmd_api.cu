@@ -80,6 +80,7 @@ struct md_ctx {
     std::vector<CellGrid> grids;
     CellGrid* d_grid = nullptr;
     int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr, *d_cell_order = nullptr;
+    int32_t* d_cell_oct = nullptr;
     void *d_cpos = nullptr, *d_cposg = nullptr;
     double *d_eatom = nullptr, *d_obs_x = nullptr, *d_obs_v = nullptr;
     // pinned staging
@@ -167,6 +168,7 @@ void fill_dev(md_ctx* c) {
     d.cell_order = c->d_cell_order;
     d.cell_count = c->d_cell_count;
     d.cell_atoms = c->d_cell_atoms;
+    d.cell_oct = c->d_cell_oct;
     d.cpos = c->d_cpos;
     d.cposg = c->d_cposg;
     d.eatom = c->d_eatom;
@@ -204,7 +206,8 @@ bool make_grids(md_ctx* c, const double* pos, const double* mass) {
         const double r_fcc = a * std::cbrt(3.0 * n / (16.0 * kPi));
         const double r_now = std::min(std::sqrt(r2max), 3.0 * r_fcc);
         const double E = std::max(1.3 * r_fcc, 1.1 * r_now) + rc;
-        const int G = std::max(1, std::min(128, (int)std::floor(2.0 * E / rc)));
+        // (1 + 1e-6): h > rcut strictly, so rounding at a cell face cannot matter
+        const int G = std::max(1, std::min(128, (int)std::floor(2.0 * E / (rc * (1.0 + 1e-6)))));
         CellGrid g{};
         g.G = G;
         g.off = off;
@@ -388,7 +391,7 @@ void free_all(md_ctx* c) {
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
-                    c->d_cpos, c->d_cposg, c->d_cell_order};
+                    c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -686,6 +689,8 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         CKC(cudaMemcpy(c->d_cell_order, order.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice));
         CKC(cudaMalloc(&c->d_cell_count, sizeof(int32_t) * c->n_cells));
         CKC(cudaMalloc(&c->d_cell_atoms, sizeof(int32_t) * kCellCap * (size_t)c->n_cells));
+        CKC(cudaMalloc(&c->d_cell_oct, sizeof(int32_t) * 9 * (size_t)c->n_cells));
+        CKC(cudaMemset(c->d_cell_oct, 0, sizeof(int32_t) * 9 * (size_t)c->n_cells));
         CKC(cudaMalloc(&c->d_cpos, (size_t)vec4_size(c) * kCellCap * c->n_cells));
         CKC(cudaMalloc(&c->d_cposg, (size_t)vec4_size(c) * kCellCap * c->n_cells));
         CKC(cudaMalloc(&c->d_eatom, sizeof(double) * 2 * np));
@@ -1031,27 +1036,29 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
         for (int s : c->sizes) p += (double)s * (double)(s - 1);
         *pairs = p;
     } else if (pairs) {
-        // pairs tested: every atom against every atom of its 27 neighbour cells (self included)
-        std::vector<int32_t> cnt(c->n_cells);
-        CK(c, cudaMemcpyAsync(cnt.data(), c->d_cell_count, sizeof(int32_t) * c->n_cells, cudaMemcpyDeviceToHost,
+        // pairs tested: every atom of a home octant against every atom of the 5 x 5 x 5 octants
+        // around it (itself included), as binned at the current positions
+        std::vector<int32_t> oct((size_t)9 * c->n_cells);
+        CK(c, cudaMemcpyAsync(oct.data(), c->d_cell_oct, sizeof(int32_t) * 9 * c->n_cells, cudaMemcpyDeviceToHost,
                               c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
+        auto noct = [&](const CellGrid& g, int X, int Y, int Z) -> int64_t {  // octant coordinates in the grid
+            if (X < 0 || Y < 0 || Z < 0 || X >= 2 * g.G || Y >= 2 * g.G || Z >= 2 * g.G) return 0;
+            const int cc = g.off + ((Z / 2) * g.G + Y / 2) * g.G + X / 2, o = (X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2);
+            return oct[(size_t)cc * 9 + o + 1] - oct[(size_t)cc * 9 + o];
+        };
         double p = 0;
         for (const CellGrid& g : c->grids)
-            for (int z = 0; z < g.G; ++z)
-                for (int y = 0; y < g.G; ++y)
-                    for (int x = 0; x < g.G; ++x) {
-                        const int hc = std::min(cnt[g.off + (z * g.G + y) * g.G + x], kCellCap);
-                        if (hc == 0) continue;
+            for (int Z = 0; Z < 2 * g.G; ++Z)
+                for (int Y = 0; Y < 2 * g.G; ++Y)
+                    for (int X = 0; X < 2 * g.G; ++X) {
+                        const int64_t n = noct(g, X, Y, Z);
+                        if (n == 0) continue;
                         int64_t nbr = 0;
-                        for (int dz = -1; dz <= 1; ++dz)
-                            for (int dy = -1; dy <= 1; ++dy)
-                                for (int dx = -1; dx <= 1; ++dx) {
-                                    const int X = x + dx, Y = y + dy, Z = z + dz;
-                                    if (X < 0 || Y < 0 || Z < 0 || X >= g.G || Y >= g.G || Z >= g.G) continue;
-                                    nbr += std::min(cnt[g.off + (Z * g.G + Y) * g.G + X], kCellCap);
-                                }
-                        p += (double)hc * (double)nbr;
+                        for (int dz = -2; dz <= 2; ++dz)
+                            for (int dy = -2; dy <= 2; ++dy)
+                                for (int dx = -2; dx <= 2; ++dx) nbr += noct(g, X + dx, Y + dy, Z + dz);
+                        p += (double)n * (double)nbr;
                     }
         *pairs = p;
     }

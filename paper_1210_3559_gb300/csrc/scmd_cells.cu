@@ -2,19 +2,23 @@
 //
 // The paper evaluates every pair and names efficient cutoff schemes as work in progress
 // (Sec. II). With rcut > 0 a context may instead give each cluster a cubic grid of G^3 cells of
-// side h >= rcut, fixed when the context is created: the cube [-E, E)^3 around the cluster's
+// side h > rcut, fixed when the context is created: the cube [-E, E)^3 around the cluster's
 // origin (the centre of mass that the MIXED pair coordinates are measured from), with E a
 // margin beyond the cluster's radius. Atoms outside the cube are clamped into its border
-// cells; clamping is monotone per axis, so two atoms closer than rcut still sit in the same or
-// in adjacent cells. Per MD step:
+// cells; clamping is monotone per axis and moves an atom only outward, so two atoms closer than
+// rcut are still found by the stencil below. Per MD step:
 //   k_cell_clear, k_cell_bin : atoms binned into cells of fixed capacity (atomic slots;
 //                              an overflow sets status bit 1, reported by the host);
-//   k_cell_sort              : each cell's list sorted by atom index, so the order of every
-//                              sum below and hence the results are independent of the order in
-//                              which the atomic slots were taken;
-//   k_cell_density           : rho_i over the 27 neighbour cells (Eq. 2 with the cutoff);
-//   k_cell_force             : F_i over the 27 neighbour cells (-grad of Eq. 1 with the
-//                              cutoff), then the integrator step of the all-pairs path.
+//   k_cell_sort              : each cell's list sorted by (octant, atom index), so the order of
+//                              every sum below and hence the results are independent of the order
+//                              in which the atomic slots were taken;
+//   k_cell_density           : rho_i over the neighbour octants (Eq. 2 with the cutoff);
+//   k_cell_force             : F_i over the neighbour octants (-grad of Eq. 1 with the cutoff),
+//                              then the integrator step of the all-pairs path.
+// Octants: each cell is split into 2 x 2 x 2 octants of side h/2 > rcut/2. Two atoms closer than
+// rcut lie at most two octants apart per axis, so the atoms of one home octant need only the
+// 5 x 5 x 5 octants around it: 125 of the 216 octants of the 27 cells around the home cell, which
+// cuts the pairs tested by ~42 % against whole cells.
 // Pair coordinates are relative to cell centres: when the atoms are binned, each cell stores its
 // atoms' offsets x - centre (rounded once from the FP64 state to the pass precision), and a CTA
 // moves a neighbour cell's offsets to its own centre by adding (k - l) h, which is exact in FP32
@@ -22,20 +26,21 @@
 // ulp(1.5 h) ~ 5e-7 A whatever the cluster's size, where offsets from one origin per cluster
 // would carry ulp(R) (about 2e-6 A at R = 50 A).
 // One CTA per home cell, launched interior cells first (the fullest cells start early and the
-// light surface cells fill the tail). The atoms of the 27 neighbour cells are gathered into shared
-// memory in chunks; the home cell's nb atoms (nb <= 256) take nb i-slots and J = 256 / nb j-groups,
-// each walking a contiguous share of every chunk, so a warp reads one or two staged atoms per step
-// for up to 32 i-atoms. A pair is masked (r2 := inf) when r2 >= rcut^2 or when it is the atom itself
-// (recognised by its place in the staged list), like the all-pairs cutoff variant, so every tested
-// pair takes the same arithmetic as there.
+// light surface cells fill the tail), one warp per home octant. The 216 octants around the cell are
+// staged in shared memory (in chunks if they exceed it); a warp's nb home atoms take nb i-slots
+// and J = 32 / nb j-groups, each group walking a contiguous share of each of the 25 runs of
+// neighbour octants (5 octants along x are adjacent in the staged order), so a warp reads at most
+// J staged atoms per step. A pair is masked (r2 := inf) when r2 >= rcut^2 or when it is the atom
+// itself (recognised by its place in the staged list), like the all-pairs cutoff variant, so every
+// tested pair takes the same arithmetic as there.
 #include "scmd_device.cuh"
 
 namespace scmd {
 
 constexpr int kCellThreads = 256;
-constexpr int kSpan = 128;  // pair terms summed in the pass precision before folding into the wider sums
+constexpr int kBox = 6, kBoxN = 216;  // the octant box of a home cell: 6 x 6 x 6 octants
 template <int PREC> struct CellChunk;
-template <> struct CellChunk<1> { static constexpr int TJ = 2048; };  // 32 KB of float4
+template <> struct CellChunk<1> { static constexpr int TJ = 2304; };  // 36 KB of float4
 template <> struct CellChunk<0> { static constexpr int TJ = 1024; };  // 32 KB of double4
 
 // Cell index along one axis of a coordinate relative to the origin. fmin/fmax come before the
@@ -74,11 +79,14 @@ __global__ void k_cell_bin(const Dev d) {
         atomicOr(d.status, 2);
 }
 
-// One warp per cell: each entry's rank among the cell's (distinct) atom indices is its place;
-// the atom's offset from the cell centre is stored at the same place.
+// One warp per cell. Each atom's octant of the cell (the sign of its offset from the centre per
+// axis) and its rank by (octant, atom index) give its place; the offset is stored at the same place,
+// and the first place of every octant (plus the count) in cell_oct.
 template <int PREC> __global__ void k_cell_sort(const Dev d) {
     using V4 = typename Tr<PREC>::V4;
+    using R = typename Tr<PREC>::R;
     __shared__ int buf[kCellThreads / 32][kCellCap];
+    __shared__ unsigned char boct[kCellThreads / 32][kCellCap];
     pdl_launch_dependents();
     pdl_wait();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -86,22 +94,29 @@ template <int PREC> __global__ void k_cell_sort(const Dev d) {
     if (c >= d.n_cells) return;
     const int n = min(d.cell_count[c], kCellCap);
     int* a = d.cell_atoms + (size_t)c * kCellCap;
-    for (int k = lane; k < n; k += 32) buf[w][k] = a[k];
-    __syncwarp();
-    if (n == 0) return;
     const int cl = d.cell_cl[c];
     const CellGrid g = d.grid[cl];
     const int loc = c - g.off, np = d.npad;
     const double* o = d.origin + 3 * cl;
     const double ox = o[0] + cell_centre(loc % g.G, g), oy = o[1] + cell_centre((loc / g.G) % g.G, g);
     const double oz = o[2] + cell_centre(loc / (g.G * g.G), g);
+    for (int k = lane; k < n; k += 32) {
+        const int e = a[k];
+        buf[w][k] = e;
+        boct[w][k] = (unsigned char)((d.x[e] >= ox ? 1 : 0) | (d.x[np + e] >= oy ? 2 : 0) | (d.x[2 * np + e] >= oz ? 4 : 0));
+    }
+    __syncwarp();
+    if (lane < 9) {
+        int cnt = 0;
+        for (int q = 0; q < n; ++q) cnt += boct[w][q] < lane;
+        d.cell_oct[c * 9 + lane] = cnt;
+    }
     V4* cp = reinterpret_cast<V4*>(d.cpos) + (size_t)c * kCellCap;
     for (int k = lane; k < n; k += 32) {
-        const int e = buf[w][k];
+        const int e = buf[w][k], oc = boct[w][k];
         int r = 0;
-        for (int q = 0; q < n; ++q) r += buf[w][q] < e;
+        for (int q = 0; q < n; ++q) r += (boct[w][q] < oc) || (boct[w][q] == oc && buf[w][q] < e);
         a[r] = e;
-        using R = typename Tr<PREC>::R;
         V4 p;
         p.x = (R)(d.x[e] - ox);
         p.y = (R)(d.x[np + e] - oy);
@@ -111,46 +126,117 @@ template <int PREC> __global__ void k_cell_sort(const Dev d) {
     }
 }
 
-// The 27 neighbour cells of home cell c (those off the grid count as empty): their ids and
-// the prefix sums of their counts. Every thread of the CTA calls this.
-__device__ __forceinline__ int stencil(const Dev& d, int c, int cl, int* scell, int* pref) {
-    const CellGrid g = d.grid[cl];
+// The octant box of home cell c: the 27 cells around it, each split into its 2 x 2 x 2 octants of
+// side h/2 >= rcut/2, form a 6 x 6 x 6 box of octants, numbered t = (Z * 6 + Y) * 6 + X. For each
+// the source slot of its atoms (s_src) and the exclusive prefix of the counts in that order
+// (s_pref[0..216]). Off-grid cells are empty. Every thread of the CTA calls this.
+__device__ __forceinline__ int octant_box(const Dev& d, int c, const CellGrid& g, int* s_src, int* s_cnt,
+                                          int* s_pref) {
     const int loc = c - g.off, cx = loc % g.G, cy = (loc / g.G) % g.G, cz = loc / (g.G * g.G);
-    if (threadIdx.x < 27) {
-        const int k = threadIdx.x;
-        const int x = cx + k % 3 - 1, y = cy + (k / 3) % 3 - 1, z = cz + k / 9 - 1;
-        int id = -1, n = 0;
+    for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {
+        const int X = t % kBox, Y = (t / kBox) % kBox, Z = t / (kBox * kBox);
+        const int x = cx + X / 2 - 1, y = cy + Y / 2 - 1, z = cz + Z / 2 - 1;
+        int n = 0, src = 0;
         if (x >= 0 && x < g.G && y >= 0 && y < g.G && z >= 0 && z < g.G) {
-            id = g.off + (z * g.G + y) * g.G + x;
-            n = min(d.cell_count[id], kCellCap);
+            const int nc = g.off + (z * g.G + y) * g.G + x, o = (X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2);
+            const int s0 = d.cell_oct[nc * 9 + o];
+            n = d.cell_oct[nc * 9 + o + 1] - s0;
+            src = nc * kCellCap + s0;
         }
-        scell[k] = id;
-        pref[k + 1] = n;
+        s_src[t] = src;
+        s_cnt[t] = n;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        pref[0] = 0;
-        for (int k = 0; k < 27; ++k) pref[k + 1] += pref[k];
+    if (threadIdx.x < 32) {  // exclusive scan of the 216 counts, 7 per lane
+        const int lane = threadIdx.x;
+        int v[7], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const int t = lane * 7 + q;
+            v[q] = t < kBoxN ? s_cnt[t] : 0;
+            sum += v[q];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const int t = lane * 7 + q;
+            if (t < kBoxN) s_pref[t] = run;
+            run += v[q];
+        }
+        if (lane == 31) s_pref[kBoxN] = incl;
     }
     __syncthreads();
-    return pref[27];
+    return s_pref[kBoxN];
 }
 
-// Stage entries e0 .. e0 + ne - 1 of the neighbour list: cell-slot data from src (offsets from
-// the neighbour cell's centre), moved to the home cell's centre by the exact (k - l) h.
+// Stage entries e0 .. e0 + ne - 1 of the octant box (one octant per thread), moved from their
+// cell's centre to the home cell's centre by the exact (k - l) h.
 template <class V4, class R>
-__device__ __forceinline__ void gather(const V4* __restrict__ src, const int* scell, const int* pref, R h, int e0,
-                                       int ne, V4* spos) {
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const int q = e0 + e;
-        int k = 0;
-        while (pref[k + 1] <= q) ++k;
-        V4 p = src[(size_t)scell[k] * kCellCap + (q - pref[k])];
-        p.x += (R)(k % 3 - 1) * h;
-        p.y += (R)((k / 3) % 3 - 1) * h;
-        p.z += (R)(k / 9 - 1) * h;
-        spos[e] = p;
+__device__ __forceinline__ void gather_box(const V4* __restrict__ src, const int* s_src, const int* s_pref, R h,
+                                           int e0, int ne, V4* spos) {
+    for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {
+        const int a = max(s_pref[t], e0), b = min(s_pref[t + 1], e0 + ne);
+        if (a >= b) continue;
+        const R sx = (R)((t % kBox) / 2 - 1) * h, sy = (R)(((t / kBox) % kBox) / 2 - 1) * h;
+        const R sz = (R)((t / (kBox * kBox)) / 2 - 1) * h;
+        const V4* from = src + s_src[t] - s_pref[t];
+#pragma unroll 2
+        for (int q = a; q < b; ++q) {
+            V4 p = from[q];
+            p.x += sx;
+            p.y += sy;
+            p.z += sz;
+            spos[q - e0] = p;
+        }
     }
+}
+
+// One home octant per warp: its atoms (cell slots s0 + r0 .. s0 + r0 + nb - 1), the staged place of
+// its octant (for the self test) and the lane layout: nb i-slots times J = 32 / nb j-groups.
+struct OctWarp {
+    int o, s0, nb, J, is, jg, home_t;
+    bool act;
+};
+__device__ __forceinline__ OctWarp oct_warp(const Dev& d, int c, int r0) {
+    OctWarp q;
+    const int lane = threadIdx.x & 31;
+    q.o = threadIdx.x >> 5;
+    q.s0 = d.cell_oct[c * 9 + q.o];
+    q.nb = min(32, d.cell_oct[c * 9 + q.o + 1] - q.s0 - r0);
+    q.J = q.nb > 0 ? 32 / q.nb : 1;
+    q.is = q.nb > 0 ? lane % q.nb : 0;
+    q.jg = q.nb > 0 ? lane / q.nb : 0;
+    q.act = q.nb > 0 && q.jg < q.J;
+    const int ox = q.o & 1, oy = (q.o >> 1) & 1, oz = q.o >> 2;
+    q.home_t = ((2 + oz) * kBox + 2 + oy) * kBox + 2 + ox;
+    return q;
+}
+// Blocks of 32 home atoms that the warp with the fullest octant needs (the same for every warp, so
+// that the staging barriers line up).
+__device__ __forceinline__ int oct_blocks(const Dev& d, int c) {
+    int m = 0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) m = max(m, d.cell_oct[c * 9 + o + 1] - d.cell_oct[c * 9 + o]);
+    return (m + 31) / 32;
+}
+// The 25 runs of the home octant's 5 x 5 x 5 neighbour octants (5 octants along x are adjacent in
+// the staged order), clipped to the staged chunk [e0, e0 + ne): local [lo, hi) per run, written by
+// the warp's lanes into its row of the run table.
+__device__ __forceinline__ void oct_runs(const int* s_pref, int o, int e0, int ne, int2* runs) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 25) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2, rz = lane / 5, ry = lane % 5;
+        const int base = ((oz + rz) * kBox + oy + ry) * kBox + ox;
+        const int a = max(s_pref[base], e0) - e0, b = min(s_pref[base + 5], e0 + ne) - e0;
+        runs[lane] = make_int2(a, max(a, b));
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------- density pass
@@ -160,66 +246,68 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
     using V4 = typename Tr<PREC>::V4;
     constexpr int TJ = CellChunk<PREC>::TJ;
     __shared__ V4 spos[TJ];
-    __shared__ int scell[27], pref[28];
-    __shared__ double part[kCellThreads];
+    __shared__ int s_src[kBoxN], s_cnt[kBoxN], s_pref[kBoxN + 1];
+    __shared__ double part[8][32];
+    __shared__ int2 s_runs[8][25];
     pdl_launch_dependents();
     pdl_wait();
     const int c = d.cell_order[blockIdx.x];
-    const int hc = min(d.cell_count[c], kCellCap);
-    if (hc == 0) return;
+    if (d.cell_count[c] == 0) return;
     const int cl = d.cell_cl[c];
+    const CellGrid g = d.grid[cl];
     const V4* cp = reinterpret_cast<const V4*>(d.cpos);
-    const int M = stencil(d, c, cl, scell, pref);
-    const R rc2 = (R)d.pot.rcut2, h = (R)d.grid[cl].h;
+    const int M = octant_box(d, c, g, s_src, s_cnt, s_pref);
+    const R rc2 = (R)d.pot.rcut2, h = (R)g.h;
     const int mexp = d.pot.m;
-    const int* home = d.cell_atoms + (size_t)c * kCellCap;
-    for (int r0 = 0; r0 < hc; r0 += kCellThreads) {
-        const int nb = min(kCellThreads, hc - r0), J = kCellThreads / nb;
-        const int t = threadIdx.x, is = t % nb, jg = t / nb;
-        const bool act = jg < J;
-        const int i = home[r0 + is];
-        const int self = pref[13] + r0 + is;  // the home cell is stencil entry 13
-        const V4 pi = cp[(size_t)c * kCellCap + r0 + is];
+    const int nblk = oct_blocks(d, c), lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int blk = 0; blk < nblk; ++blk) {
+        const OctWarp q = oct_warp(d, c, blk * 32);
+        const int slot = q.s0 + blk * 32 + q.is;
+        const V4 pi = q.nb > 0 ? cp[(size_t)c * kCellCap + slot] : V4{};
+        const int self = s_pref[q.home_t] + blk * 32 + q.is;
         f2sum facc = {0.f, 0.f};
         double racc = 0.0;
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
-            gather(cp, scell, pref, h, e0, ne, spos);
+            gather_box(cp, s_src, s_pref, h, e0, ne, spos);
             __syncthreads();
-            if (!act) continue;
-            // this j-group's contiguous share of the chunk, summed in spans of kSpan terms
-            const int per = (ne + J - 1) / J, lo = min(ne, jg * per), hi = min(ne, lo + per);
+            oct_runs(s_pref, q.o, e0, ne, s_runs[w]);
+            if (!q.act) continue;
             const int selfl = self - e0;
-            for (int b = lo; b < hi; b += kSpan) {
-                const int stop = min(hi, b + kSpan);
-                R tacc = R(0);
+#pragma unroll 1
+            for (int run = 0; run < 25; ++run) {
+                    const int2 ab = s_runs[w][run];
+                    const int L = ab.y - ab.x, per = (L + q.J - 1) / q.J;
+                    const int lo = ab.x + min(L, q.jg * per), hi = ab.x + min(L, q.jg * per + per);
+                    R tacc = R(0);
 #pragma unroll 4
-                for (int e = b; e < stop; ++e) {
-                    const V4 p = spos[e];
-                    const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
-                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
-                    if (SPECIAL) {
-                        const R inv = inv_r2(r2);
-                        tacc = fma(inv * inv, inv, tacc);
-                    } else {
-                        const R ir = inv_r(r2);
-                        tacc += rpow(ir * ir, ir, mexp);
+                    for (int e = lo; e < hi; ++e) {
+                        const V4 p = spos[e];
+                        const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+                        R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                        r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
+                        if (SPECIAL) {
+                            const R inv = inv_r2(r2);
+                            tacc = fma(inv * inv, inv, tacc);
+                        } else {
+                            const R ir = inv_r(r2);
+                            tacc += rpow(ir * ir, ir, mexp);
+                        }
                     }
+                    if (PREC == 1)
+                        facc = f2_add(facc, (float)tacc);
+                    else
+                        racc += (double)tacc;
                 }
-                if (PREC == 1)
-                    facc = f2_add(facc, (float)tacc);
-                else
-                    racc += (double)tacc;
-            }
         }
         if (PREC == 1) racc = (double)facc.hi + (double)facc.lo;
-        part[t] = racc;
-        __syncthreads();
-        if (jg == 0) {
-            double tot = part[is];
-            for (int g = 1; g < J; ++g) tot += part[g * nb + is];
+        part[w][lane] = racc;
+        __syncwarp();
+        if (q.nb > 0 && q.jg == 0) {
+            double tot = part[w][q.is];
+            for (int k = 1; k < q.J; ++k) tot += part[w][k * q.nb + q.is];
+            const int i = d.cell_atoms[(size_t)c * kCellCap + slot];
             const double rho = tot * d.pot.am;
             d.rho[i] = rho;
             V4 p = pi;
@@ -231,9 +319,10 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
             } else {
                 p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
             }
-            reinterpret_cast<V4*>(d.cposg)[(size_t)c * kCellCap + r0 + is] = p;
+            reinterpret_cast<V4*>(d.cposg)[(size_t)c * kCellCap + slot] = p;
             if (obs) d.eatom[2 * i] = -d.pot.eps * d.pot.c * sqrt(rho);
         }
+        __syncwarp();
     }
 }
 
@@ -243,115 +332,123 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
 // step unless this is the chunk's last step or the thermostat is Berendsen (whose kernel
 // rescales and starts the next step).
 template <int PREC, int SPECIAL, int ENERGY>
-__global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_force(const Dev d, int mode, int k_local, int last) {
+__global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2)
+    k_cell_force(const Dev d, int mode, int k_local, int last) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     constexpr int TJ = CellChunk<PREC>::TJ;
     __shared__ V4 spos[TJ];
-    __shared__ int scell[27], pref[28];
-    __shared__ R partf[kCellThreads][3];
-    __shared__ double parte[ENERGY ? kCellThreads : 1];
+    __shared__ int s_src[kBoxN], s_cnt[kBoxN], s_pref[kBoxN + 1];
+    __shared__ R partf[8][32][3];
+    __shared__ double parte[ENERGY ? 8 : 1][32];
+    __shared__ int2 s_runs[8][25];
     pdl_launch_dependents();
     pdl_wait();
     const int c = d.cell_order[blockIdx.x];
-    const int hc = min(d.cell_count[c], kCellCap);
-    if (hc == 0) return;
+    if (d.cell_count[c] == 0) return;
     const int cl = d.cell_cl[c];
+    const CellGrid g = d.grid[cl];
     const V4* pg = reinterpret_cast<const V4*>(d.cposg);
-    const int M = stencil(d, c, cl, scell, pref);
+    const int M = octant_box(d, c, g, s_src, s_cnt, s_pref);
     const R A = (R)d.pot.A9;
-    const R rc2 = (R)d.pot.rcut2, h = (R)d.grid[cl].h;
+    const R rc2 = (R)d.pot.rcut2, h = (R)g.h;
     const int nexp = d.pot.n, mexp = d.pot.m;
-    const int* home = d.cell_atoms + (size_t)c * kCellCap;
-    for (int r0 = 0; r0 < hc; r0 += kCellThreads) {
-        const int nb = min(kCellThreads, hc - r0), J = kCellThreads / nb;
-        const int t = threadIdx.x, is = t % nb, jg = t / nb;
-        const bool act = jg < J;
-        const int i = home[r0 + is];
-        const int self = pref[13] + r0 + is;
-        const V4 pi = pg[(size_t)c * kCellCap + r0 + is];
+    const int nblk = oct_blocks(d, c), lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int blk = 0; blk < nblk; ++blk) {
+        const OctWarp q = oct_warp(d, c, blk * 32);
+        const int slot = q.s0 + blk * 32 + q.is;
+        const V4 pi = q.nb > 0 ? pg[(size_t)c * kCellCap + slot] : V4{};
+        const int self = s_pref[q.home_t] + blk * 32 + q.is;
         R fx = R(0), fy = R(0), fz = R(0);
         double ea = 0.0;
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
-            gather(pg, scell, pref, h, e0, ne, spos);
+            gather_box(pg, s_src, s_pref, h, e0, ne, spos);
             __syncthreads();
-            if (!act) continue;
-            const int per = (ne + J - 1) / J, lo = min(ne, jg * per), hi = min(ne, lo + per);
+            oct_runs(s_pref, q.o, e0, ne, s_runs[w]);
+            if (!q.act) continue;
             const int selfl = self - e0;
-            for (int b = lo; b < hi; b += kSpan) {
-                const int stop = min(hi, b + kSpan);
-                R sx = R(0), sy = R(0), sz = R(0), se = R(0);
+#pragma unroll 1
+            for (int run = 0; run < 25; ++run) {
+                    const int2 ab = s_runs[w][run];
+                    const int L = ab.y - ab.x, per = (L + q.J - 1) / q.J;
+                    const int lo = ab.x + min(L, q.jg * per), hi = ab.x + min(L, q.jg * per + per);
+                    R sx = R(0), sy = R(0), sz = R(0), se = R(0);
 #pragma unroll 4
-                for (int e = b; e < stop; ++e) {
-                    const V4 p = spos[e];
-                    const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
-                    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
-                    const R ir = inv_r(r2);
-                    const R inv = ir * ir;
-                    R coef, rn;
-                    if (SPECIAL) {
-                        const R inv2 = inv * inv, inv4 = inv2 * inv2;
-                        coef = inv4 * fma(A, inv * ir, -(pi.w + p.w));
-                        rn = inv4 * ir;
-                    } else {
-                        rn = rpow(inv, ir, nexp);
-                        const R rm = rpow(inv, ir, mexp);
-                        coef = inv * (A * rn - (pi.w + p.w) * rm);
+                    for (int e = lo; e < hi; ++e) {
+                        const V4 p = spos[e];
+                        const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+                        R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                        r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
+                        const R ir = inv_r(r2);
+                        const R inv = ir * ir;
+                        R coef, rn;
+                        if (SPECIAL) {
+                            const R inv2 = inv * inv, inv4 = inv2 * inv2;
+                            coef = inv4 * fma(A, inv * ir, -(pi.w + p.w));
+                            rn = inv4 * ir;
+                        } else {
+                            rn = rpow(inv, ir, nexp);
+                            const R rm = rpow(inv, ir, mexp);
+                            coef = inv * (A * rn - (pi.w + p.w) * rm);
+                        }
+                        sx = fma(coef, dx, sx);
+                        sy = fma(coef, dy, sy);
+                        sz = fma(coef, dz, sz);
+                        if (ENERGY) se += rn;
                     }
-                    sx = fma(coef, dx, sx);
-                    sy = fma(coef, dy, sy);
-                    sz = fma(coef, dz, sz);
-                    if (ENERGY) se += rn;
+                    fx += sx;
+                    fy += sy;
+                    fz += sz;
+                    if (ENERGY) ea += (double)se;
                 }
-                fx += sx;
-                fy += sy;
-                fz += sz;
-                if (ENERGY) ea += (double)se;
+        }
+        partf[w][lane][0] = fx;
+        partf[w][lane][1] = fy;
+        partf[w][lane][2] = fz;
+        if (ENERGY) parte[w][lane] = ea;
+        __syncwarp();
+        if (q.nb > 0 && q.jg == 0) {
+            R Fx = partf[w][q.is][0], Fy = partf[w][q.is][1], Fz = partf[w][q.is][2];
+            double Ep = ENERGY ? parte[w][q.is] : 0.0;
+            for (int k = 1; k < q.J; ++k) {
+                Fx += partf[w][k * q.nb + q.is][0];
+                Fy += partf[w][k * q.nb + q.is][1];
+                Fz += partf[w][k * q.nb + q.is][2];
+                if (ENERGY) Ep += parte[w][k * q.nb + q.is];
+            }
+            const int i = d.cell_atoms[(size_t)c * kCellCap + slot];
+            const int np = d.npad;
+            R* fo = reinterpret_cast<R*>(d.f);
+            fo[i] = Fx;
+            fo[np + i] = Fy;
+            fo[2 * np + i] = Fz;
+            if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+            if (ENERGY) d.eatom[2 * i + 1] = Ep;
+            if (mode == 2) {
+                const Run& r = *d.run;
+                const double hs = d.hs[i];
+                const double vx = fma(hs, (double)Fx, d.v[i]);
+                const double vy = fma(hs, (double)Fy, d.v[np + i]);
+                const double vz = fma(hs, (double)Fz, d.v[2 * np + i]);
+                d.v[i] = vx;
+                d.v[np + i] = vy;
+                d.v[2 * np + i] = vz;
+                if (r.kind != 2) {  // Berendsen: the rescale kernel records and starts the step
+                    if (ENERGY) {   // observables at the end of this step, before the next begins
+                        for (int k = 0; k < 3; ++k) d.obs_x[3 * i + k] = d.x[k * np + i];
+                        d.obs_v[3 * i] = vx;
+                        d.obs_v[3 * i + 1] = vy;
+                        d.obs_v[3 * i + 2] = vz;
+                    }
+                    if (!last)
+                        begin_step<PREC>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, (double)Fx,
+                                         (double)Fy, (double)Fz, k_local + 1);
+                }
             }
         }
-        partf[t][0] = fx;
-        partf[t][1] = fy;
-        partf[t][2] = fz;
-        if (ENERGY) parte[t] = ea;
-        __syncthreads();
-        if (jg != 0) continue;
-        R Fx = partf[is][0], Fy = partf[is][1], Fz = partf[is][2];
-        double Ep = ENERGY ? parte[is] : 0.0;
-        for (int g = 1; g < J; ++g) {
-            Fx += partf[g * nb + is][0];
-            Fy += partf[g * nb + is][1];
-            Fz += partf[g * nb + is][2];
-            if (ENERGY) Ep += parte[g * nb + is];
-        }
-        const int np = d.npad;
-        R* fo = reinterpret_cast<R*>(d.f);
-        fo[i] = Fx;
-        fo[np + i] = Fy;
-        fo[2 * np + i] = Fz;
-        if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
-        if (ENERGY) d.eatom[2 * i + 1] = Ep;
-        if (mode != 2) continue;
-        const Run& r = *d.run;
-        const double hs = d.hs[i];
-        const double vx = fma(hs, (double)Fx, d.v[i]);
-        const double vy = fma(hs, (double)Fy, d.v[np + i]);
-        const double vz = fma(hs, (double)Fz, d.v[2 * np + i]);
-        d.v[i] = vx;
-        d.v[np + i] = vy;
-        d.v[2 * np + i] = vz;
-        if (r.kind == 2) continue;  // Berendsen: the rescale kernel records and starts the step
-        if (ENERGY) {               // observables at the end of this step, before the next begins
-            for (int k = 0; k < 3; ++k) d.obs_x[3 * i + k] = d.x[k * np + i];
-            d.obs_v[3 * i] = vx;
-            d.obs_v[3 * i + 1] = vy;
-            d.obs_v[3 * i + 2] = vz;
-        }
-        if (!last)
-            begin_step<PREC>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, (double)Fx, (double)Fy,
-                             (double)Fz, k_local + 1);
+        __syncwarp();
     }
 }
 

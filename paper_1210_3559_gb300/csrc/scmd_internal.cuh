@@ -127,6 +127,7 @@ struct Dev {
     const int32_t* cell_order; // [n_cells] pair-pass launch order: cells nearest their cluster's centre first
     int32_t* cell_count; // [n_cells] atoms binned into each cell (may exceed kCellCap: overflow)
     int32_t* cell_atoms; // [n_cells][kCellCap] padded atom indices, ascending within a cell
+    int32_t* cell_oct;   // [n_cells][9] first place of each octant of the cell in its sorted slots, then the count
     void* cpos;          // [n_cells][kCellCap] V4 (x - cell centre, 0) in the pass precision
     void* cposg;         // [n_cells][kCellCap] V4 (x - cell centre, B6 rho^-1/2), density pass
     double* eatom;       // [npad][2] per-atom -eps c sqrt(rho_i) and sum_j r_ij^-n
