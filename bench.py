@@ -10,7 +10,8 @@ default --steps 400 covers the whole 2e5-step cooling schedule. L2 is flushed (a
 write) before every timed iteration and that flush is outside the timed events.
 
 Other configs (--config): ni6000, ni20000 (all pairs, MIXED), ni50000 (rcut = 8.8 A on the
-cell list, MIXED), ni147 (FP64 NVE), batched512 (512 clusters of 55..2000 atoms).
+cell list, MIXED), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one context), batched512 (512
+clusters of 55..2000 atoms).
 
 value  : atom-timesteps/s over all ranks (sum of atoms x MD steps / max rank time).
 e2e    : the same metric through the C ABI with host buffers every iteration
@@ -87,6 +88,14 @@ def workload(name: str, rank: int):
         return dict(sizes=[147], pos=pos, vel=vel, mass=m, prec="fp64", dt=1.0, melt_steps=0, melt_T=0.0,
                     schedule=None, gamma=0.0, seed=1 + seed_off,
                     desc="Ni147 Mackay icosahedron, 1500 K, NVE dt=1 fs, FP64")
+    if name == "ni147x64":  # 64 independent replicas of the Ni147 case in one context
+        p1 = inputs.mackay_icosahedron(3, 2.49)
+        m1 = inputs.masses(147)
+        pos = np.concatenate([p1] * 64)
+        vel = np.concatenate([inputs.maxwell_boltzmann(p1, m1, 1500.0, seed=1 + 100 * b + seed_off) for b in range(64)])
+        return dict(sizes=[147] * 64, pos=pos, vel=vel, mass=inputs.masses(len(pos)), prec="fp64", dt=1.0,
+                    melt_steps=0, melt_T=0.0, schedule=None, gamma=0.0, seed=1 + seed_off,
+                    desc="64 replicas of Ni147 Mackay icosahedron, 1500 K, NVE dt=1 fs, FP64")
     if name == "batched512":
         sizes = inputs.batched_sizes(512, 55, 2000, seed=5 + seed_off)
         parts, vels = [], []
@@ -231,7 +240,8 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="ni2000", choices=["ni2000", "ni6000", "ni20000", "ni50000", "ni147", "batched512"])
+    ap.add_argument("--config", default="ni2000", choices=["ni2000", "ni6000", "ni20000", "ni50000", "ni147", "ni147x64",
+                                                       "batched512"])
     ap.add_argument("--md-steps", type=int, default=500, help="MD steps per timed iteration")
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
     ap.add_argument("--no-tune", action="store_true")

@@ -229,6 +229,36 @@ def test_berendsen_trajectory_short_horizon(scmd, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_trajectory_within_oracle_sensitivity_bound(scmd, prec):
+    """The GPU trajectory stays within the divergence that the dynamics itself produces from an error
+    of the precision's size. The oracle is run twice, once with one coordinate moved by d0 = 1e-10 A;
+    its separation d(t) gives the growth of small errors. The GPU run may then deviate from the oracle
+    by at most 100 d(t) e0 / d0, with e0 = 1e-15 R for FP64 (R = the cluster radius) and 1e-6 A for
+    MIXED (its FP32 pair coordinates)."""
+    pos = inputs.mackay_icosahedron(3, 2.49)
+    m = inputs.masses(147)
+    vel = inputs.maxwell_boltzmann(pos, m, 1500.0, seed=1)
+    checkpoints = [250, 500, 1000, 2000]
+    a = oracle_batch([147], pos, vel)
+    pert = pos.copy()
+    d0 = 1e-10
+    pert[17, 0] += d0
+    b = oracle_batch([147], pert, vel)
+    ctx = make(scmd, [147], pos, vel, prec=prec, graph_chunk=250)
+    e0 = 1e-15 * np.linalg.norm(pos, axis=1).max() if prec == FP64 else 1e-6
+    done = 0
+    for t in checkpoints:
+        a.run(t - done, 1.0)
+        b.run(t - done, 1.0)
+        scmd.md_step(ctx, t - done, 1.0)
+        done = t
+        growth = max(np.max(np.abs(b.pos - a.pos)), d0) / d0
+        p, _, _ = scmd.md_get_state(ctx)
+        dev = np.max(np.abs(p - a.pos))
+        assert dev <= 100 * growth * e0, (t, dev, growth)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_checkpoint_resume_is_bitwise(scmd, prec):
     pos = inputs.fcc_sphere(200)
     vel = inputs.maxwell_boltzmann(pos, inputs.masses(200), 1500.0, seed=6)
