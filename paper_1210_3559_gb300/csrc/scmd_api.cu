@@ -81,6 +81,7 @@ struct md_ctx {
     CellGrid* d_grid = nullptr;
     int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr, *d_cell_order = nullptr;
     int32_t* d_cell_oct = nullptr;
+    uint8_t* d_cell_obyte = nullptr;
     void *d_cpos = nullptr, *d_cposg = nullptr;
     double *d_eatom = nullptr, *d_obs_x = nullptr, *d_obs_v = nullptr;
     // pinned staging
@@ -169,6 +170,7 @@ void fill_dev(md_ctx* c) {
     d.cell_count = c->d_cell_count;
     d.cell_atoms = c->d_cell_atoms;
     d.cell_oct = c->d_cell_oct;
+    d.cell_obyte = c->d_cell_obyte;
     d.cpos = c->d_cpos;
     d.cposg = c->d_cposg;
     d.eatom = c->d_eatom;
@@ -215,6 +217,7 @@ bool make_grids(md_ctx* c, const double* pos, const double* mass) {
         if ((double)hf < 2.0 * E / G) hf = std::nextafter(hf, 1e30f);
         g.h = (double)hf;
         g.E = 0.5 * G * g.h;
+        g.inv_h = 1.0 / g.h;
         if (1.25 * 4.0 * g.h * g.h * g.h / (a * a * a) > kCellCap) return false;
         c->grids[b] = g;
         off += G * G * G;
@@ -391,7 +394,7 @@ void free_all(md_ctx* c) {
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
-                    c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct};
+                    c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -690,6 +693,7 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         CKC(cudaMalloc(&c->d_cell_count, sizeof(int32_t) * c->n_cells));
         CKC(cudaMalloc(&c->d_cell_atoms, sizeof(int32_t) * kCellCap * (size_t)c->n_cells));
         CKC(cudaMalloc(&c->d_cell_oct, sizeof(int32_t) * 9 * (size_t)c->n_cells));
+        CKC(cudaMalloc(&c->d_cell_obyte, (size_t)kCellCap * c->n_cells));
         CKC(cudaMemset(c->d_cell_oct, 0, sizeof(int32_t) * 9 * (size_t)c->n_cells));
         CKC(cudaMalloc(&c->d_cpos, (size_t)vec4_size(c) * kCellCap * c->n_cells));
         CKC(cudaMalloc(&c->d_cposg, (size_t)vec4_size(c) * kCellCap * c->n_cells));

@@ -46,7 +46,7 @@ template <> struct CellChunk<0> { static constexpr int TJ = 1024; };  // 32 KB o
 // Cell index along one axis of a coordinate relative to the origin. fmin/fmax come before the
 // conversion: far or non-finite coordinates land in a border cell.
 __device__ __forceinline__ int cell_axis(double rel, const CellGrid& g) {
-    return (int)fmin(fmax(floor((rel + g.E) / g.h), 0.0), (double)(g.G - 1));
+    return (int)fmin(fmax(floor((rel + g.E) * g.inv_h), 0.0), (double)(g.G - 1));
 }
 // Centre of cell k along one axis, relative to the origin (exact: h is a binary32 value).
 __device__ __forceinline__ double cell_centre(int k, const CellGrid& g) { return -g.E + (k + 0.5) * g.h; }
@@ -58,8 +58,12 @@ __global__ void k_cell_clear(const Dev d) {
         d.cell_count[c] = 0;
 }
 
-// One thread per padded atom: its cell (from the FP64 state), and an atomic slot in it.
-__global__ void k_cell_bin(const Dev d) {
+// One thread per padded atom: its cell (from the FP64 state), an atomic slot in it, and at that
+// slot its octant of the cell (the sign of its offset from the centre per axis) and the offset itself
+// rounded once to the pass precision (in the cposg slots, free until the density pass).
+template <int PREC> __global__ void k_cell_bin(const Dev d) {
+    using V4 = typename Tr<PREC>::V4;
+    using R = typename Tr<PREC>::R;
     pdl_launch_dependents();
     pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,22 +73,30 @@ __global__ void k_cell_bin(const Dev d) {
     const CellGrid g = d.grid[cl];
     const double* o = d.origin + 3 * cl;
     const int np = d.npad;
-    const int cx = cell_axis(d.x[i] - o[0], g), cy = cell_axis(d.x[np + i] - o[1], g);
-    const int cz = cell_axis(d.x[2 * np + i] - o[2], g);
+    const double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
+    const int cx = cell_axis(x - o[0], g), cy = cell_axis(y - o[1], g), cz = cell_axis(z - o[2], g);
     const int c = g.off + (cz * g.G + cy) * g.G + cx;
     const int slot = atomicAdd(d.cell_count + c, 1);
-    if (slot < kCellCap)
-        d.cell_atoms[(size_t)c * kCellCap + slot] = i;
-    else
+    if (slot >= kCellCap) {
         atomicOr(d.status, 2);
+        return;
+    }
+    const double ox = o[0] + cell_centre(cx, g), oy = o[1] + cell_centre(cy, g), oz = o[2] + cell_centre(cz, g);
+    const size_t k = (size_t)c * kCellCap + slot;
+    d.cell_atoms[k] = i;
+    d.cell_obyte[k] = (uint8_t)((x >= ox ? 1 : 0) | (y >= oy ? 2 : 0) | (z >= oz ? 4 : 0));
+    V4 p;
+    p.x = (R)(x - ox);
+    p.y = (R)(y - oy);
+    p.z = (R)(z - oz);
+    p.w = R(0);
+    reinterpret_cast<V4*>(d.cposg)[k] = p;
 }
 
-// One warp per cell. Each atom's octant of the cell (the sign of its offset from the centre per
-// axis) and its rank by (octant, atom index) give its place; the offset is stored at the same place,
-// and the first place of every octant (plus the count) in cell_oct.
+// One warp per cell: each atom's rank by (octant, atom index) is its place; its offset moves there
+// (cposg -> cpos), and the first place of every octant (plus the count) goes to cell_oct.
 template <int PREC> __global__ void k_cell_sort(const Dev d) {
     using V4 = typename Tr<PREC>::V4;
-    using R = typename Tr<PREC>::R;
     __shared__ int buf[kCellThreads / 32][kCellCap];
     __shared__ unsigned char boct[kCellThreads / 32][kCellCap];
     pdl_launch_dependents();
@@ -93,17 +105,11 @@ template <int PREC> __global__ void k_cell_sort(const Dev d) {
     const int c = blockIdx.x * (kCellThreads / 32) + w;
     if (c >= d.n_cells) return;
     const int n = min(d.cell_count[c], kCellCap);
-    int* a = d.cell_atoms + (size_t)c * kCellCap;
-    const int cl = d.cell_cl[c];
-    const CellGrid g = d.grid[cl];
-    const int loc = c - g.off, np = d.npad;
-    const double* o = d.origin + 3 * cl;
-    const double ox = o[0] + cell_centre(loc % g.G, g), oy = o[1] + cell_centre((loc / g.G) % g.G, g);
-    const double oz = o[2] + cell_centre(loc / (g.G * g.G), g);
+    const size_t base = (size_t)c * kCellCap;
+    int* a = d.cell_atoms + base;
     for (int k = lane; k < n; k += 32) {
-        const int e = a[k];
-        buf[w][k] = e;
-        boct[w][k] = (unsigned char)((d.x[e] >= ox ? 1 : 0) | (d.x[np + e] >= oy ? 2 : 0) | (d.x[2 * np + e] >= oz ? 4 : 0));
+        buf[w][k] = a[k];
+        boct[w][k] = d.cell_obyte[base + k];
     }
     __syncwarp();
     if (lane < 9) {
@@ -111,18 +117,14 @@ template <int PREC> __global__ void k_cell_sort(const Dev d) {
         for (int q = 0; q < n; ++q) cnt += boct[w][q] < lane;
         d.cell_oct[c * 9 + lane] = cnt;
     }
-    V4* cp = reinterpret_cast<V4*>(d.cpos) + (size_t)c * kCellCap;
+    const V4* from = reinterpret_cast<const V4*>(d.cposg) + base;
+    V4* cp = reinterpret_cast<V4*>(d.cpos) + base;
     for (int k = lane; k < n; k += 32) {
         const int e = buf[w][k], oc = boct[w][k];
         int r = 0;
         for (int q = 0; q < n; ++q) r += (boct[w][q] < oc) || (boct[w][q] == oc && buf[w][q] < e);
         a[r] = e;
-        V4 p;
-        p.x = (R)(d.x[e] - ox);
-        p.y = (R)(d.x[np + e] - oy);
-        p.z = (R)(d.x[2 * np + e] - oz);
-        p.w = R(0);
-        cp[r] = p;
+        cp[r] = from[k];
     }
 }
 
@@ -508,7 +510,8 @@ __global__ void k_cell_ke(const Dev d) {
 cudaError_t launch_cell_build(const Dev& d, cudaStream_t s) {
     cudaError_t e = launch_ex(k_cell_clear, (d.n_cells + 255) / 256, 256, 0, 0, s, d);
     if (e != cudaSuccess) return e;
-    e = launch_ex(k_cell_bin, (d.npad + 255) / 256, 256, 0, 0, s, d);
+    e = d.prec == 1 ? launch_ex(k_cell_bin<1>, (d.npad + 255) / 256, 256, 0, 0, s, d)
+                    : launch_ex(k_cell_bin<0>, (d.npad + 255) / 256, 256, 0, 0, s, d);
     if (e != cudaSuccess) return e;
     return d.prec == 1 ? launch_ex(k_cell_sort<1>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d)
                        : launch_ex(k_cell_sort<0>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d);

@@ -56,7 +56,7 @@ struct Item {
 // with |k - l| <= 1 per axis, is exact in FP32.
 struct CellGrid {
     int32_t G, off;
-    double h, E;
+    double h, E, inv_h;
 };
 
 // Derived potential constants.
@@ -128,8 +128,10 @@ struct Dev {
     int32_t* cell_count; // [n_cells] atoms binned into each cell (may exceed kCellCap: overflow)
     int32_t* cell_atoms; // [n_cells][kCellCap] padded atom indices, ascending within a cell
     int32_t* cell_oct;   // [n_cells][9] first place of each octant of the cell in its sorted slots, then the count
+    uint8_t* cell_obyte; // [n_cells][kCellCap] octant of each binned atom, in bin (unsorted) order
     void* cpos;          // [n_cells][kCellCap] V4 (x - cell centre, 0) in the pass precision
-    void* cposg;         // [n_cells][kCellCap] V4 (x - cell centre, B6 rho^-1/2), density pass
+    void* cposg;         // [n_cells][kCellCap] V4 (x - cell centre, B6 rho^-1/2), density pass (between the
+                         // bin and sort kernels: the offsets in bin order)
     double* eatom;       // [npad][2] per-atom -eps c sqrt(rho_i) and sum_j r_ij^-n
     double* obs_x;       // [npad][3] positions at an observation (end of the step)
     double* obs_v;       // [npad][3] velocities at an observation
