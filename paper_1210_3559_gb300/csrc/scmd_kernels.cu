@@ -30,6 +30,15 @@
 #include "scmd_device.cuh"
 
 namespace scmd {
+// The j-range of an item is split over the warps of its thread-block cluster in units of
+// 32 / kSplit<PREC> atoms. FP32 passes use whole 32-atom tiles. FP64 passes use 4-atom units: an FP64
+// warp instruction occupies an SM sub-partition's FP64 pipe for ~68 cycles on this part, so a whole
+// tile of pairs is ~20 us of one warp's work, and a small cluster (a few tiles) needs finer units to
+// spread over more warps.
+template <int PREC> struct SplitOf;
+template <> struct SplitOf<1> { static constexpr int S = 1; };
+template <> struct SplitOf<0> { static constexpr int S = 8; };
+
 // ------------------------------------------------------------- density pass
 // Shared memory: tiles [W][32] V4 | red [W][BI] double | inbox [C][BI] double (read on rank 0)
 template <int PREC, int IPT, int SPECIAL, int CUT>
@@ -53,9 +62,11 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
     const V4* mir = reinterpret_cast<const V4*>(d.mirror);
     const R rc2 = (R)d.pot.rcut2;
     const int mexp = d.pot.m;
-    const int ntile = (it.nj + 31) >> 5;
+    constexpr int S = SplitOf<PREC>::S, L = 32 / S;
+    const int ntile = (it.nj + 31) >> 5, nunit = ntile * S;
     const int Q = C * W, qi = rank * W + warp;
-    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
+    const int u_beg = (int)(((long long)nunit * qi) / Q), u_end = (int)(((long long)nunit * (qi + 1)) / Q);
+    const int t_last = (u_end - 1) / S;  // last tile this warp touches
     const int tdiag = (it.i0 - it.j0) >> 5;
     pdl_wait();  // positions come from the previous kernel
 
@@ -64,7 +75,7 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
     f2sum facc[IPT];
     R sacc[IPT];
     V4 nxt;
-    if (t_beg < t_end) nxt = mir[it.j0 + (t_beg << 5) + lane];
+    if (u_beg < u_end) nxt = mir[it.j0 + ((u_beg / S) << 5) + lane];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const V4 p = mir[it.i0 + lane + 32 * q];
@@ -76,14 +87,19 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
         sacc[q] = R(0);
     }
     V4* tile = tiles + warp * 32;
-    int span = 0;
-    for (int t = t_beg; t < t_end; ++t) {
+    int span = 0, tcur = -1;
+    for (int u = u_beg; u < u_end; ++u) {
+        const int t = u / S, k0 = (u - t * S) * L;
         const int jb = it.j0 + (t << 5);
-        __syncwarp();
-        tile[lane] = nxt;
-        __syncwarp();
-        if (t + 1 < t_end) nxt = mir[jb + 32 + lane];
+        if (S == 1 || t != tcur) {  // stage tile t (the next one is already in flight)
+            __syncwarp();
+            tile[lane] = nxt;
+            __syncwarp();
+            if (t < t_last) nxt = mir[jb + 32 + lane];
+            tcur = t;
+        }
         const int valid = min(32, it.nj - (t << 5));
+        const int k1 = min(k0 + L, valid);
         const bool diag = (t >= tdiag) && (t < tdiag + IPT);
         R tacc[IPT];
 #pragma unroll
@@ -105,16 +121,16 @@ __global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __r
             }                                                                  \
         }                                                                      \
     }
-        if (!diag && valid == 32) {
+        if (!diag && k1 - k0 == L) {
 #pragma unroll 8
-            for (int k = 0; k < 32; ++k) SCMD_DENSITY_BODY(false)
+            for (int k = k0; k < k0 + L; ++k) SCMD_DENSITY_BODY(false)
         } else {
-            for (int k = 0; k < valid; ++k) SCMD_DENSITY_BODY(true)
+            for (int k = k0; k < k1; ++k) SCMD_DENSITY_BODY(true)
         }
 #undef SCMD_DENSITY_BODY
 #pragma unroll
         for (int q = 0; q < IPT; ++q) sacc[q] += tacc[q];
-        if (++span == 4) {
+        if (++span == 4 * S) {
             span = 0;
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
@@ -210,9 +226,11 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     const R A = (R)d.pot.A9;
     const R rc2 = (R)d.pot.rcut2;
     const int nexp = d.pot.n, mexp = d.pot.m;
-    const int ntile = (it.nj + 31) >> 5;
+    constexpr int S = SplitOf<PREC>::S, L = 32 / S;
+    const int ntile = (it.nj + 31) >> 5, nunit = ntile * S;
     const int Q = C * W, qi = rank * W + warp;
-    const int t_beg = (int)(((long long)ntile * qi) / Q), t_end = (int)(((long long)ntile * (qi + 1)) / Q);
+    const int u_beg = (int)(((long long)nunit * qi) / Q), u_end = (int)(((long long)nunit * (qi + 1)) / Q);
+    const int t_last = (u_end - 1) / S;
     const int tdiag = (it.i0 - it.j0) >> 5;
     // epilogue owner: rank 0, thread t < BI owns atom i0 + t
     const bool owner = rank == 0 && threadIdx.x < BI;
@@ -252,7 +270,7 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     R es[IPT];
     double ea[IPT];
     V4 nxt;
-    if (t_beg < t_end) nxt = pg[it.j0 + (t_beg << 5) + lane];
+    if (u_beg < u_end) nxt = pg[it.j0 + ((u_beg / S) << 5) + lane];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const V4 p = pg[it.i0 + lane + 32 * q];
@@ -266,14 +284,19 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
         ea[q] = 0.0;
     }
     V4* tile = tiles + warp * 32;
-    int span = 0;
-    for (int t = t_beg; t < t_end; ++t) {
+    int span = 0, tcur = -1;
+    for (int u = u_beg; u < u_end; ++u) {
+        const int t = u / S, k0 = (u - t * S) * L;
         const int jb = it.j0 + (t << 5);
-        __syncwarp();
-        tile[lane] = nxt;
-        __syncwarp();
-        if (t + 1 < t_end) nxt = pg[jb + 32 + lane];
+        if (S == 1 || t != tcur) {
+            __syncwarp();
+            tile[lane] = nxt;
+            __syncwarp();
+            if (t < t_last) nxt = pg[jb + 32 + lane];
+            tcur = t;
+        }
         const int valid = min(32, it.nj - (t << 5));
+        const int k1 = min(k0 + L, valid);
         const bool diag = (t >= tdiag) && (t < tdiag + IPT);
         R tx[IPT], ty[IPT], tz[IPT], te[IPT];
 #pragma unroll
@@ -304,11 +327,11 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
             if (ENERGY) te[q] += rn;                                           \
         }                                                                      \
     }
-        if (!diag && valid == 32) {
+        if (!diag && k1 - k0 == L) {
 #pragma unroll 8
-            for (int k = 0; k < 32; ++k) SCMD_FORCE_BODY(false)
+            for (int k = k0; k < k0 + L; ++k) SCMD_FORCE_BODY(false)
         } else {
-            for (int k = 0; k < valid; ++k) SCMD_FORCE_BODY(true)
+            for (int k = k0; k < k1; ++k) SCMD_FORCE_BODY(true)
         }
 #undef SCMD_FORCE_BODY
 #pragma unroll
@@ -318,7 +341,7 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
             sz[q] += tz[q];
             if (ENERGY) es[q] += te[q];
         }
-        if (++span == 4) {
+        if (++span == 4 * S) {
             span = 0;
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
