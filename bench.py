@@ -289,7 +289,7 @@ def main():
         cfg.tune = 0
     rcut = w.get("rcut", 0.0)
     ctx = scmd.md_create(cfg, sizes, w["pos"], w["vel"], w["mass"], scmd.sc_params(rcut=rcut))
-    cells = scmd.md_launch_counts(ctx)[0] == 5
+    cells = scmd.md_get_path(ctx) == scmd.MD_PATH_CELLS
     if args.shapes:
         v = [int(x) for x in args.shapes.split(",")]
         scmd.md_set_launch(ctx, 0, *v[0:3])

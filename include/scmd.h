@@ -242,6 +242,10 @@ md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* 
  * steps) and per graph replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);
 
+/* The pair path the context runs (MD_PATH_ALLPAIRS or MD_PATH_CELLS; MD_PATH_AUTO is resolved at
+ * create time) into *path. */
+md_status md_get_path(const md_ctx* ctx, int32_t* path);
+
 /* Last error message of ctx, or of the calling thread's last failed md_create when ctx is NULL. */
 const char* md_last_error(const md_ctx* ctx);
 

@@ -1179,6 +1179,12 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     return MD_OK;
 }
 
+md_status md_get_path(const md_ctx* c, int32_t* path) {
+    if (!c || !path) return MD_ERR_INVALID;
+    *path = c->path == 1 ? MD_PATH_CELLS : MD_PATH_ALLPAIRS;
+    return MD_OK;
+}
+
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
     if (per_step) *per_step = c->path == 1 ? 5 : 2;

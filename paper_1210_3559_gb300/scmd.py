@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
                 "md_autotune": ([_VP, i32], i32),
                 "md_time_passes": ([_VP, i32, _DP, _DP, _DP], i32),
                 "md_launch_counts": ([_VP, P(i32), P(i32)], i32),
+                "md_get_path": ([_VP, P(i32)], i32),
                 "md_last_error": ([_VP], ctypes.c_char_p),
                 "md_destroy": ([_VP], None),
                 "md_philox4x32_10": ([P(u32), P(u32), i32], i32),
@@ -105,7 +106,7 @@ def lib() -> ctypes.CDLL:
 def exported_symbols():
     return ["md_abi_version", "md_create", "md_energy_forces", "md_get_density", "md_step", "md_observables",
             "md_obs_history", "md_clear_history", "md_get_state", "md_set_state", "md_get_forces", "md_recenter",
-            "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts",
+            "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts", "md_get_path",
             "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals",
             "md_energy_forces_noalloc"]
 
@@ -287,6 +288,12 @@ def md_launch_counts(ctx: Context):
     a, b = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().md_launch_counts(ctx.handle, ctypes.byref(a), ctypes.byref(b)), ctx.handle)
     return a.value, b.value
+
+
+def md_get_path(ctx: Context) -> int:
+    p = ctypes.c_int32()
+    _check(lib().md_get_path(ctx.handle, ctypes.byref(p)), ctx.handle)
+    return p.value
 
 
 def md_philox4x32_10(words) -> np.ndarray:

@@ -111,6 +111,7 @@ def test_cells_full_size_parity(scmd, prec):
     pos = lattice(50000, 24)
     vel = inputs.maxwell_boltzmann(pos, inputs.masses(50000), 300.0, seed=3)
     ctx = make(scmd, [50000], pos, vel, prec=prec, rcut=RC, path=AUTO)
+    assert scmd.md_get_path(ctx) == CELLS
     assert scmd.md_launch_counts(ctx)[0] == 5  # clear, bin, sort, density, force
     E, F = scmd.md_energy_forces(ctx)
     check_cluster(F, E[0], scmd.md_get_density(ctx), pos, prec, rcut=RC)
@@ -279,4 +280,6 @@ def test_cells_invalid_configurations(scmd):
         make(scmd, [55], pos, rcut=20.0, path=CELLS)
     assert e.value.status == scmd.MD_ERR_INVALID
     ctx = make(scmd, [55], pos, rcut=20.0, path=ALLPAIRS)  # the all-pairs path takes any cutoff
-    assert scmd.md_launch_counts(ctx)[0] == 2
+    assert scmd.md_get_path(ctx) == ALLPAIRS and scmd.md_launch_counts(ctx)[0] == 2
+    small = make(scmd, [55], pos, rcut=8.8)  # automatic choice: a small cluster keeps all pairs
+    assert scmd.md_get_path(small) == ALLPAIRS
