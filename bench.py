@@ -48,9 +48,9 @@ METRIC = "atom-timesteps/s & pair-evals/s vs FP32 peak; mixed vs FP64 at stated 
 UNIT = "atom-timesteps/s"
 FP32_LANES_PER_SM = 128
 FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n,m) = (9,6)
-# DRAM bytes (read + write) of one force-pass launch at the default workload, from the ncu
-# capture summarised in profiles/k_force_ni2000_mixed.md (cold caches; None when stale).
-FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 234496}
+# DRAM bytes (read + write) of one force-pass launch, from the ncu captures summarised in
+# profiles/k_force_ni2000_mixed.md and profiles/k_cell_passes_ni50000_mixed.md (cold caches).
+FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 234496, "ni50000": 1277184}
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
 
 
