@@ -105,3 +105,16 @@ def test_energy_drift_recovers_a_linear_trend():
     assert d["slope_eV_per_atom_per_ns"] == pytest.approx(0.05, rel=1e-9)
     assert d["max_abs_dE_eV_per_atom"] == pytest.approx(0.05 * 0.02, rel=1e-9)
     assert d["rms_eV_per_atom"] < 1e-12
+
+
+def test_cycle_transition_temperatures_on_synthetic_curves():
+    """The heating-cooling analysis finds the steepest rise and fall of E(T) (a latent-heat step on
+    a linear heat-capacity background, with noise)."""
+    from paper_1210_3559_gb300 import cycle
+    rng = np.random.default_rng(4)
+    T_up = np.arange(400.0, 1400.0, 1.0)
+    e_up = -4.4 + 2.6e-4 * (T_up - 400) + 0.06 / (1 + np.exp(-(T_up - 1180.0) / 4.0)) + 3e-4 * rng.standard_normal(len(T_up))
+    T_dn = T_up[::-1]
+    e_dn = -4.4 + 2.6e-4 * (T_dn - 400) + 0.06 / (1 + np.exp(-(T_dn - 790.0) / 4.0)) + 3e-4 * rng.standard_normal(len(T_dn))
+    assert abs(cycle._steepest(T_up, e_up) - 1180.0) <= 5.0
+    assert abs(cycle._steepest(T_dn, e_dn) - 790.0) <= 5.0
