@@ -1,9 +1,9 @@
 """Heating-cooling cycle of icosahedral nickel clusters and the hysteresis of melting and freezing.
 
-Usage: python -m paper_1210_3559_gb300.cycle [--replicas 8] [--shells 7] [--T-low 400] [--T-high 1400]
+Usage: python -m paper_1210_3559_gb300.cycle [--replicas 8] [--shells 8] [--T-low 400] [--T-high 1400]
                                             [--rate 1.0] [--out result.json]
 
-Independent replicas of a Mackay icosahedron (7 shells: 2057 atoms, the paper's Ni2047-2057 cluster) are
+Independent replicas of a Mackay icosahedron (8 shells: 2057 atoms, the paper's Ni2047-2057 cluster) are
 heated linearly from T-low to T-high and cooled back at the same rate (K/ps) under the Langevin
 thermostat (gamma = 10/ps, dt = 1 fs, the paper's settings), all in one context on the GPU, with the total
 energy per atom recorded every picosecond (the paper's cycle, Sec. III). For each replica: the melting
@@ -23,18 +23,22 @@ from . import analysis, inputs
 from . import scmd
 
 
-def _steepest(T: np.ndarray, e: np.ndarray, window_K: float = 20.0) -> float:
-    """Bath temperature at which the energy rises fastest with temperature (largest dE/dT from a
-    centred difference over window_K): melting on a heating leg, freezing on a cooling leg (where the
-    energy falls as the temperature falls)."""
+def _steepest(T: np.ndarray, e: np.ndarray, window_K: float = 40.0, smooth_K: float = 20.0) -> float:
+    """Bath temperature at which the energy rises fastest with temperature: melting on a heating leg,
+    freezing on a cooling leg (where the energy falls as the temperature falls). The energy is first
+    averaged over smooth_K of bath temperature (a liquid cluster's energy fluctuates by ~5e-3 eV/atom
+    per picosecond sample), then dE/dT is a centred difference over window_K."""
     dT = abs(T[1] - T[0])
+    ns = max(1, int(round(smooth_K / dT)))
+    es = np.convolve(e, np.ones(ns) / ns, mode="valid")
+    Ts = T[(ns - 1) // 2:(ns - 1) // 2 + len(es)]
     w = max(1, int(round(window_K / dT / 2)))
-    slope = (e[2 * w:] - e[:-2 * w]) / (T[2 * w:] - T[:-2 * w])
+    slope = (es[2 * w:] - es[:-2 * w]) / (Ts[2 * w:] - Ts[:-2 * w])
     k = int(np.argmax(slope))
-    return float(T[k + w])
+    return float(Ts[k + w])
 
 
-def run(replicas=8, shells=7, T_low=400.0, T_high=1400.0, rate_K_per_ps=1.0, dt=1.0, gamma=10.0, seed=21,
+def run(replicas=8, shells=8, T_low=400.0, T_high=1400.0, rate_K_per_ps=1.0, dt=1.0, gamma=10.0, seed=21,
         precision=scmd.MD_PREC_MIXED, segment_ps=50.0):
     p1 = inputs.mackay_icosahedron(shells, 2.49)
     n = len(p1)
@@ -98,7 +102,7 @@ def run(replicas=8, shells=7, T_low=400.0, T_high=1400.0, rate_K_per_ps=1.0, dt=
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--replicas", type=int, default=8)
-    ap.add_argument("--shells", type=int, default=7)
+    ap.add_argument("--shells", type=int, default=8)
     ap.add_argument("--T-low", type=float, default=400.0)
     ap.add_argument("--T-high", type=float, default=1400.0)
     ap.add_argument("--rate", type=float, default=1.0, help="K/ps")
