@@ -2,11 +2,12 @@
 //
 // A context owns the device-resident state of a batch of clusters and issues,
 // per MD step, the density pass and the force pass (whose epilogue integrates),
-// plus a Berendsen kernel when that thermostat is selected and an observables
+// preceded on the cell-list path by the cell build (clear, bin, sort), plus a
+// Berendsen kernel when that thermostat is selected and an observables
 // reduction when a sample is due. md_step replays CUDA graphs that each hold
-// one chunk of steps (step start, 2-3 kernels per step, step counter advance);
-// graphs are cached by chunk length, the observation phase of the chunk's
-// first step, the thermostat kind and the launch shapes.
+// one chunk of steps (step start, the kernels of every step, step counter
+// advance); graphs are cached by chunk length, the observation phase of the
+// chunk's first step, the thermostat kind and the launch shapes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
