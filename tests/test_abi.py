@@ -67,3 +67,23 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(scmd.ScmdError) as e:
         scmd.md_create(scmd.config(), [2], [[0.0, 0.0, 0.0], [2.5, 0.0, 0.0]], None, [58.6934, 58.6934])
     assert e.value.status == scmd.MD_ERR_CUDA
+
+
+def test_degenerate_and_invalid_configurations_without_gpu(lib):
+    """Rejected before any device call: no cluster at all, an unknown precision or path, the cell path
+    without a cutoff, a negative cutoff."""
+    import numpy as np
+    from paper_1210_3559_gb300 import scmd
+    one = np.zeros((1, 3))
+    cases = [
+        (scmd.config(), [], np.zeros((0, 3)), [], scmd.sc_params()),
+        (scmd.config(precision=7), [1], one, [58.6934], scmd.sc_params()),
+        (scmd.config(path=9), [1], one, [58.6934], scmd.sc_params()),
+        (scmd.config(path=scmd.MD_PATH_CELLS), [1], one, [58.6934], scmd.sc_params(rcut=0.0)),
+        (scmd.config(), [1], one, [58.6934], scmd.sc_params(rcut=-1.0)),
+    ]
+    for cfg, sizes, pos, mass, prm in cases:
+        with pytest.raises(scmd.ScmdError) as e:
+            scmd.md_create(cfg, sizes, pos, None, mass, prm)
+        assert e.value.status == scmd.MD_ERR_INVALID, (sizes, cfg.precision, cfg.path)
+        assert scmd.md_last_error() != ""
