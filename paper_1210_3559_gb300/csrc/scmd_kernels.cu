@@ -42,7 +42,7 @@ template <> struct SplitOf<0> { static constexpr int S = 8; };
 // ------------------------------------------------------------- density pass
 // Shared memory: tiles [W][32] V4 | red [W][BI] double | inbox [C][BI] double (read on rank 0)
 template <int PREC, int IPT, int SPECIAL, int CUT>
-__global__ void __launch_bounds__(512, 1) k_density(const Dev d, const Item* __restrict__ items, int C, int obs) {
+__global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d, const Item* __restrict__ items, int C, int obs) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     constexpr int BI = 32 * IPT;
