@@ -68,7 +68,9 @@ typedef enum {
     MD_PATH_AUTO = 0,     /* cells when rcut_A > 0 and the largest cluster has >= 8192
                              atoms, else all pairs                                       */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
-    MD_PATH_CELLS = 2     /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
+    MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
+    MD_PATH_VERLET = 3    /* per-atom neighbour lists (rcut_A + 1 A) built on the cell grid,
+                             rebuilt when an atom has moved 0.5 A; requires rcut_A > 0     */
 } md_path;
 
 /* The cell path (not in the paper, which sums every pair and leaves cutoffs to

@@ -37,6 +37,9 @@ thread_local std::string g_create_error;
 // MD_PATH_AUTO with a cutoff takes the cell list once the largest cluster has this many atoms:
 // below it the 27 cells of side >= rcut around an atom hold most of the cluster anyway.
 constexpr int kAutoCellsMinAtoms = 8192;
+// Neighbour-list path: the lists hold the atoms within rcut + kSkin; they are rebuilt when some atom
+// has moved more than kSkin / 2 since the last rebuild.
+constexpr double kSkin = 1.0;
 constexpr double kPi = 3.14159265358979323846;
 
 struct GraphKey {
@@ -82,6 +85,11 @@ struct md_ctx {
     CellGrid* d_grid = nullptr;
     int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr, *d_cell_order = nullptr;
     int32_t* d_cell_oct = nullptr;
+    // neighbour-list path
+    int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vorder = nullptr, *d_vslot = nullptr, *d_vanchor = nullptr;
+    void *d_vpos = nullptr, *d_vposg = nullptr, *d_vshift = nullptr;
+    double* d_vxref = nullptr;
+    uint32_t* d_vdmax = nullptr;
     uint8_t* d_cell_obyte = nullptr;
     void *d_cpos = nullptr, *d_cposg = nullptr;
     double *d_eatom = nullptr, *d_obs_x = nullptr, *d_obs_v = nullptr;
@@ -172,6 +180,19 @@ void fill_dev(md_ctx* c) {
     d.cell_atoms = c->d_cell_atoms;
     d.cell_oct = c->d_cell_oct;
     d.cell_obyte = c->d_cell_obyte;
+    d.nslot = (int32_t)c->ntot;
+    d.vskin2h = (float)(0.25 * kSkin * kSkin);
+    d.vrl2 = (c->pot.rcut + kSkin) * (c->pot.rcut + kSkin);
+    d.vlist = c->d_vlist;
+    d.vcount = c->d_vcount;
+    d.vorder = c->d_vorder;
+    d.vslot = c->d_vslot;
+    d.vanchor = c->d_vanchor;
+    d.vpos = c->d_vpos;
+    d.vposg = c->d_vposg;
+    d.vxref = c->d_vxref;
+    d.vshift = c->d_vshift;
+    d.vdmax = c->d_vdmax;
     d.cpos = c->d_cpos;
     d.cposg = c->d_cposg;
     d.eatom = c->d_eatom;
@@ -179,15 +200,16 @@ void fill_dev(md_ctx* c) {
     d.obs_v = c->d_obs_v;
 }
 
-// Cell grid of every cluster (cell-list path). The cube [-E, E)^3 around the origin covers the
+// Cell grid of every cluster (cell-list and neighbour-list paths; "rcut" below is the reach:
+// rcut, or rcut + skin for the neighbour lists). The cube [-E, E)^3 around the origin covers the
 // cluster with a margin: E = max(1.3 R_fcc, 1.1 R_now) + rcut, R_fcc the radius of N atoms at
 // the fcc density 4 / a^3 and R_now the largest distance of an atom from the centre of mass
 // (clamped to 3 R_fcc so that a few far atoms cannot blow up the grid; those sit in border
 // cells). G = floor(2E / rcut) cells per axis (at most 128), side h = 2E / G >= rcut, rounded
 // up to a binary32 value (E is then G h / 2) so that offsets between cell centres are exact in FP32.
 // Returns false when a cell at the fcc density would not fit kCellCap atoms.
-bool make_grids(md_ctx* c, const double* pos, const double* mass) {
-    const double rc = c->pot.rcut, a = c->pot.a;
+bool make_grids(md_ctx* c, const double* pos, const double* mass, double reach) {
+    const double rc = reach, a = c->pot.a;
     c->grids.resize(c->B);
     int off = 0;
     for (int b = 0; b < c->B; ++b) {
@@ -292,7 +314,14 @@ md_status evaluate(md_ctx* c, bool observe) {
     const Item* i0 = items_for(c, c->shape[0], &n0);
     const Item* i1 = items_for(c, c->shape[1], &n1);
     CK(c, launch_mirror(d, c->stream));
-    if (c->path == 1) {
+    if (c->path == 2) {  // lists from the current positions (the results do not depend on when)
+        CK(c, launch_cell_build(d, c->stream));
+        CK(c, launch_v_rebuild(d, 0, 0, c->stream));
+        CK(c, cudaMemsetAsync(c->d_vdmax, 0, sizeof(uint32_t) * 2, c->stream));
+        CK(c, launch_v_density(d, observe ? 1 : 0, c->stream));
+        CK(c, launch_v_force(d, observe ? 1 : 0, 0, 0, c->stream));
+        if (observe) CK(c, launch_cell_obs(d, 1, 1, c->stream));
+    } else if (c->path == 1) {
         CK(c, launch_cell_build(d, c->stream));
         CK(c, launch_cell_density(d, observe ? 1 : 0, c->stream));
         CK(c, launch_cell_force(d, observe ? 1 : 0, 0, 0, c->stream));
@@ -327,7 +356,15 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
         const bool obs = oe > 0 && next % oe == 0;
         const bool last = k == M - 1;
         const int flags = (last ? 1 : 0) | (obs ? 2 : 0);
-        if (c->path == 1) {
+        if (c->path == 2) {
+            CK(c, launch_v_anchor(d, k, c->stream));
+            CK(c, launch_cell_build(d, c->stream, 1, k));
+            CK(c, launch_v_rebuild(d, 1, k, c->stream));
+            CK(c, launch_v_density(d, obs ? 1 : 0, c->stream));
+            CK(c, launch_v_force(d, 2, k, flags, c->stream));
+            if (obs) CK(c, launch_cell_obs(d, kind == MD_BERENDSEN ? 1 : 0, kind == MD_BERENDSEN ? 0 : 1, c->stream));
+            if (kind == MD_BERENDSEN) CK(c, launch_cell_ke(d, c->stream));
+        } else if (c->path == 1) {
             CK(c, launch_cell_build(d, c->stream));
             CK(c, launch_cell_density(d, obs ? 1 : 0, c->stream));
             CK(c, launch_cell_force(d, 2, k, flags, c->stream));
@@ -395,7 +432,9 @@ void free_all(md_ctx* c) {
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
-                    c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte};
+                    c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
+                    c->d_vlist, c->d_vcount, c->d_vorder, c->d_vslot, c->d_vanchor, c->d_vpos, c->d_vposg,
+                    c->d_vxref, c->d_vdmax, c->d_vshift};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -429,6 +468,8 @@ md_status check_status(md_ctx* c) {
     if (s & 2)
         return fail(c, MD_ERR_STATE, "a cell of the cell grid overflowed (more than %d atoms); forces are invalid",
                     kCellCap);
+    if (s & 4)
+        return fail(c, MD_ERR_STATE, "a neighbour list overflowed (more than %d entries); forces are invalid", kVMax);
     return MD_OK;
 }
 
@@ -524,10 +565,11 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     if (n_clusters < 1) return fail(nullptr, MD_ERR_INVALID, "n_clusters must be >= 1");
     if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED)
         return fail(nullptr, MD_ERR_INVALID, "unknown precision %d", cfg->precision);
-    if (cfg->path != MD_PATH_AUTO && cfg->path != MD_PATH_ALLPAIRS && cfg->path != MD_PATH_CELLS)
+    if (cfg->path != MD_PATH_AUTO && cfg->path != MD_PATH_ALLPAIRS && cfg->path != MD_PATH_CELLS &&
+        cfg->path != MD_PATH_VERLET)
         return fail(nullptr, MD_ERR_INVALID, "unknown path %d", cfg->path);
-    if (cfg->path == MD_PATH_CELLS && !(prm->rcut_A > 0))
-        return fail(nullptr, MD_ERR_INVALID, "the cell path needs a cutoff (rcut_A > 0)");
+    if ((cfg->path == MD_PATH_CELLS || cfg->path == MD_PATH_VERLET) && !(prm->rcut_A > 0))
+        return fail(nullptr, MD_ERR_INVALID, "the cell and neighbour-list paths need a cutoff (rcut_A > 0)");
     if (cfg->obs_every < 0 || cfg->graph_chunk < 0 || cfg->obs_capacity < 0)
         return fail(nullptr, MD_ERR_INVALID, "negative obs_every, graph_chunk or obs_capacity");
     if (!(std::isfinite(prm->eps_eV) && std::isfinite(prm->c) && std::isfinite(prm->a_A) && prm->a_A > 0 &&
@@ -609,10 +651,15 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     {
         int maxn = 0;
         for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
-        const bool cells = cfg->path == MD_PATH_CELLS ||
+        const bool cells = cfg->path == MD_PATH_CELLS || cfg->path == MD_PATH_VERLET ||
                            (cfg->path == MD_PATH_AUTO && P.rcut > 0 && maxn >= kAutoCellsMinAtoms);
-        c->path = cells ? 1 : 0;
-        if (cells && !make_grids(c, pos, mass)) {
+        c->path = cfg->path == MD_PATH_VERLET ? 2 : (cells ? 1 : 0);
+        if (c->path == 2 && c->npad >= (1 << 26)) {
+            delete c;
+            return fail(nullptr, MD_ERR_INVALID, "the neighbour-list path takes at most 2^26 padded atoms");
+        }
+        // the neighbour lists hold the pairs within rcut + skin, so their cells are sized by that
+        if (cells && !make_grids(c, pos, mass, c->path == 2 ? P.rcut + kSkin : P.rcut)) {
             delete c;
             return fail(nullptr, MD_ERR_INVALID,
                         "rcut_A = %g is too large for the cell path (a cell would exceed %d atoms); "
@@ -670,7 +717,7 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     CKC(cudaMalloc(&c->d_posg, (size_t)vec4_size(c) * np));
     CKC(cudaMalloc(&c->d_step, sizeof(int64_t)));
     CKC(cudaMalloc(&c->d_run, sizeof(Run)));
-    if (c->path == 1) {
+    if (c->path >= 1) {
         std::vector<int32_t> cell_cl(c->n_cells), order(c->n_cells);
         std::vector<double> depth(c->n_cells);
         for (int b = 0; b < n_clusters; ++b) {
@@ -707,6 +754,40 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         CKC(cudaMemset(c->d_eatom, 0, sizeof(double) * 2 * np));
         CKC(cudaMemset(c->d_obs_x, 0, sizeof(double) * 3 * np));
         CKC(cudaMemset(c->d_obs_v, 0, sizeof(double) * 3 * np));
+    }
+    if (c->path == 2) {
+        const size_t ns = (size_t)c->ntot;
+        CKC(cudaMalloc(&c->d_vlist, sizeof(int32_t) * kVMax * ns));
+        CKC(cudaMalloc(&c->d_vcount, sizeof(int32_t) * ns));
+        CKC(cudaMalloc(&c->d_vorder, sizeof(int32_t) * ns));
+        CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
+        CKC(cudaMalloc(&c->d_vanchor, sizeof(int32_t) * np));
+        CKC(cudaMalloc(&c->d_vpos, (size_t)vec4_size(c) * np));
+        CKC(cudaMalloc(&c->d_vposg, (size_t)vec4_size(c) * np));
+        CKC(cudaMalloc(&c->d_vxref, sizeof(double) * 3 * np));
+        CKC(cudaMalloc(&c->d_vdmax, sizeof(uint32_t) * 2));
+        CKC(cudaMalloc(&c->d_vshift, (size_t)vec4_size(c) * 64 * n_clusters));
+        CKC(cudaMemset(c->d_vdmax, 0, sizeof(uint32_t) * 2));
+        // every slot, count and entry starts as a valid atom index (atom 0, empty list)
+        CKC(cudaMemset(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns));
+        CKC(cudaMemset(c->d_vcount, 0, sizeof(int32_t) * ns));
+        CKC(cudaMemset(c->d_vorder, 0, sizeof(int32_t) * ns));
+        CKC(cudaMemset(c->d_vanchor, 0, sizeof(int32_t) * np));
+        CKC(cudaMemset(c->d_vxref, 0, sizeof(double) * 3 * np));
+        // (a_i - a_j) h for the shift code (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4 of every cluster
+        std::vector<unsigned char> tab((size_t)vec4_size(c) * 64 * n_clusters, 0);
+        for (int b = 0; b < n_clusters; ++b)
+            for (int code = 0; code < 64; ++code) {
+                const double hb = c->grids[b].h;
+                const double v[4] = {((code & 3) - 1) * hb, (((code >> 2) & 3) - 1) * hb, (((code >> 4) & 3) - 1) * hb, 0.0};
+                if (cfg->precision == MD_PREC_MIXED) {
+                    const float f[4] = {(float)v[0], (float)v[1], (float)v[2], 0.f};
+                    memcpy(tab.data() + 16 * ((size_t)b * 64 + code), f, 16);
+                } else {
+                    memcpy(tab.data() + 32 * ((size_t)b * 64 + code), v, 32);
+                }
+            }
+        CKC(cudaMemcpy(c->d_vshift, tab.data(), tab.size(), cudaMemcpyHostToDevice));
     }
     for (int k = 0; k < 2; ++k) {
         CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
@@ -997,11 +1078,19 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     int n0, n1;
     const Item* i0 = items_for(c, c->shape[0], &n0);
     const Item* i1 = items_for(c, c->shape[1], &n1);
-    const bool cells = c->path == 1;
-    auto density = [&]() { return cells ? launch_cell_density(d, 0, c->stream) : launch_density(d, i0, n0, c->shape[0], 0, c->stream); };
-    auto force = [&]() { return cells ? launch_cell_force(d, 0, 0, 0, c->stream) : launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream); };
+    const bool cells = c->path == 1, vl = c->path == 2;
+    auto density = [&]() {
+        return vl ? launch_v_density(d, 0, c->stream)
+                  : cells ? launch_cell_density(d, 0, c->stream) : launch_density(d, i0, n0, c->shape[0], 0, c->stream);
+    };
+    auto force = [&]() {
+        return vl ? launch_v_force(d, 0, 0, 0, c->stream)
+                  : cells ? launch_cell_force(d, 0, 0, 0, c->stream)
+                          : launch_force(d, i1, n1, c->shape[1], 0, 0, 0, c->stream);
+    };
     CK(c, launch_mirror(d, c->stream));
-    if (cells) CK(c, launch_cell_build(d, c->stream));
+    if (cells || vl) CK(c, launch_cell_build(d, c->stream));
+    if (vl) CK(c, launch_v_rebuild(d, 0, 0, c->stream));
     for (int w = 0; w < 3; ++w) {
         CK(c, density());
         CK(c, force());
@@ -1036,7 +1125,14 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
     if (ms_d) *ms_d = td / reps;
     if (ms_f) *ms_f = tf / reps;
-    if (pairs && !cells) {
+    if (pairs && vl) {  // list entries (pairs tested per pass)
+        std::vector<int32_t> cnt(c->ntot);
+        CK(c, cudaMemcpyAsync(cnt.data(), c->d_vcount, sizeof(int32_t) * c->ntot, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        double p = 0;
+        for (int32_t n : cnt) p += n;
+        *pairs = p;
+    } else if (pairs && !cells) {
         double p = 0;
         for (int s : c->sizes) p += (double)s * (double)(s - 1);
         *pairs = p;
@@ -1072,7 +1168,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
 
 md_status md_autotune(md_ctx* c, int32_t reps) {
     if (!c || reps < 1) return MD_ERR_INVALID;
-    if (c->path == 1) return MD_OK;  // the cell kernels have one launch shape
+    if (c->path >= 1) return MD_OK;  // the cell and neighbour-list kernels have one launch shape
     const Dev& d = c->dev;
     const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[4] = {1, 2, 4, 8};
     // Phase 1: every shape of each pass timed alone (CUDA events over reps launches).
@@ -1182,13 +1278,13 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
 
 md_status md_get_path(const md_ctx* c, int32_t* path) {
     if (!c || !path) return MD_ERR_INVALID;
-    *path = c->path == 1 ? MD_PATH_CELLS : MD_PATH_ALLPAIRS;
+    *path = c->path == 2 ? MD_PATH_VERLET : (c->path == 1 ? MD_PATH_CELLS : MD_PATH_ALLPAIRS);
     return MD_OK;
 }
 
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
-    if (per_step) *per_step = c->path == 1 ? 5 : 2;
+    if (per_step) *per_step = c->path == 2 ? 9 : (c->path == 1 ? 5 : 2);
     if (per_chunk) *per_chunk = 3;
     return MD_OK;
 }

@@ -33,27 +33,15 @@
 // J staged atoms per step. A pair is masked (r2 := inf) when r2 >= rcut^2 or when it is the atom
 // itself (recognised by its place in the staged list), like the all-pairs cutoff variant, so every
 // tested pair takes the same arithmetic as there.
-#include "scmd_device.cuh"
+#include "scmd_cells.cuh"
 
 namespace scmd {
 
-constexpr int kCellThreads = 256;
-constexpr int kBox = 6, kBoxN = 216;  // the octant box of a home cell: 6 x 6 x 6 octants
-template <int PREC> struct CellChunk;
-template <> struct CellChunk<1> { static constexpr int TJ = 2304; };  // 36 KB of float4
-template <> struct CellChunk<0> { static constexpr int TJ = 1024; };  // 32 KB of double4
-
-// Cell index along one axis of a coordinate relative to the origin. fmin/fmax come before the
-// conversion: far or non-finite coordinates land in a border cell.
-__device__ __forceinline__ int cell_axis(double rel, const CellGrid& g) {
-    return (int)fmin(fmax(floor((rel + g.E) * g.inv_h), 0.0), (double)(g.G - 1));
-}
-// Centre of cell k along one axis, relative to the origin (exact: h is a binary32 value).
-__device__ __forceinline__ double cell_centre(int k, const CellGrid& g) { return -g.E + (k + 0.5) * g.h; }
-
-__global__ void k_cell_clear(const Dev d) {
+__global__ void k_cell_clear(const Dev d, int cond, int k_local) {
     pdl_launch_dependents();
     pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
+    if (d.path == 2 && blockIdx.x == 0 && threadIdx.x == 0) *d.vslot = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.n_cells; c += gridDim.x * blockDim.x)
         d.cell_count[c] = 0;
 }
@@ -61,11 +49,12 @@ __global__ void k_cell_clear(const Dev d) {
 // One thread per padded atom: its cell (from the FP64 state), an atomic slot in it, and at that
 // slot its octant of the cell (the sign of its offset from the centre per axis) and the offset itself
 // rounded once to the pass precision (in the cposg slots, free until the density pass).
-template <int PREC> __global__ void k_cell_bin(const Dev d) {
+template <int PREC> __global__ void k_cell_bin(const Dev d, int cond, int k_local) {
     using V4 = typename Tr<PREC>::V4;
     using R = typename Tr<PREC>::R;
     pdl_launch_dependents();
     pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.npad) return;
     const int cl = d.cl_of_group[i >> 5];
@@ -95,12 +84,13 @@ template <int PREC> __global__ void k_cell_bin(const Dev d) {
 
 // One warp per cell: each atom's rank by (octant, atom index) is its place; its offset moves there
 // (cposg -> cpos), and the first place of every octant (plus the count) goes to cell_oct.
-template <int PREC> __global__ void k_cell_sort(const Dev d) {
+template <int PREC> __global__ void k_cell_sort(const Dev d, int cond, int k_local) {
     using V4 = typename Tr<PREC>::V4;
     __shared__ int buf[kCellThreads / 32][kCellCap];
     __shared__ unsigned char boct[kCellThreads / 32][kCellCap];
     pdl_launch_dependents();
     pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * (kCellThreads / 32) + w;
     if (c >= d.n_cells) return;
@@ -126,119 +116,6 @@ template <int PREC> __global__ void k_cell_sort(const Dev d) {
         a[r] = e;
         cp[r] = from[k];
     }
-}
-
-// The octant box of home cell c: the 27 cells around it, each split into its 2 x 2 x 2 octants of
-// side h/2 >= rcut/2, form a 6 x 6 x 6 box of octants, numbered t = (Z * 6 + Y) * 6 + X. For each
-// the source slot of its atoms (s_src) and the exclusive prefix of the counts in that order
-// (s_pref[0..216]). Off-grid cells are empty. Every thread of the CTA calls this.
-__device__ __forceinline__ int octant_box(const Dev& d, int c, const CellGrid& g, int* s_src, int* s_cnt,
-                                          int* s_pref) {
-    const int loc = c - g.off, cx = loc % g.G, cy = (loc / g.G) % g.G, cz = loc / (g.G * g.G);
-    for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {
-        const int X = t % kBox, Y = (t / kBox) % kBox, Z = t / (kBox * kBox);
-        const int x = cx + X / 2 - 1, y = cy + Y / 2 - 1, z = cz + Z / 2 - 1;
-        int n = 0, src = 0;
-        if (x >= 0 && x < g.G && y >= 0 && y < g.G && z >= 0 && z < g.G) {
-            const int nc = g.off + (z * g.G + y) * g.G + x, o = (X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2);
-            const int s0 = d.cell_oct[nc * 9 + o];
-            n = d.cell_oct[nc * 9 + o + 1] - s0;
-            src = nc * kCellCap + s0;
-        }
-        s_src[t] = src;
-        s_cnt[t] = n;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 216 counts, 7 per lane
-        const int lane = threadIdx.x;
-        int v[7], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const int t = lane * 7 + q;
-            v[q] = t < kBoxN ? s_cnt[t] : 0;
-            sum += v[q];
-        }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        int run = incl - sum;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const int t = lane * 7 + q;
-            if (t < kBoxN) s_pref[t] = run;
-            run += v[q];
-        }
-        if (lane == 31) s_pref[kBoxN] = incl;
-    }
-    __syncthreads();
-    return s_pref[kBoxN];
-}
-
-// Stage entries e0 .. e0 + ne - 1 of the octant box (one octant per thread), moved from their
-// cell's centre to the home cell's centre by the exact (k - l) h.
-template <class V4, class R>
-__device__ __forceinline__ void gather_box(const V4* __restrict__ src, const int* s_src, const int* s_pref, R h,
-                                           int e0, int ne, V4* spos) {
-    for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {
-        const int a = max(s_pref[t], e0), b = min(s_pref[t + 1], e0 + ne);
-        if (a >= b) continue;
-        const R sx = (R)((t % kBox) / 2 - 1) * h, sy = (R)(((t / kBox) % kBox) / 2 - 1) * h;
-        const R sz = (R)((t / (kBox * kBox)) / 2 - 1) * h;
-        const V4* from = src + s_src[t] - s_pref[t];
-#pragma unroll 2
-        for (int q = a; q < b; ++q) {
-            V4 p = from[q];
-            p.x += sx;
-            p.y += sy;
-            p.z += sz;
-            spos[q - e0] = p;
-        }
-    }
-}
-
-// One home octant per warp: its atoms (cell slots s0 + r0 .. s0 + r0 + nb - 1), the staged place of
-// its octant (for the self test) and the lane layout: nb i-slots times J = 32 / nb j-groups.
-struct OctWarp {
-    int o, s0, nb, J, is, jg, home_t;
-    bool act;
-};
-__device__ __forceinline__ OctWarp oct_warp(const Dev& d, int c, int r0) {
-    OctWarp q;
-    const int lane = threadIdx.x & 31;
-    q.o = threadIdx.x >> 5;
-    q.s0 = d.cell_oct[c * 9 + q.o];
-    q.nb = min(32, d.cell_oct[c * 9 + q.o + 1] - q.s0 - r0);
-    q.J = q.nb > 0 ? 32 / q.nb : 1;
-    q.is = q.nb > 0 ? lane % q.nb : 0;
-    q.jg = q.nb > 0 ? lane / q.nb : 0;
-    q.act = q.nb > 0 && q.jg < q.J;
-    const int ox = q.o & 1, oy = (q.o >> 1) & 1, oz = q.o >> 2;
-    q.home_t = ((2 + oz) * kBox + 2 + oy) * kBox + 2 + ox;
-    return q;
-}
-// Blocks of 32 home atoms that the warp with the fullest octant needs (the same for every warp, so
-// that the staging barriers line up).
-__device__ __forceinline__ int oct_blocks(const Dev& d, int c) {
-    int m = 0;
-#pragma unroll
-    for (int o = 0; o < 8; ++o) m = max(m, d.cell_oct[c * 9 + o + 1] - d.cell_oct[c * 9 + o]);
-    return (m + 31) / 32;
-}
-// The 25 runs of the home octant's 5 x 5 x 5 neighbour octants (5 octants along x are adjacent in
-// the staged order), clipped to the staged chunk [e0, e0 + ne): local [lo, hi) per run, written by
-// the warp's lanes into its row of the run table.
-__device__ __forceinline__ void oct_runs(const int* s_pref, int o, int e0, int ne, int2* runs) {
-    const int lane = threadIdx.x & 31;
-    if (lane < 25) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2, rz = lane / 5, ry = lane % 5;
-        const int base = ((oz + rz) * kBox + oy + ry) * kBox + ox;
-        const int a = max(s_pref[base], e0) - e0, b = min(s_pref[base + 5], e0 + ne) - e0;
-        runs[lane] = make_int2(a, max(a, b));
-    }
-    __syncwarp();
 }
 
 // ------------------------------------------------------------- density pass
@@ -507,14 +384,14 @@ __global__ void k_cell_ke(const Dev d) {
 }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_cell_build(const Dev& d, cudaStream_t s) {
-    cudaError_t e = launch_ex(k_cell_clear, (d.n_cells + 255) / 256, 256, 0, 0, s, d);
+cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond, int k_local) {
+    cudaError_t e = launch_ex(k_cell_clear, (d.n_cells + 255) / 256, 256, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
-    e = d.prec == 1 ? launch_ex(k_cell_bin<1>, (d.npad + 255) / 256, 256, 0, 0, s, d)
-                    : launch_ex(k_cell_bin<0>, (d.npad + 255) / 256, 256, 0, 0, s, d);
+    e = d.prec == 1 ? launch_ex(k_cell_bin<1>, (d.npad + 255) / 256, 256, 0, 0, s, d, cond, k_local)
+                    : launch_ex(k_cell_bin<0>, (d.npad + 255) / 256, 256, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
-    return d.prec == 1 ? launch_ex(k_cell_sort<1>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d)
-                       : launch_ex(k_cell_sort<0>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d);
+    return d.prec == 1 ? launch_ex(k_cell_sort<1>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d, cond, k_local)
+                       : launch_ex(k_cell_sort<0>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d, cond, k_local);
 }
 
 cudaError_t launch_cell_density(const Dev& d, int obs, cudaStream_t s) {

@@ -27,6 +27,7 @@ constexpr int kObsFields = 16;  // doubles per observable partial record
 constexpr int kMaxWarps = 16;
 constexpr int kMaxCluster = 8;
 constexpr int kCellCap = 256;   // atoms a cell of the cell-list path can hold
+constexpr int kVMax = 512;      // entries a neighbour list can hold
 
 // Fields of an observable partial record (per 32-atom group).
 enum ObsField {
@@ -135,6 +136,21 @@ struct Dev {
     double* eatom;       // [npad][2] per-atom -eps c sqrt(rho_i) and sum_j r_ij^-n
     double* obs_x;       // [npad][3] positions at an observation (end of the step)
     double* obs_v;       // [npad][3] velocities at an observation
+    // neighbour-list path (path == 2): per-atom lists of the atoms closer than rcut + skin at the
+    // last rebuild, rebuilt when some atom has moved more than skin / 2 since
+    int32_t nslot;       // list slots (the real atoms, in cell order at the last rebuild)
+    float vskin2h;       // (skin / 2)^2
+    double vrl2;         // (rcut + skin)^2
+    int32_t* vlist;      // [kVMax][nslot] (j << 6) | shift code, ascending j within a slot
+    int32_t* vcount;     // [nslot]
+    int32_t* vorder;     // [nslot] atom of each slot
+    int32_t* vslot;      // [1] slot counter of a rebuild
+    int32_t* vanchor;    // [npad] cell (x | y << 10 | z << 20) of each atom at the last rebuild
+    void* vpos;          // [npad] V4 (x - anchor cell centre, 0) in the pass precision
+    void* vposg;         // [npad] V4 (x - anchor cell centre, B6 rho^-1/2)
+    double* vxref;       // [3][npad] positions at the last rebuild
+    const void* vshift;  // [B][64] V4 (a_i - a_j) h of each shift code (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4
+    uint32_t* vdmax;     // [2] largest squared displacement since the rebuild (float bits), by step parity
 };
 
 constexpr int kHistFields = 20;  // doubles per history record (see md_obs packing in the API)
@@ -162,13 +178,19 @@ cudaError_t launch_normals(uint64_t seed, uint32_t cluster, int64_t step, int n,
                            cudaStream_t s);
 size_t pass_smem_bytes(int prec, Shape sh);
 // Cell-list path (defined in scmd_cells.cu).
-cudaError_t launch_cell_build(const Dev& d, cudaStream_t s);  // clear, bin, sort
+// clear, bin, sort; cond != 0: only when a neighbour-list rebuild is due at local step k_local
+cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond = 0, int k_local = 0);
 cudaError_t launch_cell_density(const Dev& d, int obs, cudaStream_t s);
 cudaError_t launch_cell_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // Observable partials of every 32-atom group from the per-atom data (from_state: read x, v;
 // else the snapshot obs_x, obs_v); with_velocity 0 leaves the velocity fields alone.
 cudaError_t launch_cell_obs(const Dev& d, int from_state, int with_velocity, cudaStream_t s);
 cudaError_t launch_cell_ke(const Dev& d, cudaStream_t s);
+// Neighbour-list path (defined in scmd_verlet.cu).
+cudaError_t launch_v_anchor(const Dev& d, int k_local, cudaStream_t s);
+cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
+cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s);
+cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // The calling thread's error message returned by md_last_error(NULL) (defined in scmd_api.cu).
 void set_thread_error(const char* msg);
 cudaError_t configure_kernels();
