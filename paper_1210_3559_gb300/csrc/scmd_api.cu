@@ -40,6 +40,7 @@ constexpr int kAutoCellsMinAtoms = 8192;
 // Neighbour-list path: the lists hold the atoms within rcut + kSkin; they are rebuilt when some atom
 // has moved more than kSkin / 2 since the last rebuild.
 constexpr double kSkin = 1.0;
+constexpr double kSkinMargin = 1e-3;  // the rebuild triggers at kSkin / 2 - kSkinMargin (covers rounding)
 constexpr double kPi = 3.14159265358979323846;
 
 struct GraphKey {
@@ -86,8 +87,10 @@ struct md_ctx {
     int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr, *d_cell_order = nullptr;
     int32_t* d_cell_oct = nullptr;
     // neighbour-list path
-    int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vorder = nullptr, *d_vslot = nullptr, *d_vanchor = nullptr;
-    void *d_vpos = nullptr, *d_vposg = nullptr, *d_vshift = nullptr;
+    int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vsub = nullptr, *d_vorder = nullptr, *d_vslotof = nullptr;
+    int32_t* d_vslot = nullptr;
+    void *d_vhi = nullptr, *d_vposg = nullptr;
+    float4* d_vlo = nullptr;
     double* d_vxref = nullptr;
     uint32_t* d_vdmax = nullptr;
     uint8_t* d_cell_obyte = nullptr;
@@ -181,17 +184,18 @@ void fill_dev(md_ctx* c) {
     d.cell_oct = c->d_cell_oct;
     d.cell_obyte = c->d_cell_obyte;
     d.nslot = (int32_t)c->ntot;
-    d.vskin2h = (float)(0.25 * kSkin * kSkin);
+    d.vskin2h = (float)((0.5 * kSkin - kSkinMargin) * (0.5 * kSkin - kSkinMargin));
     d.vrl2 = (c->pot.rcut + kSkin) * (c->pot.rcut + kSkin);
     d.vlist = c->d_vlist;
     d.vcount = c->d_vcount;
+    d.vsub = c->d_vsub;
     d.vorder = c->d_vorder;
+    d.vslotof = c->d_vslotof;
     d.vslot = c->d_vslot;
-    d.vanchor = c->d_vanchor;
-    d.vpos = c->d_vpos;
+    d.vhi = c->d_vhi;
+    d.vlo = c->d_vlo;
     d.vposg = c->d_vposg;
     d.vxref = c->d_vxref;
-    d.vshift = c->d_vshift;
     d.vdmax = c->d_vdmax;
     d.cpos = c->d_cpos;
     d.cposg = c->d_cposg;
@@ -241,7 +245,12 @@ bool make_grids(md_ctx* c, const double* pos, const double* mass, double reach) 
         g.h = (double)hf;
         g.E = 0.5 * G * g.h;
         g.inv_h = 1.0 / g.h;
-        if (1.25 * 4.0 * g.h * g.h * g.h / (a * a * a) > kCellCap) return false;
+        // a cell at the fcc density (or the whole cluster, if smaller) must fit kCellCap atoms
+        if (std::min(1.25 * 4.0 * g.h * g.h * g.h / (a * a * a), (double)n) > kCellCap) return false;
+        // neighbour lists: the coordinates of the atoms inside the grid cube, shifted by a power of two
+        // S >= E + 32, lie in [32, 2S), so the FP32 high parts of two of them closer than 16 A differ
+        // exactly (Sterbenz's lemma)
+        g.frame = std::exp2(std::ceil(std::log2(g.E + 32.0)));
         c->grids[b] = g;
         off += G * G * G;
     }
@@ -357,7 +366,7 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
         const bool last = k == M - 1;
         const int flags = (last ? 1 : 0) | (obs ? 2 : 0);
         if (c->path == 2) {
-            CK(c, launch_v_anchor(d, k, c->stream));
+            CK(c, launch_v_pos(d, k, c->stream));
             CK(c, launch_cell_build(d, c->stream, 1, k));
             CK(c, launch_v_rebuild(d, 1, k, c->stream));
             CK(c, launch_v_density(d, obs ? 1 : 0, c->stream));
@@ -433,8 +442,8 @@ void free_all(md_ctx* c) {
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
                     c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
-                    c->d_vlist, c->d_vcount, c->d_vorder, c->d_vslot, c->d_vanchor, c->d_vpos, c->d_vposg,
-                    c->d_vxref, c->d_vdmax, c->d_vshift};
+                    c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi, c->d_vlo,
+                    c->d_vposg, c->d_vxref, c->d_vdmax};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -654,9 +663,9 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         const bool cells = cfg->path == MD_PATH_CELLS || cfg->path == MD_PATH_VERLET ||
                            (cfg->path == MD_PATH_AUTO && P.rcut > 0 && maxn >= kAutoCellsMinAtoms);
         c->path = cfg->path == MD_PATH_VERLET ? 2 : (cells ? 1 : 0);
-        if (c->path == 2 && c->npad >= (1 << 26)) {
+        if (c->path == 2 && c->ntot >= (1 << 26)) {
             delete c;
-            return fail(nullptr, MD_ERR_INVALID, "the neighbour-list path takes at most 2^26 padded atoms");
+            return fail(nullptr, MD_ERR_INVALID, "the neighbour-list path takes at most 2^26 atoms");
         }
         // the neighbour lists hold the pairs within rcut + skin, so their cells are sized by that
         if (cells && !make_grids(c, pos, mass, c->path == 2 ? P.rcut + kSkin : P.rcut)) {
@@ -759,35 +768,23 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         const size_t ns = (size_t)c->ntot;
         CKC(cudaMalloc(&c->d_vlist, sizeof(int32_t) * kVMax * ns));
         CKC(cudaMalloc(&c->d_vcount, sizeof(int32_t) * ns));
+        CKC(cudaMalloc(&c->d_vsub, sizeof(int32_t) * kVLanes * ns));
         CKC(cudaMalloc(&c->d_vorder, sizeof(int32_t) * ns));
+        CKC(cudaMalloc(&c->d_vslotof, sizeof(int32_t) * np));
         CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
-        CKC(cudaMalloc(&c->d_vanchor, sizeof(int32_t) * np));
-        CKC(cudaMalloc(&c->d_vpos, (size_t)vec4_size(c) * np));
-        CKC(cudaMalloc(&c->d_vposg, (size_t)vec4_size(c) * np));
-        CKC(cudaMalloc(&c->d_vxref, sizeof(double) * 3 * np));
+        CKC(cudaMalloc(&c->d_vhi, (size_t)vec4_size(c) * ns));
+        if (cfg->precision == MD_PREC_MIXED) CKC(cudaMalloc(&c->d_vlo, sizeof(float4) * ns));
+        CKC(cudaMalloc(&c->d_vposg, (size_t)vec4_size(c) * ns));
+        CKC(cudaMalloc(&c->d_vxref, sizeof(double) * 3 * ns));
         CKC(cudaMalloc(&c->d_vdmax, sizeof(uint32_t) * 2));
-        CKC(cudaMalloc(&c->d_vshift, (size_t)vec4_size(c) * 64 * n_clusters));
         CKC(cudaMemset(c->d_vdmax, 0, sizeof(uint32_t) * 2));
-        // every slot, count and entry starts as a valid atom index (atom 0, empty list)
+        // every slot, count and entry starts as a valid index (atom 0, empty list)
         CKC(cudaMemset(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns));
         CKC(cudaMemset(c->d_vcount, 0, sizeof(int32_t) * ns));
+        CKC(cudaMemset(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns));
         CKC(cudaMemset(c->d_vorder, 0, sizeof(int32_t) * ns));
-        CKC(cudaMemset(c->d_vanchor, 0, sizeof(int32_t) * np));
-        CKC(cudaMemset(c->d_vxref, 0, sizeof(double) * 3 * np));
-        // (a_i - a_j) h for the shift code (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4 of every cluster
-        std::vector<unsigned char> tab((size_t)vec4_size(c) * 64 * n_clusters, 0);
-        for (int b = 0; b < n_clusters; ++b)
-            for (int code = 0; code < 64; ++code) {
-                const double hb = c->grids[b].h;
-                const double v[4] = {((code & 3) - 1) * hb, (((code >> 2) & 3) - 1) * hb, (((code >> 4) & 3) - 1) * hb, 0.0};
-                if (cfg->precision == MD_PREC_MIXED) {
-                    const float f[4] = {(float)v[0], (float)v[1], (float)v[2], 0.f};
-                    memcpy(tab.data() + 16 * ((size_t)b * 64 + code), f, 16);
-                } else {
-                    memcpy(tab.data() + 32 * ((size_t)b * 64 + code), v, 32);
-                }
-            }
-        CKC(cudaMemcpy(c->d_vshift, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemset(c->d_vslotof, 0, sizeof(int32_t) * np));
+        CKC(cudaMemset(c->d_vxref, 0, sizeof(double) * 3 * ns));
     }
     for (int k = 0; k < 2; ++k) {
         CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));

@@ -28,6 +28,8 @@ constexpr int kMaxWarps = 16;
 constexpr int kMaxCluster = 8;
 constexpr int kCellCap = 256;   // atoms a cell of the cell-list path can hold
 constexpr int kVMax = 512;      // entries a neighbour list can hold
+constexpr int kVLog = 3;        // a list is split into kVLanes sub-lists, one per thread of its atom
+constexpr int kVLanes = 1 << kVLog;
 
 // Fields of an observable partial record (per 32-atom group).
 enum ObsField {
@@ -58,6 +60,7 @@ struct Item {
 struct CellGrid {
     int32_t G, off;
     double h, E, inv_h;
+    double frame;  // neighbour-list path: power-of-two shift S of the split FP32 coordinates
 };
 
 // Derived potential constants.
@@ -141,15 +144,16 @@ struct Dev {
     int32_t nslot;       // list slots (the real atoms, in cell order at the last rebuild)
     float vskin2h;       // (skin / 2)^2
     double vrl2;         // (rcut + skin)^2
-    int32_t* vlist;      // [kVMax][nslot] (j << 6) | shift code, ascending j within a slot
+    int32_t* vlist;      // [nslot][kVMax] slots of the neighbours, by (atom mod kVLanes, atom)
     int32_t* vcount;     // [nslot]
+    int32_t* vsub;       // [nslot][kVLanes] end of each sub-list (the entries j with j mod kVLanes = t)
     int32_t* vorder;     // [nslot] atom of each slot
+    int32_t* vslotof;    // [npad] slot of each atom
     int32_t* vslot;      // [1] slot counter of a rebuild
-    int32_t* vanchor;    // [npad] cell (x | y << 10 | z << 20) of each atom at the last rebuild
-    void* vpos;          // [npad] V4 (x - anchor cell centre, 0) in the pass precision
-    void* vposg;         // [npad] V4 (x - anchor cell centre, B6 rho^-1/2)
+    void* vhi;           // [nslot] V4 by slot: MIXED (hi part of x - o + S, 0); FP64 (x, y, z, 0)
+    float4* vlo;         // [nslot] MIXED: low part of x - o + S
+    void* vposg;         // [nslot] V4 (vhi.xyz, B6 rho^-1/2), written by the density pass
     double* vxref;       // [3][npad] positions at the last rebuild
-    const void* vshift;  // [B][64] V4 (a_i - a_j) h of each shift code (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4
     uint32_t* vdmax;     // [2] largest squared displacement since the rebuild (float bits), by step parity
 };
 
@@ -187,7 +191,7 @@ cudaError_t launch_cell_force(const Dev& d, int mode, int k_local, int flags, cu
 cudaError_t launch_cell_obs(const Dev& d, int from_state, int with_velocity, cudaStream_t s);
 cudaError_t launch_cell_ke(const Dev& d, cudaStream_t s);
 // Neighbour-list path (defined in scmd_verlet.cu).
-cudaError_t launch_v_anchor(const Dev& d, int k_local, cudaStream_t s);
+cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s);
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s);
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);

@@ -4,66 +4,81 @@
 // built. As long as no atom has moved more than skin / 2 since, every pair closer than rcut is in
 // the lists, so each pass tests only those entries (about (rcut + skin)^3 / rcut^3 of the pairs that
 // count, against ~4x for the octants of the cell-list path). Per MD step:
-//   k_v_anchor : every atom's offset from the centre of its cell at the last rebuild (its anchor),
-//                in the pass precision, and the largest squared displacement since the rebuild;
-//   rebuild, when that displacement exceeds (skin / 2)^2 (the kernels exit at once otherwise):
+//   k_v_pos    : every atom's pass coordinates, by list slot, and the largest squared displacement
+//                since the last rebuild;
+//   rebuild, when that displacement exceeds the trigger (the kernels exit at once otherwise):
 //     the cell build of the cell-list path (clear, bin, sort), then
 //     k_v_build  : one CTA per home cell, the octant box staged in shared memory as in the
 //                  cell-list passes; every atom closer than rcut + skin is appended to the home
-//                  atom's list as (j << 6) | code, code = the cell offset a_i - a_j per axis + 1;
-//     k_v_sort   : one warp per list, a bitonic sort by j;
-//     k_v_commit : the new anchors, their offsets and the reference positions;
-//   k_v_density, k_v_force : one thread per list (atoms in cell order, for cache locality).
-// A pair's separation is (o_i - o_j) + (a_i - a_j) h, with o the anchor offsets and the shift taken
-// from a per-cluster table of the 27 codes (exact in FP32: h is a binary32 value and |a_i - a_j| <= 1).
-// Results do not depend on when the lists were built: a list holds every pair inside rcut in
-// ascending j, a pair outside rcut is masked (r2 := inf) and adds an exact zero, and the pass-precision
-// partial sums are folded every kSpanV pairs *inside rcut*. Resuming from a checkpoint (which rebuilds
+//                  atom's list. The home cell's atoms take consecutive slots (cell order);
+//     k_v_sort   : one warp per list, a bitonic sort by (j mod kVLanes, j), the atoms turned into
+//                  their slots, and the ends of the kVLanes sub-lists;
+//     k_v_commit : the pass coordinates in the new slot order and the reference positions;
+//   k_v_density, k_v_force : kVLanes threads per atom, thread t over sub-list t.
+// MIXED pass coordinates are x - o + S split into FP32 high and low parts, S a power of two with
+// every coordinate of the cluster in [32, 2S): the high parts of two atoms less than 16 A apart
+// differ exactly, and dx = (hi_i - hi_j) + (lo_i - lo_j) is within about one rounding of the FP64
+// separation. FP64 passes read the positions themselves.
+// Results do not depend on when the lists were built: what a thread sums is the pairs inside rcut
+// whose j is in its residue class, in ascending j (a pair outside rcut is masked to r2 = inf and
+// adds an exact zero); its pass-precision partial sums are folded every kSpanV pairs inside rcut;
+// and the kVLanes partials are added in a fixed tree. Resuming from a checkpoint (which rebuilds
 // the lists) therefore reproduces an uninterrupted run bit for bit, as on the other paths.
 #include "scmd_cells.cuh"
 
 namespace scmd {
 
-constexpr int kSpanV = 128;       // pairs inside rcut summed in the pass precision before a fold
+constexpr int kSpanV = 64;  // pairs inside rcut a thread sums in the pass precision before a fold
 constexpr int kVThreads = 256;
 template <int PREC> struct BuildChunk;  // staged atoms per chunk of the list build (48 KB static limit)
 template <> struct BuildChunk<1> { static constexpr int TJ = 1536; };
 template <> struct BuildChunk<0> { static constexpr int TJ = 768; };
+static_assert(kVLog >= 1 && kVLog <= 4, "an atom's threads must sit in one warp");
 
-__device__ __forceinline__ int anchor_pack(int x, int y, int z) { return x | (y << 10) | (z << 20); }
+// Pass coordinates of atom i at slot s (see the top of the file).
+template <int PREC>
+__device__ __forceinline__ void v_store(const Dev& d, int s, int i, double x, double y, double z) {
+    if (PREC == 1) {
+        const int cl = d.cl_of_group[i >> 5];
+        const double* o = d.origin + 3 * cl;
+        const double S = d.grid[cl].frame;
+        const double ux = (x - o[0]) + S, uy = (y - o[1]) + S, uz = (z - o[2]) + S;
+        float4 h, l;
+        h.x = (float)ux;
+        h.y = (float)uy;
+        h.z = (float)uz;
+        h.w = 0.f;
+        l.x = (float)(ux - (double)h.x);
+        l.y = (float)(uy - (double)h.y);
+        l.z = (float)(uz - (double)h.z);
+        l.w = 0.f;
+        reinterpret_cast<float4*>(d.vhi)[s] = h;
+        d.vlo[s] = l;
+    } else {
+        reinterpret_cast<double4*>(d.vhi)[s] = make_double4(x, y, z, 0.0);
+    }
+}
 
 // ---------------------------------------------------------------- every step
-// Offsets from the anchor cells' centres, and the largest squared displacement since the rebuild
-// under the step's parity (the other parity's slot is cleared for the next step).
-template <int PREC> __global__ void k_v_anchor(const Dev d, int k_local) {
-    using V4 = typename Tr<PREC>::V4;
-    using R = typename Tr<PREC>::R;
+// Pass coordinates, and the largest squared displacement since the rebuild under the step's parity
+// (the other parity's slot is cleared for the next step).
+template <int PREC> __global__ void k_v_pos(const Dev d, int k_local) {
     pdl_launch_dependents();
     pdl_wait();
     const int64_t step = *d.step_base + k_local;
     if (blockIdx.x == 0 && threadIdx.x == 0) d.vdmax[(step + 1) & 1] = 0u;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     float dmax = 0.f;
-    if (i < d.npad) {
-        const int cl = d.cl_of_group[i >> 5];
-        if (i - d.poff[cl] < d.nreal[cl]) {
-            const CellGrid g = d.grid[cl];
-            const double* o = d.origin + 3 * cl;
-            const int np = d.npad, a = d.vanchor[i];
-            const double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
-            V4 p;
-            p.x = (R)(x - (o[0] + cell_centre(a & 1023, g)));
-            p.y = (R)(y - (o[1] + cell_centre((a >> 10) & 1023, g)));
-            p.z = (R)(z - (o[2] + cell_centre(a >> 20, g)));
-            p.w = R(0);
-            reinterpret_cast<V4*>(d.vpos)[i] = p;
-            const double ex = x - d.vxref[i], ey = y - d.vxref[np + i], ez = z - d.vxref[2 * np + i];
-            dmax = (float)(ex * ex + ey * ey + ez * ez);
-            if (!(dmax <= 3.0e38f)) dmax = 3.0e38f;  // non-finite positions force a rebuild
-        }
+    if (s < d.nslot) {
+        const int np = d.npad, ns = d.nslot, i = d.vorder[s];
+        const double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
+        v_store<PREC>(d, s, i, x, y, z);
+        const double ex = x - d.vxref[s], ey = y - d.vxref[ns + s], ez = z - d.vxref[2 * ns + s];
+        dmax = (float)(ex * ex + ey * ey + ez * ez);
+        if (!(dmax <= 3.0e38f)) dmax = 3.0e38f;  // non-finite positions force a rebuild
     }
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, s));
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if ((threadIdx.x & 31) == 0 && dmax > 0.f) atomicMax(d.vdmax + (step & 1), __float_as_uint(dmax));
 }
 
@@ -77,7 +92,6 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
     constexpr int TJ = BuildChunk<PREC>::TJ;
     __shared__ V4 spos[TJ];
     __shared__ int sidx[TJ];
-    __shared__ unsigned char scode[TJ];
     __shared__ int s_src[kBoxN], s_cnt[kBoxN], s_pref[kBoxN + 1];
     __shared__ int2 s_runs[8][25];
     __shared__ int s_len[kCellCap];
@@ -88,15 +102,18 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
     const int c = d.cell_order[blockIdx.x];
     const int hc = min(d.cell_count[c], kCellCap);
     if (hc == 0) return;
-    const int cl = d.cell_cl[c];
-    const CellGrid g = d.grid[cl];
+    const CellGrid g = d.grid[d.cell_cl[c]];
     const V4* cp = reinterpret_cast<const V4*>(d.cpos);
     const int M = octant_box(d, c, g, s_src, s_cnt, s_pref);
     for (int k = threadIdx.x; k < hc; k += blockDim.x) s_len[k] = 0;
     if (threadIdx.x == 0) s_base = atomicAdd(d.vslot, hc);
     __syncthreads();
-    const int base = s_base, ns = d.nslot;
-    for (int k = threadIdx.x; k < hc; k += blockDim.x) d.vorder[base + k] = d.cell_atoms[(size_t)c * kCellCap + k];
+    const int base = s_base;
+    for (int k = threadIdx.x; k < hc; k += blockDim.x) {
+        const int a = d.cell_atoms[(size_t)c * kCellCap + k];
+        d.vorder[base + k] = a;
+        d.vslotof[a] = base + k;
+    }
     const R rl2 = (R)d.vrl2, h = (R)g.h;
     const int nblk = oct_blocks(d, c), w = threadIdx.x >> 5;
     bool overflow = false;
@@ -105,15 +122,14 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
         const int k_home = q.s0 + blk * 32 + q.is;  // the home atom's place in its cell
         const V4 pi = q.nb > 0 ? cp[(size_t)c * kCellCap + k_home] : V4{};
         const int self = s_pref[q.home_t] + blk * 32 + q.is;
-        int* list = d.vlist + base + k_home;
+        int* list = d.vlist + (size_t)(base + k_home) * kVMax;
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
-            for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {  // stage positions, atoms and codes
+            for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {  // stage atoms, shifted to the home cell
                 const int a = max(s_pref[t], e0), b = min(s_pref[t + 1], e0 + ne);
                 const int dx = (t % kBox) / 2 - 1, dy = ((t / kBox) % kBox) / 2 - 1, dz = (t / (kBox * kBox)) / 2 - 1;
                 const R sx = (R)dx * h, sy = (R)dy * h, sz = (R)dz * h;
-                const unsigned char code = (unsigned char)((1 - dx) | ((1 - dy) << 2) | ((1 - dz) << 4));
                 for (int e = a; e < b; ++e) {
                     const int src = s_src[t] + (e - s_pref[t]);
                     V4 p = cp[src];
@@ -122,7 +138,6 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
                     p.z += sz;
                     spos[e - e0] = p;
                     sidx[e - e0] = d.cell_atoms[src];
-                    scode[e - e0] = code;
                 }
             }
             __syncthreads();
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
                     if (r2 < rl2 && e != selfl) {
                         const int slot = atomicAdd(&s_len[k_home], 1);
                         if (slot < kVMax)
-                            list[(size_t)slot * ns] = (sidx[e] << 6) | scode[e];
+                            list[slot] = sidx[e];
                         else
                             overflow = true;
                     }
@@ -153,8 +168,10 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
     for (int k = threadIdx.x; k < hc; k += blockDim.x) d.vcount[base + k] = min(s_len[k], kVMax);
 }
 
-// One warp per list: a bitonic sort of its entries (by j, which sits in the high bits).
+// One warp per list: a bitonic sort of its entries by the key (j mod kVLanes, j); then the atoms
+// are replaced by their slots and the end of every residue class is recorded.
 __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int k_local) {
+    constexpr int HB = 32 - kVLog;  // the residue sits in the top kVLog bits of a key
     __shared__ uint32_t buf[kVThreads / 32][kVMax];
     pdl_launch_dependents();
     pdl_wait();
@@ -162,12 +179,15 @@ __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * (kVThreads / 32) + w;
     if (s >= d.nslot) return;
-    const int n = d.vcount[s], ns = d.nslot;
+    const int n = d.vcount[s];
     int P = 32;
     while (P < n) P <<= 1;
     uint32_t* b = buf[w];
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(d.vlist) + s;
-    for (int e = lane; e < P; e += 32) b[e] = e < n ? src[(size_t)e * ns] : 0xffffffffu;
+    int* row = d.vlist + (size_t)s * kVMax;
+    for (int e = lane; e < P; e += 32) {
+        const uint32_t j = e < n ? (uint32_t)row[e] : 0u;
+        b[e] = e < n ? ((j & (kVLanes - 1)) << HB) | (j >> kVLog) : 0xffffffffu;
+    }
     __syncwarp();
     for (int k = 2; k <= P; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -183,65 +203,89 @@ __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int
             }
             __syncwarp();
         }
-    uint32_t* dst = reinterpret_cast<uint32_t*>(d.vlist) + s;
-    for (int e = lane; e < n; e += 32) dst[(size_t)e * ns] = b[e];
+    for (int e = lane; e < n; e += 32) {
+        const uint32_t key = b[e];
+        const uint32_t j = ((key & ((1u << HB) - 1)) << kVLog) | (key >> HB);
+        row[e] = d.vslotof[j];
+    }
+    if (lane < kVLanes) {  // end of class `lane`: the first key of a higher class
+        const uint32_t bound = (uint32_t)(lane + 1) << HB;
+        int lo = 0, hi = n;
+        if (lane == kVLanes - 1) lo = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (b[mid] < bound) lo = mid + 1; else hi = mid;
+        }
+        d.vsub[(size_t)s * kVLanes + lane] = lo;
+    }
 }
 
-// New anchors (the cell each atom was binned into by this rebuild), their offsets and the positions
-// the next displacements are measured from.
+// Pass coordinates in the new slot order and the positions the next displacements are measured from.
 template <int PREC> __global__ void k_v_commit(const Dev d, int cond, int k_local) {
-    using V4 = typename Tr<PREC>::V4;
-    using R = typename Tr<PREC>::R;
     pdl_launch_dependents();
     pdl_wait();
     if (cond && !vlist_rebuild_due(d, k_local)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.npad) return;
-    const int cl = d.cl_of_group[i >> 5];
-    if (i - d.poff[cl] >= d.nreal[cl]) return;
-    const CellGrid g = d.grid[cl];
-    const double* o = d.origin + 3 * cl;
-    const int np = d.npad;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.nslot) return;
+    const int np = d.npad, ns = d.nslot, i = d.vorder[s];
     const double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
-    const int cx = cell_axis(x - o[0], g), cy = cell_axis(y - o[1], g), cz = cell_axis(z - o[2], g);
-    d.vanchor[i] = anchor_pack(cx, cy, cz);
-    d.vxref[i] = x;
-    d.vxref[np + i] = y;
-    d.vxref[2 * np + i] = z;
-    V4 p;
-    p.x = (R)(x - (o[0] + cell_centre(cx, g)));
-    p.y = (R)(y - (o[1] + cell_centre(cy, g)));
-    p.z = (R)(z - (o[2] + cell_centre(cz, g)));
-    p.w = R(0);
-    reinterpret_cast<V4*>(d.vpos)[i] = p;
+    v_store<PREC>(d, s, i, x, y, z);
+    d.vxref[s] = x;
+    d.vxref[ns + s] = y;
+    d.vxref[2 * ns + s] = z;
 }
 
 // ---------------------------------------------------------------- passes
+// Separation of the atoms at slots a (coordinates pa, la) and q.
+template <int PREC>
+__device__ __forceinline__ void v_sep(const Dev& d, const typename Tr<PREC>::V4& pa, const float4& la,
+                                      const typename Tr<PREC>::V4& pq, int q, typename Tr<PREC>::R& dx,
+                                      typename Tr<PREC>::R& dy, typename Tr<PREC>::R& dz) {
+    if (PREC == 1) {
+        const float4 lq = d.vlo[q];
+        dx = (pa.x - pq.x) + (la.x - lq.x);
+        dy = (pa.y - pq.y) + (la.y - lq.y);
+        dz = (pa.z - pq.z) + (la.z - lq.z);
+    } else {
+        dx = pa.x - pq.x;
+        dy = pa.y - pq.y;
+        dz = pa.z - pq.z;
+    }
+}
+
+// The sum of a double over the kVLanes threads of an atom, in a fixed tree (every thread gets it).
+__device__ __forceinline__ double v_group_sum(double v) {
+    const unsigned mask = ((1u << kVLanes) - 1u) << (threadIdx.x & 31 & ~(kVLanes - 1));
+#pragma unroll
+    for (int o = 1; o < kVLanes; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
 template <int PREC, int SPECIAL>
 __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     pdl_launch_dependents();
     pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.nslot) return;
-    const int i = d.vorder[s], n = d.vcount[s], ns = d.nslot;
-    const int cl = d.cl_of_group[i >> 5];
-    const V4* vp = reinterpret_cast<const V4*>(d.vpos);
-    const V4* sh = reinterpret_cast<const V4*>(d.vshift) + 64 * cl;
-    const V4 pi = vp[i];
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = gt >> kVLog, t = gt & (kVLanes - 1);
+    if (s >= d.nslot) return;  // whole atoms leave together
+    const V4* vp = reinterpret_cast<const V4*>(d.vhi);
+    const V4 pi = vp[s];
+    const float4 li = PREC == 1 ? d.vlo[s] : float4{};
+    const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
     const R rc2 = (R)d.pot.rcut2;
     const int mexp = d.pot.m;
-    const int* lst = d.vlist + s;
+    const int* lst = d.vlist + (size_t)s * kVMax;
     f2sum facc = {0.f, 0.f};
     double racc = 0.0;
     R tacc = R(0);
     int cnt = 0;
 #pragma unroll 4
-    for (int e = 0; e < n; ++e) {
-        const uint32_t q = (uint32_t)lst[(size_t)e * ns];
-        const V4 pj = vp[q >> 6], t = sh[q & 63];
-        const R dx = (pi.x - pj.x) + t.x, dy = (pi.y - pj.y) + t.y, dz = (pi.z - pj.z) + t.z;
+    for (int e = beg; e < end; ++e) {
+        const int q = lst[e];
+        R dx, dy, dz;
+        v_sep<PREC>(d, pi, li, vp[q], q, dx, dy, dz);
         R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const bool in = r2 < rc2;
         r2 = in ? r2 : big<R>();
@@ -268,7 +312,9 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     } else {
         racc += (double)tacc;
     }
-    const double rho = racc * d.pot.am;
+    const double rho = v_group_sum(racc) * d.pot.am;
+    if (t != 0) return;
+    const int i = d.vorder[s];
     d.rho[i] = rho;
     V4 p = pi;
     if (PREC == 1) {
@@ -279,7 +325,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     } else {
         p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
     }
-    reinterpret_cast<V4*>(d.vposg)[i] = p;
+    reinterpret_cast<V4*>(d.vposg)[s] = p;
     if (obs) d.eatom[2 * i] = -d.pot.eps * d.pot.c * sqrt(rho);
 }
 
@@ -291,25 +337,26 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
     using V4 = typename Tr<PREC>::V4;
     pdl_launch_dependents();
     pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.nslot) return;
-    const int i = d.vorder[s], n = d.vcount[s], ns = d.nslot;
-    const int cl = d.cl_of_group[i >> 5];
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = gt >> kVLog, t = gt & (kVLanes - 1);
+    if (s >= d.nslot) return;  // whole atoms leave together
     const V4* vp = reinterpret_cast<const V4*>(d.vposg);
-    const V4* sh = reinterpret_cast<const V4*>(d.vshift) + 64 * cl;
-    const V4 pi = vp[i];
+    const V4 pi = vp[s];
+    const float4 li = PREC == 1 ? d.vlo[s] : float4{};
+    const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
     const R A = (R)d.pot.A9;
     const R rc2 = (R)d.pot.rcut2;
     const int nexp = d.pot.n, mexp = d.pot.m;
-    const int* lst = d.vlist + s;
+    const int* lst = d.vlist + (size_t)s * kVMax;
     R fx = R(0), fy = R(0), fz = R(0), sx = R(0), sy = R(0), sz = R(0), se = R(0);
     double ea = 0.0;
     int cnt = 0;
 #pragma unroll 4
-    for (int e = 0; e < n; ++e) {
-        const uint32_t q = (uint32_t)lst[(size_t)e * ns];
-        const V4 pj = vp[q >> 6], t = sh[q & 63];
-        const R dx = (pi.x - pj.x) + t.x, dy = (pi.y - pj.y) + t.y, dz = (pi.z - pj.z) + t.z;
+    for (int e = beg; e < end; ++e) {
+        const int q = lst[e];
+        const V4 pj = vp[q];
+        R dx, dy, dz;
+        v_sep<PREC>(d, pi, li, pj, q, dx, dy, dz);
         R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const bool in = r2 < rc2;
         r2 = in ? r2 : big<R>();
@@ -342,8 +389,13 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
             cnt = 0;
         }
     }
-    const R Fx = fx + sx, Fy = fy + sy, Fz = fz + sz;
-    const double Ep = ea + (double)se;
+    const double gx = v_group_sum((double)(fx + sx));
+    const double gy = v_group_sum((double)(fy + sy));
+    const double gz = v_group_sum((double)(fz + sz));
+    const double Ep = ENERGY ? v_group_sum(ea + (double)se) : 0.0;
+    if (t != 0) return;
+    const R Fx = (R)gx, Fy = (R)gy, Fz = (R)gz;
+    const int i = d.vorder[s];
     const int np = d.npad;
     R* fo = reinterpret_cast<R*>(d.f);
     fo[i] = Fx;
@@ -353,6 +405,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
     if (ENERGY) d.eatom[2 * i + 1] = Ep;
     if (mode != 2) return;
     const Run& r = *d.run;
+    const int cl = d.cl_of_group[i >> 5];
     const double hs = d.hs[i];
     const double vx = fma(hs, (double)Fx, d.v[i]);
     const double vy = fma(hs, (double)Fy, d.v[np + i]);
@@ -373,25 +426,30 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
 }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_v_anchor(const Dev& d, int k_local, cudaStream_t s) {
-    const int grid = (d.npad + kVThreads - 1) / kVThreads;
-    return d.prec == 1 ? launch_ex(k_v_anchor<1>, grid, kVThreads, 0, 0, s, d, k_local)
-                       : launch_ex(k_v_anchor<0>, grid, kVThreads, 0, 0, s, d, k_local);
+cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s) {
+    const int grid = (d.nslot + kVThreads - 1) / kVThreads;
+    return d.prec == 1 ? launch_ex(k_v_pos<1>, grid, kVThreads, 0, 0, s, d, k_local)
+                       : launch_ex(k_v_pos<0>, grid, kVThreads, 0, 0, s, d, k_local);
 }
 
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s) {
     cudaError_t e = d.prec == 1 ? launch_ex(k_v_build<1>, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local)
                                 : launch_ex(k_v_build<0>, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
-    e = launch_ex(k_v_sort, (d.nslot + 7) / 8, kVThreads, 0, 0, s, d, cond, k_local);
+    e = launch_ex(k_v_sort, (d.nslot + kVThreads / 32 - 1) / (kVThreads / 32), kVThreads, 0, 0, s, d, cond,
+                  k_local);
     if (e != cudaSuccess) return e;
-    const int grid = (d.npad + kVThreads - 1) / kVThreads;
+    const int grid = (d.nslot + kVThreads - 1) / kVThreads;
     return d.prec == 1 ? launch_ex(k_v_commit<1>, grid, kVThreads, 0, 0, s, d, cond, k_local)
                        : launch_ex(k_v_commit<0>, grid, kVThreads, 0, 0, s, d, cond, k_local);
 }
 
+static int v_pass_grid(const Dev& d) {
+    return (int)(((int64_t)d.nslot * kVLanes + kVThreads - 1) / kVThreads);
+}
+
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s) {
-    const int grid = (d.nslot + kVThreads - 1) / kVThreads;
+    const int grid = v_pass_grid(d);
     const bool sp = d.pot.special != 0;
     if (d.prec == 1)
         return sp ? launch_ex(k_v_density<1, 1>, grid, kVThreads, 0, 0, s, d, obs)
@@ -402,7 +460,7 @@ cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s) {
 
 template <int PREC, int ENERGY>
 static cudaError_t v_force_e(const Dev& d, int mode, int k, int last, cudaStream_t s) {
-    const int grid = (d.nslot + kVThreads - 1) / kVThreads;
+    const int grid = v_pass_grid(d);
     return d.pot.special ? launch_ex(k_v_force<PREC, 1, ENERGY>, grid, kVThreads, 0, 0, s, d, mode, k, last)
                          : launch_ex(k_v_force<PREC, 0, ENERGY>, grid, kVThreads, 0, 0, s, d, mode, k, last);
 }

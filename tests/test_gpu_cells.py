@@ -276,9 +276,12 @@ def test_cells_invalid_configurations(scmd):
     with pytest.raises(scmd.ScmdError) as e:
         make(scmd, [55], pos, rcut=0.0, path=CELLS)
     assert e.value.status == scmd.MD_ERR_INVALID
-    with pytest.raises(scmd.ScmdError) as e:  # cells of side >= 20 A would hold > 256 atoms
-        make(scmd, [55], pos, rcut=20.0, path=CELLS)
+    big = inputs.fcc_sphere(2000)
+    with pytest.raises(scmd.ScmdError) as e:  # cells of side >= 20 A would hold > 256 of its atoms
+        make(scmd, [2000], big, rcut=20.0, path=CELLS)
     assert e.value.status == scmd.MD_ERR_INVALID
+    tiny = make(scmd, [55], pos, rcut=20.0, path=CELLS)  # a cluster of fewer atoms than a cell holds
+    assert scmd.md_get_path(tiny) == CELLS
     ctx = make(scmd, [55], pos, rcut=20.0, path=ALLPAIRS)  # the all-pairs path takes any cutoff
     assert scmd.md_get_path(ctx) == ALLPAIRS and scmd.md_launch_counts(ctx)[0] == 2
     small = make(scmd, [55], pos, rcut=8.8)  # automatic choice: a small cluster keeps all pairs

@@ -132,8 +132,8 @@ def test_verlet_checkpoint_resume_is_bitwise(scmd, prec):
 
 
 def test_verlet_matches_cells_bitwise_free(scmd):
-    """Same input, both cutoff paths, MIXED: the same pairs, different coordinate frames (offsets from
-    build-time anchors against cell centres): agreement at the MIXED tolerance."""
+    """Same input, both cutoff paths, MIXED: the same pairs, different coordinate frames (split
+    global coordinates against offsets from cell centres): agreement at the MIXED tolerance."""
     pos = lattice(3000, 34)
     a = make(scmd, [3000], pos, prec=MIXED, rcut=RC, path=VERLET)
     b = make(scmd, [3000], pos, prec=MIXED, rcut=RC, path=CELLS)
