@@ -7,6 +7,8 @@ CPU-baseline leg of ``bench.py`` may import this package. The product library
 Every function follows the plain definitions of the paper (Eq. 1 energy, Eq. 2
 density, the derivative of Eq. 1 for forces, velocity Verlet with a Langevin
 thermostat, Sec. II "Computational approach"); see the C source for each.
+The structural observables of Sec. III (central-atom pair distances, mean squared
+displacement, common-neighbour analysis) are in structure_oracle.c.
 """
 from __future__ import annotations
 
@@ -18,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "sc_oracle.c")
+_SRCS = [os.path.join(_HERE, "sc_oracle.c"), os.path.join(_HERE, "structure_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -26,11 +28,12 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile sc_oracle.c with gcc (-O2, IEEE double, OpenMP) into oracle/_build."""
+    """Compile the C sources with gcc (-O2, IEEE double evaluated as written, OpenMP) into oracle/_build."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", *_SRCS, "-o", tmp,
+               "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -79,6 +82,15 @@ def _load():
             lib.orc_md_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _DP, _DP, _DP,
                                          _DP, ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_double, ctypes.POINTER(Thermostat)]
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.ors_com.argtypes = [ctypes.c_int, _DP, _DP, _DP]
+            lib.ors_rdf.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int64), i32p]
+            lib.ors_msd.argtypes = [ctypes.c_int, _DP, _DP, _DP, ctypes.c_double, i32p]
+            lib.ors_msd.restype = ctypes.c_double
+            lib.ors_cna_signature.argtypes = [ctypes.c_int, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                              i32p]
+            lib.ors_cna.argtypes = [ctypes.c_int, _DP, ctypes.c_double, i32p, i32p]
             _lib = lib
     return _lib
 
@@ -170,6 +182,63 @@ def observables(pos, vel, mass, p: Params | None = None) -> dict:
     _load().orc_observables(len(pos), _dp(pos), _dp(vel), _dp(mass), ctypes.byref(p), ctypes.byref(o))
     return dict(epot=o.epot, ekin=o.ekin, etot=o.etot, T=o.T, com=np.array(o.com[:]),
                 mom=np.array(o.mom[:]), angmom=np.array(o.angmom[:]))
+
+
+# ---------------------------------------------------------------- structure (Sec. III)
+CNA_OTHER, CNA_FCC, CNA_HCP, CNA_ICO = 0, 1, 2, 3
+
+
+def _i32p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def com(pos, mass) -> np.ndarray:
+    """Centre of mass sum m x / sum m."""
+    pos = _pos(pos)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    X = np.zeros(3)
+    _load().ors_com(len(pos), _dp(pos), _dp(mass), _dp(X))
+    return X
+
+
+def rdf(pos, mass, r_core: float, bin_A: float, nbins: int):
+    """(counts[nbins], n_core): pair distances from the atoms within r_core of the centre of mass to
+    every other atom, histogrammed in bins of bin_A."""
+    pos = _pos(pos)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    counts = np.zeros(int(nbins), dtype=np.int64)
+    nc = np.zeros(1, dtype=np.int32)
+    _load().ors_rdf(len(pos), _dp(pos), _dp(mass), float(r_core), float(bin_A), int(nbins),
+                    counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _i32p(nc))
+    return counts, int(nc[0])
+
+
+def msd(pos, ref, mass, r_core: float = 0.0):
+    """(MSD in A^2, atoms averaged): displacement from ref with the centre-of-mass motion removed, over
+    the atoms within r_core of the reference centre of mass (all atoms if r_core <= 0)."""
+    pos = _pos(pos)
+    ref = _pos(ref)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    n = np.zeros(1, dtype=np.int32)
+    v = _load().ors_msd(len(pos), _dp(pos), _dp(ref), _dp(mass), float(r_core), _i32p(n))
+    return v, int(n[0])
+
+
+def cna_signature(pos, i: int, j: int, r_nb: float = 3.0):
+    """Common-neighbour signature (k, b, l) of the pair i-j."""
+    pos = _pos(pos)
+    out = np.zeros(3, dtype=np.int32)
+    _load().ors_cna_signature(len(pos), _dp(pos), float(r_nb), int(i), int(j), _i32p(out))
+    return tuple(int(x) for x in out)
+
+
+def cna(pos, r_nb: float = 3.0):
+    """(class[N], neighbours[N]): CNA_FCC / CNA_HCP / CNA_ICO / CNA_OTHER per atom."""
+    pos = _pos(pos)
+    cls = np.zeros(len(pos), dtype=np.int32)
+    nnb = np.zeros(len(pos), dtype=np.int32)
+    _load().ors_cna(len(pos), _dp(pos), float(r_nb), _i32p(cls), _i32p(nnb))
+    return cls, nnb
 
 
 def thermostat(kind=NVE, T0=0.0, T1=None, gamma_ps=1.0, tau_ps=0.1, seed=0) -> Thermostat:
