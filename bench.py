@@ -289,7 +289,9 @@ def main():
         cfg.tune = 0
     rcut = w.get("rcut", 0.0)
     ctx = scmd.md_create(cfg, sizes, w["pos"], w["vel"], w["mass"], scmd.sc_params(rcut=rcut))
-    cells = scmd.md_get_path(ctx) == scmd.MD_PATH_CELLS
+    path = scmd.md_get_path(ctx)
+    cells = path in (scmd.MD_PATH_CELLS, scmd.MD_PATH_VERLET)  # a cutoff path
+    path_name = {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists"}.get(path, "all pairs")
     if args.shapes:
         v = [int(x) for x in args.shapes.split(",")]
         scmd.md_set_launch(ctx, 0, *v[0:3])
@@ -357,7 +359,7 @@ def main():
 
     # pass timings with CUDA events on the library's stream (same state, same launch shapes)
     ms_d, ms_f, pairs = scmd.md_time_passes(ctx, 50)
-    if cells:  # pairs tested by the cell list at the final state (27 neighbour cells per atom)
+    if cells:  # pairs tested at the final state (octants of the cell list, or list entries)
         pairs_per_eval = pairs
     pair_rate = pairs_per_eval * md_steps_total * world / t_max
     peak_clock = (clocks or {}).get("sm_max_mhz", 2070.0)
@@ -442,8 +444,10 @@ def main():
             e1.record(stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
+        p64 = scmd.md_get_path(c64)
         fp64 = {"value": natoms * m64 * reps64 / t64, "unit": UNIT,
-                "pair_evals_per_s": pairs_per_eval * m64 * reps64 / t64,
+                "pair_evals_per_s": (useful_pairs if cells else pairs_per_eval) * m64 * reps64 / t64,
+                "path": {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists"}.get(p64, "all pairs"),
                 "sample": f"{reps64} x {m64} MD steps, same state and thermostat, per GPU"}
         scmd.md_destroy(c64)
 
@@ -487,8 +491,8 @@ def main():
                        "md_steps_per_step": M, "dt_fs": dt, "precision": prec,
                        "l2": "flushed (256 MB write) before every timed iteration, outside the timed events",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "launch_shapes": {k: list(v) for k, v in shapes.items()} if not cells else "cell list",
-                       "rcut_A": rcut or None, "path": "cells" if cells else "all pairs",
+                       "launch_shapes": {k: list(v) for k, v in shapes.items()} if not cells else path_name,
+                       "rcut_A": rcut or None, "path": path_name,
                        "wall_s_timed_region": t_wall},
             "pair_evals_per_s": pair_rate if not cells else useful_pairs * md_steps_total * world / t_max,
             "candidate_pairs_per_s": pair_rate if cells else None,
@@ -500,7 +504,9 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": FORCE_DRAM_BYTES_PER_LAUNCH.get(args.config) if prec == "mixed" else None,
-                         "kernel": "k_cell_force (force pass, cell list)" if cells else "k_force (force pass)",
+                         "kernel": {"cells": "k_cell_force (force pass, cell list)",
+                                    "neighbour lists": "k_v_force (force pass, neighbour lists)"}.get(
+                                        path_name, "k_force (force pass)"),
                          "ms_per_launch": ms_f,
                          "density_pass_ms_per_launch": ms_d, "pairs_per_launch": alg_pairs,
                          "tested_pairs_per_launch": pairs if cells else None,

@@ -65,8 +65,8 @@ typedef enum {
 } md_precision;
 
 typedef enum {
-    MD_PATH_AUTO = 0,     /* cells when rcut_A > 0 and the largest cluster has >= 8192
-                             atoms, else all pairs                                       */
+    MD_PATH_AUTO = 0,     /* when rcut_A > 0 and the largest cluster has >= 8192 atoms:
+                             cells in MIXED, neighbour lists in FP64; else all pairs     */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
     MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
     MD_PATH_VERLET = 3    /* per-atom neighbour lists (rcut_A + 1 A) built on the cell grid,
@@ -244,8 +244,8 @@ md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* 
  * steps) and per graph replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);
 
-/* The pair path the context runs (MD_PATH_ALLPAIRS or MD_PATH_CELLS; MD_PATH_AUTO is resolved at
- * create time) into *path. */
+/* The pair path the context runs (MD_PATH_ALLPAIRS, MD_PATH_CELLS or MD_PATH_VERLET;
+ * MD_PATH_AUTO is resolved at create time) into *path. */
 md_status md_get_path(const md_ctx* ctx, int32_t* path);
 
 /* Last error message of ctx, or of the calling thread's last failed md_create when ctx is NULL. */
@@ -294,6 +294,44 @@ md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int
  */
 md_status md_energy_forces_noalloc(const double* pos_dev, int32_t n_atoms, const md_sc_params* params,
                                    double* forces_dev, double* epot_dev, uint64_t stream);
+
+/* ------------------------------------------------------------------------
+ * Structural observables (Sec. III), computed on the device from the current
+ * positions; only the small results are copied back. Distances that decide a
+ * bin or a neighbour are evaluated in FP64 as dx = x_i - x_j per axis,
+ * r^2 = (dx dx + dy dy) + dz dz, r = sqrt(r^2), each step rounded once.
+ * ------------------------------------------------------------------------ */
+
+/* Pair-distance histogram of the central atoms of every cluster (the g(r) of
+ * the atoms near the centre, Sec. III). The core of cluster b is its atoms
+ * closer than r_core_A to its centre of mass; every ordered pair (c, j), c in
+ * the core and j any other atom of b, adds one to counts[b][floor(r_cj / bin_A)]
+ * when that is below nbins. counts[n_clusters][nbins] (host, overwritten);
+ * n_core[n_clusters] (host, may be NULL). nbins in 1..8192, bin_A > 0,
+ * r_core_A >= 0; else MD_ERR_INVALID. Accumulate frames on the host. */
+md_status md_rdf(md_ctx* ctx, double r_core_A, double bin_A, int32_t nbins, int64_t* counts, int32_t* n_core);
+
+/* Store the current positions as the reference of md_msd. The atoms averaged
+ * are those closer than r_core_A to their cluster's centre of mass now (every
+ * atom when r_core_A <= 0). */
+md_status md_msd_reference(md_ctx* ctx, double r_core_A);
+
+/* Mean squared displacement since the reference, with each cluster's
+ * centre-of-mass motion removed: msd_A2[b] = mean over the selected atoms of
+ * |(x_i - X) - (x0_i - X0)|^2 (X the centre of mass), in A^2; n_atoms[b] (may be
+ * NULL) the atoms averaged. MD_ERR_STATE before any md_msd_reference. */
+md_status md_msd(md_ctx* ctx, double* msd_A2, int32_t* n_atoms);
+
+/* Common-neighbour analysis (Honeycutt and Andersen 1987; the crystalline
+ * fraction of the cluster). Atoms closer than r_nb_A are neighbours; a bond i-j
+ * has the signature (common neighbours, bonds among them, bonds in the largest
+ * connected set of those). An atom with exactly 12 neighbours is fcc when all 12
+ * signatures are 421, hcp when six are 421 and six 422, icosahedral when all are
+ * 555; every other atom is "other". counts[n_clusters][4] (host): atoms that are
+ * other, fcc, hcp, icosahedral. cls[Ntot] (host, may be NULL): 0..3 per atom.
+ * capped[n_clusters] (host, may be NULL): atoms counted as other only because a
+ * neighbour has more than 32 neighbours (none in a condensed metal at 3 A). */
+md_status md_cna(md_ctx* ctx, double r_nb_A, int32_t* counts, int8_t* cls, int32_t* capped);
 
 #ifdef __cplusplus
 }

@@ -86,6 +86,10 @@ struct md_ctx {
     CellGrid* d_grid = nullptr;
     int32_t *d_cell_cl = nullptr, *d_cell_count = nullptr, *d_cell_atoms = nullptr, *d_cell_order = nullptr;
     int32_t* d_cell_oct = nullptr;
+    // structural observables (allocated at first use)
+    StructBufs sb{};
+    int sb_nbins = 0;
+    bool msd_ref = false;
     // neighbour-list path
     int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vsub = nullptr, *d_vorder = nullptr, *d_vslotof = nullptr;
     int32_t* d_vslot = nullptr;
@@ -443,7 +447,9 @@ void free_all(md_ctx* c) {
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
                     c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
                     c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi, c->d_vlo,
-                    c->d_vposg, c->d_vxref, c->d_vdmax};
+                    c->d_vposg, c->d_vxref, c->d_vdmax,
+                    c->sb.com, c->sb.core, c->sb.ncore, c->sb.hist, c->sb.ref, c->sb.ref_com, c->sb.sel, c->sb.msd,
+                    c->sb.nsel, c->sb.nb, c->sb.nnb, c->sb.cls, c->sb.counts, c->sb.capped};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -660,9 +666,12 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     {
         int maxn = 0;
         for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
-        const bool cells = cfg->path == MD_PATH_CELLS || cfg->path == MD_PATH_VERLET ||
-                           (cfg->path == MD_PATH_AUTO && P.rcut > 0 && maxn >= kAutoCellsMinAtoms);
-        c->path = cfg->path == MD_PATH_VERLET ? 2 : (cells ? 1 : 0);
+        // automatic: with a cutoff and a large cluster, the cell list in MIXED (its passes read shared
+        // memory) and the neighbour lists in FP64 (whose pipe the tested pairs bound)
+        const bool big = cfg->path == MD_PATH_AUTO && P.rcut > 0 && maxn >= kAutoCellsMinAtoms;
+        const bool verlet = cfg->path == MD_PATH_VERLET || (big && cfg->precision == MD_PREC_FP64);
+        const bool cells = verlet || cfg->path == MD_PATH_CELLS || big;
+        c->path = verlet ? 2 : (cells ? 1 : 0);
         if (c->path == 2 && c->ntot >= (1 << 26)) {
             delete c;
             return fail(nullptr, MD_ERR_INVALID, "the neighbour-list path takes at most 2^26 atoms");
@@ -1311,6 +1320,106 @@ md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int
     if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToHost);
     if (dout) cudaFree(dout);
     if (e != cudaSuccess) return fail(nullptr, MD_ERR_CUDA, "normals: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- structural observables (Sec. III)
+namespace {
+constexpr int kMaxBins = 8192;  // histogram bins (shared-memory counters of one CTA)
+
+md_status struct_alloc(md_ctx* c) {
+    if (c->sb.com) return MD_OK;
+    const size_t np = (size_t)c->npad, B = (size_t)c->B;
+    StructBufs& b = c->sb;
+    CK(c, cudaMalloc(&b.com, sizeof(double) * 3 * B));
+    CK(c, cudaMalloc(&b.core, sizeof(int32_t) * np));
+    CK(c, cudaMalloc(&b.ncore, sizeof(int32_t) * B));
+    CK(c, cudaMalloc(&b.ref, sizeof(double) * 3 * np));
+    CK(c, cudaMalloc(&b.ref_com, sizeof(double) * 3 * B));
+    CK(c, cudaMalloc(&b.sel, np));
+    CK(c, cudaMalloc(&b.msd, sizeof(double) * B));
+    CK(c, cudaMalloc(&b.nsel, sizeof(int32_t) * B));
+    CK(c, cudaMalloc(&b.nb, sizeof(int32_t) * kNbCap * np));
+    CK(c, cudaMalloc(&b.nnb, sizeof(int32_t) * np));
+    CK(c, cudaMalloc(&b.cls, np));
+    CK(c, cudaMalloc(&b.counts, sizeof(int32_t) * 4 * B));
+    CK(c, cudaMalloc(&b.capped, sizeof(int32_t) * B));
+    CK(c, cudaMemsetAsync(b.nnb, 0, sizeof(int32_t) * np, c->stream));
+    CK(c, cudaMemsetAsync(b.cls, 0, np, c->stream));
+    return MD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+md_status md_rdf(md_ctx* c, double r_core_A, double bin_A, int32_t nbins, int64_t* counts, int32_t* n_core) {
+    if (!c || !counts) return MD_ERR_INVALID;
+    if (!(std::isfinite(r_core_A) && r_core_A >= 0) || !(std::isfinite(bin_A) && bin_A > 0))
+        return fail(c, MD_ERR_INVALID, "r_core_A must be >= 0 and bin_A > 0");
+    if (nbins < 1 || nbins > kMaxBins) return fail(c, MD_ERR_INVALID, "nbins must be in 1..%d", kMaxBins);
+    md_status st = struct_alloc(c);
+    if (st != MD_OK) return st;
+    if (nbins > c->sb_nbins) {
+        if (c->sb.hist) cudaFree(c->sb.hist);
+        c->sb.hist = nullptr;
+        c->sb_nbins = 0;
+        CK(c, cudaMalloc(&c->sb.hist, sizeof(unsigned long long) * (size_t)c->B * nbins));
+        c->sb_nbins = nbins;
+    }
+    CK(c, cudaMemsetAsync(c->sb.hist, 0, sizeof(unsigned long long) * (size_t)c->B * nbins, c->stream));
+    int maxn = 1;
+    for (int s : c->sizes) maxn = std::max(maxn, s);
+    const int Y = std::max(1, std::min(128, (maxn + 511) / 512));
+    CK(c, launch_rdf(c->dev, c->sb, r_core_A, bin_A, nbins, Y, c->stream));
+    CK(c, cudaMemcpyAsync(counts, c->sb.hist, sizeof(int64_t) * (size_t)c->B * nbins, cudaMemcpyDeviceToHost,
+                          c->stream));
+    if (n_core)
+        CK(c, cudaMemcpyAsync(n_core, c->sb.ncore, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MD_OK;
+}
+
+md_status md_msd_reference(md_ctx* c, double r_core_A) {
+    if (!c) return MD_ERR_INVALID;
+    if (!std::isfinite(r_core_A)) return fail(c, MD_ERR_INVALID, "r_core_A must be finite");
+    md_status st = struct_alloc(c);
+    if (st != MD_OK) return st;
+    CK(c, launch_msd_ref(c->dev, c->sb, r_core_A, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->msd_ref = true;
+    return MD_OK;
+}
+
+md_status md_msd(md_ctx* c, double* msd_A2, int32_t* n_atoms) {
+    if (!c || !msd_A2) return MD_ERR_INVALID;
+    if (!c->msd_ref) return fail(c, MD_ERR_STATE, "no reference configuration: call md_msd_reference first");
+    CK(c, launch_msd(c->dev, c->sb, c->stream));
+    CK(c, cudaMemcpyAsync(msd_A2, c->sb.msd, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    if (n_atoms)
+        CK(c, cudaMemcpyAsync(n_atoms, c->sb.nsel, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return MD_OK;
+}
+
+md_status md_cna(md_ctx* c, double r_nb_A, int32_t* counts, int8_t* cls, int32_t* capped) {
+    if (!c || !counts) return MD_ERR_INVALID;
+    if (!(std::isfinite(r_nb_A) && r_nb_A > 0)) return fail(c, MD_ERR_INVALID, "r_nb_A must be > 0");
+    md_status st = struct_alloc(c);
+    if (st != MD_OK) return st;
+    CK(c, cudaMemsetAsync(c->sb.counts, 0, sizeof(int32_t) * 4 * c->B, c->stream));
+    CK(c, cudaMemsetAsync(c->sb.capped, 0, sizeof(int32_t) * c->B, c->stream));
+    CK(c, launch_cna(c->dev, c->sb, r_nb_A, c->stream));
+    CK(c, cudaMemcpyAsync(counts, c->sb.counts, sizeof(int32_t) * 4 * c->B, cudaMemcpyDeviceToHost, c->stream));
+    if (capped)
+        CK(c, cudaMemcpyAsync(capped, c->sb.capped, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    int8_t* st8 = reinterpret_cast<int8_t*>(c->h_stage);
+    if (cls) CK(c, cudaMemcpyAsync(st8, c->sb.cls, (size_t)c->npad, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (cls)
+        for (int b = 0; b < c->B; ++b)
+            for (int a = 0; a < c->sizes[b]; ++a) cls[c->off[b] + a] = st8[c->poff[b] + a];
     return MD_OK;
 }
 

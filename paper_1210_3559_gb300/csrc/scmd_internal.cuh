@@ -195,6 +195,30 @@ cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s);
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s);
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
+// Structural observables (defined in scmd_structure.cu).
+constexpr int kNbCap = 32;  // neighbours a CNA list stores (the count is exact beyond)
+struct StructBufs {
+    double* com;               // [B][3]
+    int32_t* core;             // [npad] core atoms of each cluster, from its padded offset on
+    int32_t* ncore;            // [B]
+    unsigned long long* hist;  // [B][nbins]
+    double* ref;               // [3][npad] reference positions of the displacement
+    double* ref_com;           // [B][3]
+    uint8_t* sel;              // [npad] atoms the displacement averages over
+    double* msd;               // [B]
+    int32_t* nsel;             // [B]
+    int32_t* nb;               // [npad][kNbCap] neighbours, ascending
+    int32_t* nnb;              // [npad]
+    int8_t* cls;               // [npad] 0 other, 1 fcc, 2 hcp, 3 icosahedral
+    int32_t* counts;           // [B][4] atoms of each class
+    int32_t* capped;           // [B] atoms left "other" because a neighbour had more than kNbCap neighbours
+};
+// Y CTAs per cluster share its pair-distance histogram.
+cudaError_t launch_rdf(const Dev& d, const StructBufs& sb, double r_core, double width, int nbins, int Y,
+                       cudaStream_t s);
+cudaError_t launch_msd_ref(const Dev& d, const StructBufs& sb, double r_core, cudaStream_t s);
+cudaError_t launch_msd(const Dev& d, const StructBufs& sb, cudaStream_t s);
+cudaError_t launch_cna(const Dev& d, const StructBufs& sb, double r_nb, cudaStream_t s);
 // The calling thread's error message returned by md_last_error(NULL) (defined in scmd_api.cu).
 void set_thread_error(const char* msg);
 cudaError_t configure_kernels();

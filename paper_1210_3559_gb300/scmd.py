@@ -94,6 +94,10 @@ def lib() -> ctypes.CDLL:
                 "md_philox4x32_10": ([P(u32), P(u32), i32], i32),
                 "md_langevin_normals": ([u64, u32, i64, i32, i32, _DP], i32),
                 "md_energy_forces_noalloc": ([_VP, i32, P(md_sc_params), _VP, _VP, u64], i32),
+                "md_rdf": ([_VP, ctypes.c_double, ctypes.c_double, i32, P(i64), P(i32)], i32),
+                "md_msd_reference": ([_VP, ctypes.c_double], i32),
+                "md_msd": ([_VP, _DP, P(i32)], i32),
+                "md_cna": ([_VP, ctypes.c_double, P(i32), P(ctypes.c_int8), P(i32)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -108,7 +112,7 @@ def exported_symbols():
             "md_obs_history", "md_clear_history", "md_get_state", "md_set_state", "md_get_forces", "md_recenter",
             "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts", "md_get_path",
             "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals",
-            "md_energy_forces_noalloc"]
+            "md_energy_forces_noalloc", "md_rdf", "md_msd_reference", "md_msd", "md_cna"]
 
 
 def md_abi_version() -> int:
@@ -294,6 +298,44 @@ def md_get_path(ctx: Context) -> int:
     p = ctypes.c_int32()
     _check(lib().md_get_path(ctx.handle, ctypes.byref(p)), ctx.handle)
     return p.value
+
+
+CNA_OTHER, CNA_FCC, CNA_HCP, CNA_ICO = 0, 1, 2, 3
+
+
+def md_rdf(ctx: Context, r_core_A: float, bin_A: float, nbins: int):
+    """(counts[B][nbins] int64, n_core[B]): pair distances from each cluster's central atoms."""
+    counts = np.zeros((ctx.n_clusters, int(nbins)), dtype=np.int64)
+    nc = np.zeros(ctx.n_clusters, dtype=np.int32)
+    _check(lib().md_rdf(ctx.handle, float(r_core_A), float(bin_A), int(nbins),
+                        counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                        nc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), ctx.handle)
+    return counts, nc
+
+
+def md_msd_reference(ctx: Context, r_core_A: float = 0.0):
+    _check(lib().md_msd_reference(ctx.handle, float(r_core_A)), ctx.handle)
+
+
+def md_msd(ctx: Context):
+    """(msd[B] in A^2, atoms averaged[B]) since md_msd_reference, centre-of-mass motion removed."""
+    v = np.zeros(ctx.n_clusters)
+    n = np.zeros(ctx.n_clusters, dtype=np.int32)
+    _check(lib().md_msd(ctx.handle, v.ctypes.data_as(_DP), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           ctx.handle)
+    return v, n
+
+
+def md_cna(ctx: Context, r_nb_A: float = 3.0, per_atom: bool = False):
+    """counts[B][4] (other, fcc, hcp, icosahedral); with per_atom also (class[Ntot] int8, capped[B])."""
+    counts = np.zeros((ctx.n_clusters, 4), dtype=np.int32)
+    capped = np.zeros(ctx.n_clusters, dtype=np.int32)
+    cls = np.zeros(ctx.ntot, dtype=np.int8) if per_atom else None
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    _check(lib().md_cna(ctx.handle, float(r_nb_A), counts.ctypes.data_as(I32),
+                        cls.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if per_atom else None,
+                        capped.ctypes.data_as(I32)), ctx.handle)
+    return (counts, cls, capped) if per_atom else counts
 
 
 def md_philox4x32_10(words) -> np.ndarray:
