@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 
 class Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("c", ctypes.c_double), ("a", ctypes.c_double),
-                ("n", ctypes.c_int), ("m", ctypes.c_int), ("rcut", ctypes.c_double)]
+                ("n", ctypes.c_int), ("m", ctypes.c_int), ("rcut", ctypes.c_double), ("shift", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class Thermostat(ctypes.Structure):
@@ -106,9 +107,10 @@ def _pos(pos) -> np.ndarray:
     return pos
 
 
-def params(eps=1.5707e-2, c=39.432, a=3.52, n=9, m=6, rcut=0.0) -> Params:
-    """Sutton-Chen parameters; defaults are the paper's Ni set (Sec. II A)."""
-    return Params(float(eps), float(c), float(a), int(n), int(m), float(rcut))
+def params(eps=1.5707e-2, c=39.432, a=3.52, n=9, m=6, rcut=0.0, shift=False) -> Params:
+    """Sutton-Chen parameters; defaults are the paper's Ni set (Sec. II A). With rcut > 0 the pair
+    terms are truncated at rcut, or with shift=True also shifted by their value at rcut."""
+    return Params(float(eps), float(c), float(a), int(n), int(m), float(rcut), 1 if shift else 0, 0)
 
 
 def num_threads(n: int = 0) -> int:

@@ -49,6 +49,9 @@ typedef struct {
     int n;        /* repulsive exponent n                */
     int m;        /* density exponent m                  */
     double rcut;  /* strict cutoff r < rcut in Angstrom; <= 0 means all pairs */
+    int shift;    /* with a cutoff: 0 plain truncation; 1 every pair term inside rcut
+                     shifted by its value at rcut, so the energy is continuous      */
+    int reserved;
 } orc_params;
 
 typedef struct {
@@ -85,6 +88,15 @@ static int interacts(double r, const orc_params* p) {
     return !(p->rcut > 0.0) || r < p->rcut;
 }
 
+/* The terms of one pair inside the cutoff: (a/r)^k, less (a/rcut)^k for the
+ * shifted form, which then vanishes continuously at rcut. The shift does not
+ * depend on r, so the derivatives (and the force formula below) are those of
+ * the plain terms; only rho_i, and through it g_i, carry the shift.           */
+static double term(double r, int k, const orc_params* p) {
+    const double t = pow(p->a / r, k);
+    return (p->shift && p->rcut > 0.0) ? t - pow(p->a / p->rcut, k) : t;
+}
+
 /* First sweep: rho_i = sum_{j != i} (a/r_ij)^m  (Eq. 2). */
 void orc_density(int N, const double* pos, const orc_params* p, double* rho) {
     int i;
@@ -95,7 +107,7 @@ void orc_density(int N, const double* pos, const orc_params* p, double* rho) {
             if (j == i) continue;
             double r = dist(pos, i, j, d);
             if (!interacts(r, p)) continue;
-            acc += pow(p->a / r, p->m);
+            acc += term(r, p->m, p);
         }
         rho[i] = acc;
     }
@@ -108,6 +120,7 @@ static double inv_sqrt_rho(double rho) { return rho > 0.0 ? 1.0 / sqrt(rho) : 0.
 /*
  * Energy and forces of one isolated cluster.
  *   e_terms[0] = pair part      eps * 1/2 * sum_i sum_{j != i} (a/r_ij)^n
+ *                (each term shifted by its value at rcut in the shifted form)
  *   e_terms[1] = embedding part -eps * c * sum_i sqrt(rho_i)
  * Force, from differentiating Eq. 1 (with s = a/r_ij, g_k = rho_k^(-1/2)):
  *   d(s^k)/dr = -k s^k / r and rho_j depends on r_i through the (i,j) term, so
@@ -132,7 +145,7 @@ double orc_energy_forces(int N, const double* pos, const orc_params* p, double* 
                 if (j == i) continue;
                 double r = dist(pos, i, j, d);
                 if (!interacts(r, p)) continue;
-                acc += pow(p->a / r, p->n);
+                acc += term(r, p->n, p);
             }
             pair_i[i] = acc;
         }
@@ -185,7 +198,7 @@ void orc_atom_energies(int N, const double* pos, const orc_params* p, double* e_
             if (j == i) continue;
             double r = dist(pos, i, j, d);
             if (!interacts(r, p)) continue;
-            acc += pow(p->a / r, p->n);
+            acc += term(r, p->n, p);
         }
         e_atom[i] = p->eps * (0.5 * acc - p->c * sqrt(rho[i]));
     }

@@ -408,3 +408,69 @@ def test_maxwell_boltzmann_temperature_and_momenta():
     assert o["T"] == pytest.approx(2000.0, rel=1e-12)
     assert np.abs(o["mom"]).max() < 1e-12
     assert np.abs(o["angmom"]).max() < 1e-9
+
+
+# ------------------------------------------------------------ shifted cutoff
+@pytest.mark.parametrize("r", [2.3, 2.6, 4.0, 8.0])
+def test_shifted_dimer_closed_form(r):
+    """Two atoms: each has rho = (a/r)^m - (a/rc)^m, so U = eps [(a/r)^n - (a/rc)^n
+    - 2 c sqrt((a/r)^m - (a/rc)^m)]; F = -dU/dr along the axis."""
+    eps, c, a, n, m, rc = 1.5707e-2, 39.432, 3.52, 9, 6, 8.8
+    p = oracle.params(rcut=rc, shift=True)
+    U, F, _, rho = oracle.energy_forces([[0, 0, 0], [r, 0, 0]], p)
+    sn, sm, cn, cm = (a / r) ** n, (a / r) ** m, (a / rc) ** n, (a / rc) ** m
+    assert U == pytest.approx(eps * ((sn - cn) - 2 * c * np.sqrt(sm - cm)), rel=1e-13)
+    assert rho[0] == pytest.approx(sm - cm, rel=1e-13)
+    dU = eps * (-n * sn / r + c * m * sm / r / np.sqrt(sm - cm))
+    assert F[1][0] == pytest.approx(-dU, rel=1e-12) and F[0][0] == pytest.approx(dU, rel=1e-12)
+
+
+def test_shifted_energy_is_continuous_at_the_cutoff():
+    """A dimer approaching rc from inside: the shifted energy goes to zero like sqrt(rc - r) (the
+    embedding term), the truncated one keeps a finite jump. In a cluster, a pair crossing rc leaves
+    the shifted energy continuous: along a path that carries one pair through rc, consecutive
+    energies differ by no more than the force times the step, while the truncated energy jumps."""
+    rc = 8.8
+    ps, pt = oracle.params(rcut=rc, shift=True), oracle.params(rcut=rc)
+    u1 = oracle.energy([[0, 0, 0], [rc - 1e-6, 0, 0]], ps)
+    u2 = oracle.energy([[0, 0, 0], [rc - 1e-8, 0, 0]], ps)
+    assert abs(u1) < 1e-4 and u1 / u2 == pytest.approx(10.0, rel=1e-3)
+    assert oracle.energy([[0, 0, 0], [rc - 1e-8, 0, 0]], pt) < -0.07
+    pos = inputs.jitter(inputs.fcc_sphere(43), 0.1, 7)
+    k = int(np.argmax(np.linalg.norm(pos, axis=1)))
+    u = pos[k] / np.linalg.norm(pos[k])
+    # carry atom k outwards by 1 A in steps of 1e-4 A: several pairs leave rc on the way
+    steps = np.arange(0, 10001) * 1e-4
+    d0 = np.linalg.norm(pos - pos[k], axis=1)
+    crossing = np.sum((d0 < rc) & (np.linalg.norm(pos - (pos[k] + u), axis=1) >= rc))
+    assert crossing > 0
+    def path(p):  # energies and the work of the force along the path (trapezoid rule)
+        E, W = [], []
+        for t in steps[::50]:
+            q = pos.copy()
+            q[k] = pos[k] + t * u
+            U, F, _, _ = oracle.energy_forces(q, p)
+            E.append(U)
+            W.append(F[k] @ u)
+        E, W = np.array(E), np.array(W)
+        return np.abs(np.diff(E) + 0.5 * (W[1:] + W[:-1]) * 50e-4)  # dE = -F.dx, up to O(dx^3)
+
+    rs, rt = path(ps), path(pt)
+    assert np.max(rs) < 1e-5                  # smooth where pairs cross rc
+    assert np.max(rt) > 100 * np.max(rs)      # the truncated energy jumps there
+
+
+def test_shifted_forces_match_central_differences():
+    pos = inputs.jitter(inputs.fcc_sphere(43), 0.1, 7)
+    rc = 5.3
+    d = np.linalg.norm(pos[:, None] - pos[None], axis=-1)
+    assert np.min(np.abs(d[np.triu_indices(len(pos), 1)] - rc)) > 1e-3
+    p = oracle.params(rcut=rc, shift=True)
+    _, F, _, _ = oracle.energy_forces(pos, p)
+    Fn = numeric_forces(pos, p)
+    assert np.linalg.norm(F - Fn) / np.linalg.norm(F) < 1e-8
+    # the shift lowers every rho by (a/rc)^m per neighbour inside rc
+    _, _, _, rho_t = oracle.energy_forces(pos, oracle.params(rcut=rc))
+    _, _, _, rho_s = oracle.energy_forces(pos, p)
+    nin = np.sum((d < rc) & (d > 0), axis=1)
+    assert np.allclose(rho_t - rho_s, nin * (3.52 / rc) ** 6, rtol=1e-10, atol=0)
