@@ -302,6 +302,7 @@ def main():
         scmd.md_step(ctx, w["melt_steps"], dt, scmd.thermostat(scmd.MD_LANGEVIN, w["melt_T"], w["melt_T"],
                                                                gamma_per_ps=w["gamma"], seed=w["seed"]))
     melt_pos, melt_vel, _ = scmd.md_get_state(ctx)  # start of the NVE drift runs
+    cna_melt = None if args.skip_analysis else scmd.md_cna(ctx, 3.0)  # on the device (Sec. III)
     M = args.md_steps
 
     def therm(k):
@@ -397,13 +398,19 @@ def main():
             snap_err.append(float(np.linalg.norm(Fs - Fr) / np.linalg.norm(Fr)))
     structure = None
     if rank == 0 and analysis_on:
-        from paper_1210_3559_gb300 import analysis
         obs_end = scmd.md_observables(ctx)
+        cna_end = scmd.md_cna(ctx, 3.0)
+
+        def fractions(counts):  # cluster 0: other, fcc, hcp, icosahedral
+            f = counts[0] / max(n0, 1)
+            return {"fcc": float(f[1]), "hcp": float(f[2]), "icosahedral": float(f[3]),
+                    "crystalline": float(f[1] + f[2])}
         structure = {"cluster": 0, "atoms": n0,
                      "epot_per_atom_start_eV": obs_start[0]["epot"] / n0, "epot_per_atom_end_eV": obs_end[0]["epot"] / n0,
                      "T_start_K": obs_start[0]["T"], "T_end_K": obs_end[0]["T"],
-                     "crystalline_fraction_end": analysis.crystalline_fraction(pos_f[:n0], 3.52),
-                     "crystalline_fraction_start_of_schedule": analysis.crystalline_fraction(melt_pos[:n0], 3.52)}
+                     "crystalline_fraction_end": fractions(cna_end),
+                     "crystalline_fraction_start_of_schedule": fractions(cna_melt),
+                     "cna": "on the device (md_cna, neighbours closer than 3.0 A)"}
 
     # e2e through the C ABI with host buffers: set_state (H2D) + md_step + get_state (D2H)
     pos_h = torch.from_numpy(pos_f.copy()).pin_memory().numpy()

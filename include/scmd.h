@@ -65,8 +65,9 @@ typedef enum {
 } md_precision;
 
 typedef enum {
-    MD_PATH_AUTO = 0,     /* when rcut_A > 0 and the largest cluster has >= 8192 atoms:
-                             cells in MIXED, neighbour lists in FP64; else all pairs     */
+    MD_PATH_AUTO = 0,     /* when rcut_A > 0 and the largest cluster has >= 8192 atoms
+                             (or the cutoff is shifted): cells in MIXED, neighbour lists
+                             in FP64; else all pairs                                     */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
     MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
     MD_PATH_VERLET = 3    /* per-atom neighbour lists (rcut_A + 1 A) built on the cell grid,
@@ -86,7 +87,12 @@ typedef enum {
 /* Sutton-Chen parameters (Eq. 1, Eq. 2). Paper's Ni set (Sec. II A):
  * eps_eV = 1.5707e-2, a_A = 3.52, c = 39.432, n = 9, m = 6.
  * rcut_A <= 0: all pairs. rcut_A > 0: a pair enters both rho and the pair sum
- * only when r_ij < rcut_A (plain truncation, no shift). */
+ * only when r_ij < rcut_A. cutoff_shift = 0: plain truncation. cutoff_shift = 1
+ * (needs rcut_A > 0; the cell and neighbour-list paths only): each pair inside
+ * rcut_A contributes (a/r)^n - (a/rcut)^n to the pair sum and (a/r)^m -
+ * (a/rcut)^m to rho, so the energy is continuous when pairs cross the cutoff;
+ * forces are its gradient (the derivative formula of the plain terms, with the
+ * shifted rho). Zero-initialise: reserved must be 0. */
 typedef struct {
     double eps_eV;
     double c;
@@ -94,6 +100,8 @@ typedef struct {
     int32_t n;
     int32_t m;
     double rcut_A;
+    int32_t cutoff_shift;
+    int32_t reserved;
 } md_sc_params;
 
 /* Context configuration. Zero-initialise, then set what you need. */
@@ -281,7 +289,8 @@ md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int
  *   stream                  cudaStream_t on which the work is queued (0 = default stream)
  * The caller owns all three buffers. The arithmetic is that of md_energy_forces
  * in MIXED precision (FP32 pair terms, FP64 rho and energy), all pairs, or the
- * strict cutoff when params->rcut_A > 0. The call queues its kernels and returns;
+ * strict cutoff when params->rcut_A > 0 (plain truncation: cutoff_shift must be
+ * 0). The call queues its kernels and returns;
  * synchronise the stream before reading the outputs. Working data lives in one
  * fixed array compiled into the library (kept by every GPU that loads it until the
  * process exits), so n_atoms is limited to 1..16384: anything else returns

@@ -589,8 +589,12 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         return fail(nullptr, MD_ERR_INVALID, "negative obs_every, graph_chunk or obs_capacity");
     if (!(std::isfinite(prm->eps_eV) && std::isfinite(prm->c) && std::isfinite(prm->a_A) && prm->a_A > 0 &&
           std::isfinite(prm->rcut_A) && prm->rcut_A >= 0 && prm->n >= 1 && prm->n <= 32 && prm->m >= 1 &&
-          prm->m <= 32))
+          prm->m <= 32 && (prm->cutoff_shift == 0 || prm->cutoff_shift == 1) && prm->reserved == 0))
         return fail(nullptr, MD_ERR_INVALID, "invalid Sutton-Chen parameters");
+    if (prm->cutoff_shift && !(prm->rcut_A > 0))
+        return fail(nullptr, MD_ERR_INVALID, "a shifted cutoff needs rcut_A > 0");
+    if (prm->cutoff_shift && cfg->path == MD_PATH_ALLPAIRS)
+        return fail(nullptr, MD_ERR_INVALID, "the shifted cutoff runs on the cell and neighbour-list paths");
     int64_t ntot = 0;
     for (int b = 0; b < n_clusters; ++b) {
         if (sizes[b] < 1) return fail(nullptr, MD_ERR_INVALID, "cluster %d has size %d", b, sizes[b]);
@@ -663,12 +667,15 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     P.A9f = (float)P.A9;
     P.rcut2f = (float)P.rcut2;
     P.special = (P.n == 9 && P.m == 6) ? 1 : 0;
+    P.shift = prm->cutoff_shift;
+    P.shm = P.shift ? std::pow(P.rcut, -(double)P.m) : 0.0;
+    P.shn = P.shift ? std::pow(P.rcut, -(double)P.n) : 0.0;
     {
         int maxn = 0;
         for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
         // automatic: with a cutoff and a large cluster, the cell list in MIXED (its passes read shared
         // memory) and the neighbour lists in FP64 (whose pipe the tested pairs bound)
-        const bool big = cfg->path == MD_PATH_AUTO && P.rcut > 0 && maxn >= kAutoCellsMinAtoms;
+        const bool big = cfg->path == MD_PATH_AUTO && P.rcut > 0 && (maxn >= kAutoCellsMinAtoms || P.shift);
         const bool verlet = cfg->path == MD_PATH_VERLET || (big && cfg->precision == MD_PREC_FP64);
         const bool cells = verlet || cfg->path == MD_PATH_CELLS || big;
         c->path = verlet ? 2 : (cells ? 1 : 0);

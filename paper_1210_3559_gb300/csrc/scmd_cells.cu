@@ -119,7 +119,7 @@ template <int PREC> __global__ void k_cell_sort(const Dev d, int cond, int k_loc
 }
 
 // ------------------------------------------------------------- density pass
-template <int PREC, int SPECIAL>
+template <int PREC, int SPECIAL, int SHIFT>
 __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_density(const Dev d, int obs) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
         const int self = s_pref[q.home_t] + blk * 32 + q.is;
         f2sum facc = {0.f, 0.f};
         double racc = 0.0;
+        int nin = 0;  // pairs inside rcut (the shifted form subtracts rcut^-m for each)
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
@@ -165,7 +166,9 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
                         const V4 p = spos[e];
                         const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
                         R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                        r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
+                        const bool in = r2 < rc2 && e != selfl;
+                        r2 = in ? r2 : big<R>();
+                        if (SHIFT) nin += in;
                         if (SPECIAL) {
                             const R inv = inv_r2(r2);
                             tacc = fma(inv * inv, inv, tacc);
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
                 }
         }
         if (PREC == 1) racc = (double)facc.hi + (double)facc.lo;
+        if (SHIFT) racc -= (double)nin * d.pot.shm;
         part[w][lane] = racc;
         __syncwarp();
         if (q.nb > 0 && q.jg == 0) {
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2)
         const int self = s_pref[q.home_t] + blk * 32 + q.is;
         R fx = R(0), fy = R(0), fz = R(0);
         double ea = 0.0;
+        int nin = 0;  // pairs inside rcut, counted with the energy (the shifted form)
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
             __syncthreads();
@@ -259,7 +264,9 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2)
                         const V4 p = spos[e];
                         const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
                         R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                        r2 = (r2 < rc2 && e != selfl) ? r2 : big<R>();
+                        const bool in = r2 < rc2 && e != selfl;
+                        r2 = in ? r2 : big<R>();
+                        if (ENERGY) nin += in;
                         const R ir = inv_r(r2);
                         const R inv = ir * ir;
                         R coef, rn;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2)
         partf[w][lane][0] = fx;
         partf[w][lane][1] = fy;
         partf[w][lane][2] = fz;
-        if (ENERGY) parte[w][lane] = ea;
+        if (ENERGY) parte[w][lane] = d.pot.shift ? ea - (double)nin * d.pot.shn : ea;
         __syncwarp();
         if (q.nb > 0 && q.jg == 0) {
             R Fx = partf[w][q.is][0], Fy = partf[w][q.is][1], Fz = partf[w][q.is][2];
@@ -394,13 +401,16 @@ cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond, int k_loca
                        : launch_ex(k_cell_sort<0>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d, cond, k_local);
 }
 
+template <int PREC, int SHIFT>
+static cudaError_t cell_density_s(const Dev& d, int obs, cudaStream_t s) {
+    return d.pot.special ? launch_ex(k_cell_density<PREC, 1, SHIFT>, d.n_cells, kCellThreads, 0, 0, s, d, obs)
+                         : launch_ex(k_cell_density<PREC, 0, SHIFT>, d.n_cells, kCellThreads, 0, 0, s, d, obs);
+}
+
 cudaError_t launch_cell_density(const Dev& d, int obs, cudaStream_t s) {
-    const bool sp = d.pot.special != 0;
-    if (d.prec == 1)
-        return sp ? launch_ex(k_cell_density<1, 1>, d.n_cells, kCellThreads, 0, 0, s, d, obs)
-                  : launch_ex(k_cell_density<1, 0>, d.n_cells, kCellThreads, 0, 0, s, d, obs);
-    return sp ? launch_ex(k_cell_density<0, 1>, d.n_cells, kCellThreads, 0, 0, s, d, obs)
-              : launch_ex(k_cell_density<0, 0>, d.n_cells, kCellThreads, 0, 0, s, d, obs);
+    const bool sh = d.pot.shift != 0;
+    if (d.prec == 1) return sh ? cell_density_s<1, 1>(d, obs, s) : cell_density_s<1, 0>(d, obs, s);
+    return sh ? cell_density_s<0, 1>(d, obs, s) : cell_density_s<0, 0>(d, obs, s);
 }
 
 template <int PREC, int ENERGY>

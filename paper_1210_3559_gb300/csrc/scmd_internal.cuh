@@ -73,6 +73,9 @@ struct Pot {
     double ecoef;// 1/2 eps a^n          (pair energy scale)
     float A9f, rcut2f;
     int special; // 1 when (n, m) = (9, 6): compile-time exponents
+    int shift;   // 1: every pair term inside rcut less its value at rcut
+    double shm;  // rcut^-m: the density shift per pair (rho = a^m (sum r^-m - shm * pairs))
+    double shn;  // rcut^-n: the pair-energy shift per pair
 };
 
 // Integrator / thermostat parameters of the current md_step call (device resident).

@@ -182,8 +182,9 @@ md_status md_energy_forces_noalloc(const double* pos_dev, int32_t n_atoms, const
     }
     if (!(std::isfinite(params->eps_eV) && std::isfinite(params->c) && std::isfinite(params->a_A) &&
           params->a_A > 0 && std::isfinite(params->rcut_A) && params->rcut_A >= 0 && params->n >= 1 &&
-          params->n <= 32 && params->m >= 1 && params->m <= 32))
+          params->n <= 32 && params->m >= 1 && params->m <= 32 && params->reserved == 0))
         return na_fail(MD_ERR_INVALID, "invalid Sutton-Chen parameters");
+    if (params->cutoff_shift != 0) return na_fail(MD_ERR_INVALID, "this entry point sums plain (unshifted) terms");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 256) return na_fail(MD_ERR_CUDA, "no usable CUDA device");

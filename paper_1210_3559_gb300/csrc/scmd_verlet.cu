@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     f2sum facc = {0.f, 0.f};
     double racc = 0.0;
     R tacc = R(0);
-    int cnt = 0;
+    int cnt = 0, nfold = 0;  // pairs inside rcut: nfold * kSpanV + cnt
 #pragma unroll 4
     for (int e = beg; e < end; ++e) {
         const int q = lst[e];
@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
                 racc += (double)tacc;
             tacc = R(0);
             cnt = 0;
+            ++nfold;
         }
     }
     if (PREC == 1) {
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     } else {
         racc += (double)tacc;
     }
+    if (d.pot.shift) racc -= (double)(nfold * kSpanV + cnt) * d.pot.shm;
     const double rho = v_group_sum(racc) * d.pot.am;
     if (t != 0) return;
     const int i = d.vorder[s];
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
     const int* lst = d.vlist + (size_t)s * kVMax;
     R fx = R(0), fy = R(0), fz = R(0), sx = R(0), sy = R(0), sz = R(0), se = R(0);
     double ea = 0.0;
-    int cnt = 0;
+    int cnt = 0, nfold = 0;  // pairs inside rcut: nfold * kSpanV + cnt
 #pragma unroll 4
     for (int e = beg; e < end; ++e) {
         const int q = lst[e];
@@ -387,12 +389,15 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
                 se = R(0);
             }
             cnt = 0;
+            ++nfold;
         }
     }
     const double gx = v_group_sum((double)(fx + sx));
     const double gy = v_group_sum((double)(fy + sy));
     const double gz = v_group_sum((double)(fz + sz));
-    const double Ep = ENERGY ? v_group_sum(ea + (double)se) : 0.0;
+    const double Ep =
+        ENERGY ? v_group_sum(ea + (double)se - (d.pot.shift ? (double)(nfold * kSpanV + cnt) * d.pot.shn : 0.0))
+               : 0.0;
     if (t != 0) return;
     const R Fx = (R)gx, Fy = (R)gy, Fz = (R)gz;
     const int i = d.vorder[s];

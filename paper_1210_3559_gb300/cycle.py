@@ -19,7 +19,7 @@ import time
 
 import numpy as np
 
-from . import analysis, inputs
+from . import inputs
 from . import scmd
 
 
@@ -57,7 +57,7 @@ def run(replicas=8, shells=8, T_low=400.0, T_high=1400.0, rate_K_per_ps=1.0, dt=
     scmd.md_step(ctx, int(round(20000.0 / dt)), dt, scmd.thermostat(scmd.MD_LANGEVIN, T_low, T_low, gamma_per_ps=gamma,
                                                                     seed=seed))
     start = scmd.md_observables(ctx)
-    start_pos, _, _ = scmd.md_get_state(ctx)
+    cna_start = scmd.md_cna(ctx, 3.0)  # per replica: other, fcc, hcp, icosahedral (on the device)
     scmd.md_clear_history(ctx)
     t0 = time.perf_counter()
     temps = []
@@ -73,7 +73,7 @@ def run(replicas=8, shells=8, T_low=400.0, T_high=1400.0, rate_K_per_ps=1.0, dt=
     wall = time.perf_counter() - t0
     hist = scmd.md_obs_history(ctx)
     end = scmd.md_observables(ctx)
-    end_pos, _, _ = scmd.md_get_state(ctx)
+    cna_end = scmd.md_cna(ctx, 3.0)
     scmd.md_destroy(ctx)
     T = np.array(temps[:len(hist)])
     e = np.array([[h[b]["etot"] for b in range(replicas)] for h in hist]) / n
@@ -85,8 +85,9 @@ def run(replicas=8, shells=8, T_low=400.0, T_high=1400.0, rate_K_per_ps=1.0, dt=
         out.append({"T_melt_K": t_melt, "T_freeze_K": t_freeze, "hysteresis_K": t_melt - t_freeze,
                     "e_start_eV_per_atom": start[b]["etot"] / n, "e_end_eV_per_atom": end[b]["etot"] / n,
                     "epot_start_eV_per_atom": start[b]["epot"] / n, "epot_end_eV_per_atom": end[b]["epot"] / n,
-                    "crystalline_start": analysis.crystalline_fraction(start_pos[b * n:(b + 1) * n])["crystalline"],
-                    "crystalline_end": analysis.crystalline_fraction(end_pos[b * n:(b + 1) * n])["crystalline"]})
+                    "crystalline_start": float(cna_start[b, 1] + cna_start[b, 2]) / n,
+                    "crystalline_end": float(cna_end[b, 1] + cna_end[b, 2]) / n,
+                    "icosahedral_start": int(cna_start[b, 3]), "icosahedral_end": int(cna_end[b, 3])})
     hyst = np.array([c["hysteresis_K"] for c in out])
     return {"replicas": replicas, "atoms_per_cluster": n, "T_low_K": T_low, "T_high_K": T_high,
             "rate_K_per_ps": rate_K_per_ps, "dt_fs": dt, "gamma_per_ps": gamma,

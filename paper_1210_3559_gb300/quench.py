@@ -46,14 +46,14 @@ def run(n_clusters=512, nmin=55, nmax=2000, T=900.0, steps=250000, melt_steps=10
     scmd.md_step(ctx, steps, dt, scmd.thermostat(scmd.MD_LANGEVIN, T, T, gamma_per_ps=gamma, seed=seed + 1))
     wall = time.perf_counter() - t0
     hist = scmd.md_obs_history(ctx)
-    final_pos, _, _ = scmd.md_get_state(ctx)
+    cna = scmd.md_cna(ctx, 3.0)  # per cluster: other, fcc, hcp, icosahedral (on the device)
     scmd.md_destroy(ctx)
     e = np.array([[h[b]["etot"] for b in range(len(sizes))] for h in hist]) / np.asarray(sizes)[None, :]
     off = np.concatenate([[0], np.cumsum(sizes)])
     out = []
     for b, n in enumerate(sizes):
         tn = analysis.solidification_time(e[:, b], dt_ps=every * dt / 1000.0)
-        cf = analysis.crystalline_fraction(final_pos[off[b]:off[b + 1]])["crystalline"]
+        cf = float(cna[b, 1] + cna[b, 2]) / n
         out.append({"n": int(n), "t_nuc_ps": tn, "crystalline_end": cf})
     horizon = steps * dt / 1000.0
     times = np.array([c["t_nuc_ps"] for c in out if c["t_nuc_ps"] is not None])

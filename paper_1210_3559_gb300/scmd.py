@@ -26,7 +26,8 @@ _STATUS = {0: "MD_OK", 1: "MD_ERR_INVALID", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4
 
 class md_sc_params(ctypes.Structure):
     _fields_ = [("eps_eV", ctypes.c_double), ("c", ctypes.c_double), ("a_A", ctypes.c_double),
-                ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("rcut_A", ctypes.c_double)]
+                ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("rcut_A", ctypes.c_double),
+                ("cutoff_shift", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class md_config(ctypes.Structure):
@@ -138,9 +139,10 @@ def _arr(a, n=None):
     return a
 
 
-def sc_params(eps=1.5707e-2, c=39.432, a=3.52, n=9, m=6, rcut=0.0) -> md_sc_params:
-    """Sutton-Chen parameters; defaults are the paper's Ni set (Sec. II A)."""
-    return md_sc_params(float(eps), float(c), float(a), int(n), int(m), float(rcut))
+def sc_params(eps=1.5707e-2, c=39.432, a=3.52, n=9, m=6, rcut=0.0, shift=False) -> md_sc_params:
+    """Sutton-Chen parameters; defaults are the paper's Ni set (Sec. II A). rcut > 0 truncates the
+    pair terms at rcut; shift=True also shifts them by their value there (continuous energy)."""
+    return md_sc_params(float(eps), float(c), float(a), int(n), int(m), float(rcut), 1 if shift else 0, 0)
 
 
 def config(precision=MD_PREC_MIXED, path=MD_PATH_AUTO, obs_every=0, graph_chunk=0, tune=0, obs_capacity=0,

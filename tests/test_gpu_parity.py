@@ -45,8 +45,8 @@ def rel_force_err(F, Fr):
     return np.linalg.norm(F - Fr) / (n if n > 0 else 1.0)
 
 
-def check_cluster(F, E, rho, pos, prec, rcut=0.0):
-    p = oracle.params(rcut=rcut)
+def check_cluster(F, E, rho, pos, prec, rcut=0.0, shift=False):
+    p = oracle.params(rcut=rcut, shift=shift)
     Er, Fr, _, rhor = oracle.energy_forces(pos, p)
     tol = TOL[prec]
     if np.linalg.norm(Fr) > 0:
