@@ -94,7 +94,10 @@ struct md_ctx {
     int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vsub = nullptr, *d_vorder = nullptr, *d_vslotof = nullptr;
     int32_t* d_vslot = nullptr;
     void *d_vhi = nullptr, *d_vposg = nullptr;
-    float4* d_vlo = nullptr;
+    int32_t *d_q_n = nullptr, *d_cell_base = nullptr, *d_q_cell = nullptr, *d_q_list = nullptr, *d_q_count = nullptr;
+    float4 *d_q_ref = nullptr, *d_q_box = nullptr;
+    int nqmax = 0;
+    int32_t nslot = 0;  // list slots: the atoms (FP64), or 4 * nqmax (MIXED quads)
     double* d_vxref = nullptr;
     uint32_t* d_vdmax = nullptr;
     uint8_t* d_cell_obyte = nullptr;
@@ -187,7 +190,7 @@ void fill_dev(md_ctx* c) {
     d.cell_atoms = c->d_cell_atoms;
     d.cell_oct = c->d_cell_oct;
     d.cell_obyte = c->d_cell_obyte;
-    d.nslot = (int32_t)c->ntot;
+    d.nslot = c->nslot;
     d.vskin2h = (float)((0.5 * kSkin - kSkinMargin) * (0.5 * kSkin - kSkinMargin));
     d.vrl2 = (c->pot.rcut + kSkin) * (c->pot.rcut + kSkin);
     d.vlist = c->d_vlist;
@@ -197,7 +200,14 @@ void fill_dev(md_ctx* c) {
     d.vslotof = c->d_vslotof;
     d.vslot = c->d_vslot;
     d.vhi = c->d_vhi;
-    d.vlo = c->d_vlo;
+    d.nqmax = c->nqmax;
+    d.q_n = c->d_q_n;
+    d.cell_base = c->d_cell_base;
+    d.q_ref = c->d_q_ref;
+    d.q_box = c->d_q_box;
+    d.q_cell = c->d_q_cell;
+    d.q_list = c->d_q_list;
+    d.q_count = c->d_q_count;
     d.vposg = c->d_vposg;
     d.vxref = c->d_vxref;
     d.vdmax = c->d_vdmax;
@@ -251,10 +261,6 @@ bool make_grids(md_ctx* c, const double* pos, const double* mass, double reach) 
         g.inv_h = 1.0 / g.h;
         // a cell at the fcc density (or the whole cluster, if smaller) must fit kCellCap atoms
         if (std::min(1.25 * 4.0 * g.h * g.h * g.h / (a * a * a), (double)n) > kCellCap) return false;
-        // neighbour lists: the coordinates of the atoms inside the grid cube, shifted by a power of two
-        // S >= E + 32, lie in [32, 2S), so the FP32 high parts of two of them closer than 16 A differ
-        // exactly (Sterbenz's lemma)
-        g.frame = std::exp2(std::ceil(std::log2(g.E + 32.0)));
         c->grids[b] = g;
         off += G * G * G;
     }
@@ -446,7 +452,8 @@ void free_all(md_ctx* c) {
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
                     c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
-                    c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi, c->d_vlo,
+                    c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi,
+                    c->d_q_n, c->d_cell_base, c->d_q_cell, c->d_q_list, c->d_q_count, c->d_q_ref, c->d_q_box,
                     c->d_vposg, c->d_vxref, c->d_vdmax,
                     c->sb.com, c->sb.core, c->sb.ncore, c->sb.hist, c->sb.ref, c->sb.ref_com, c->sb.sel, c->sb.msd,
                     c->sb.nsel, c->sb.nb, c->sb.nnb, c->sb.cls, c->sb.counts, c->sb.capped};
@@ -781,26 +788,43 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         CKC(cudaMemset(c->d_obs_v, 0, sizeof(double) * 3 * np));
     }
     if (c->path == 2) {
-        const size_t ns = (size_t)c->ntot;
-        CKC(cudaMalloc(&c->d_vlist, sizeof(int32_t) * kVMax * ns));
-        CKC(cudaMalloc(&c->d_vcount, sizeof(int32_t) * ns));
-        CKC(cudaMalloc(&c->d_vsub, sizeof(int32_t) * kVLanes * ns));
+        const bool quads = cfg->precision == MD_PREC_MIXED;
+        // MIXED: every cell's atoms padded to whole quads (at most 3 empty slots per cell)
+        c->nqmax = quads ? (int)((c->ntot + 3 * (int64_t)c->n_cells + 3) / 4) : 0;
+        const size_t ns = quads ? 4 * (size_t)c->nqmax : (size_t)c->ntot;
+        c->nslot = (int32_t)ns;
         CKC(cudaMalloc(&c->d_vorder, sizeof(int32_t) * ns));
         CKC(cudaMalloc(&c->d_vslotof, sizeof(int32_t) * np));
-        CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
         CKC(cudaMalloc(&c->d_vhi, (size_t)vec4_size(c) * ns));
-        if (cfg->precision == MD_PREC_MIXED) CKC(cudaMalloc(&c->d_vlo, sizeof(float4) * ns));
         CKC(cudaMalloc(&c->d_vposg, (size_t)vec4_size(c) * ns));
         CKC(cudaMalloc(&c->d_vxref, sizeof(double) * 3 * ns));
         CKC(cudaMalloc(&c->d_vdmax, sizeof(uint32_t) * 2));
         CKC(cudaMemset(c->d_vdmax, 0, sizeof(uint32_t) * 2));
-        // every slot, count and entry starts as a valid index (atom 0, empty list)
-        CKC(cudaMemset(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns));
-        CKC(cudaMemset(c->d_vcount, 0, sizeof(int32_t) * ns));
-        CKC(cudaMemset(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns));
+        // every slot and entry starts as a valid index (atom 0, empty list)
         CKC(cudaMemset(c->d_vorder, 0, sizeof(int32_t) * ns));
         CKC(cudaMemset(c->d_vslotof, 0, sizeof(int32_t) * np));
         CKC(cudaMemset(c->d_vxref, 0, sizeof(double) * 3 * ns));
+        if (quads) {
+            const size_t nq = (size_t)c->nqmax;
+            CKC(cudaMalloc(&c->d_q_n, sizeof(int32_t)));
+            CKC(cudaMalloc(&c->d_cell_base, sizeof(int32_t) * c->n_cells));
+            CKC(cudaMalloc(&c->d_q_ref, sizeof(float4) * nq));
+            CKC(cudaMalloc(&c->d_q_box, sizeof(float4) * 2 * nq));
+            CKC(cudaMalloc(&c->d_q_cell, sizeof(int32_t) * nq));
+            CKC(cudaMalloc(&c->d_q_list, sizeof(int32_t) * kQMax * nq));
+            CKC(cudaMalloc(&c->d_q_count, sizeof(int32_t) * nq));
+            CKC(cudaMemset(c->d_q_n, 0, sizeof(int32_t)));
+            CKC(cudaMemset(c->d_cell_base, 0, sizeof(int32_t) * c->n_cells));
+            CKC(cudaMemset(c->d_q_count, 0, sizeof(int32_t) * nq));
+        } else {
+            CKC(cudaMalloc(&c->d_vlist, sizeof(int32_t) * kVMax * ns));
+            CKC(cudaMalloc(&c->d_vcount, sizeof(int32_t) * ns));
+            CKC(cudaMalloc(&c->d_vsub, sizeof(int32_t) * kVLanes * ns));
+            CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
+            CKC(cudaMemset(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns));
+            CKC(cudaMemset(c->d_vcount, 0, sizeof(int32_t) * ns));
+            CKC(cudaMemset(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns));
+        }
     }
     for (int k = 0; k < 2; ++k) {
         CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
@@ -1138,7 +1162,17 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
     if (ms_d) *ms_d = td / reps;
     if (ms_f) *ms_f = tf / reps;
-    if (pairs && vl) {  // list entries (pairs tested per pass)
+    if (pairs && vl && c->nqmax > 0) {  // quad lists: 16 pairs tested per listed quad
+        int32_t nq = 0;
+        std::vector<int32_t> cnt(c->nqmax);
+        CK(c, cudaMemcpyAsync(&nq, c->d_q_n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(cnt.data(), c->d_q_count, sizeof(int32_t) * c->nqmax, cudaMemcpyDeviceToHost,
+                              c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        double p = 0;
+        for (int q = 0; q < nq && q < c->nqmax; ++q) p += 16.0 * cnt[q];
+        *pairs = p;
+    } else if (pairs && vl) {  // list entries (pairs tested per pass)
         std::vector<int32_t> cnt(c->ntot);
         CK(c, cudaMemcpyAsync(cnt.data(), c->d_vcount, sizeof(int32_t) * c->ntot, cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));

@@ -41,7 +41,7 @@ __global__ void k_cell_clear(const Dev d, int cond, int k_local) {
     pdl_launch_dependents();
     pdl_wait();
     if (cond && !vlist_rebuild_due(d, k_local)) return;
-    if (d.path == 2 && blockIdx.x == 0 && threadIdx.x == 0) *d.vslot = 0;
+    if (d.path == 2 && d.vslot && blockIdx.x == 0 && threadIdx.x == 0) *d.vslot = 0;  // FP64 lists
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.n_cells; c += gridDim.x * blockDim.x)
         d.cell_count[c] = 0;
 }

@@ -30,6 +30,7 @@ constexpr int kCellCap = 256;   // atoms a cell of the cell-list path can hold
 constexpr int kVMax = 512;      // entries a neighbour list can hold
 constexpr int kVLog = 3;        // a list is split into kVLanes sub-lists, one per thread of its atom
 constexpr int kVLanes = 1 << kVLog;
+constexpr int kQMax = 768;      // quads a quad's neighbour list can hold (MIXED lists)
 
 // Fields of an observable partial record (per 32-atom group).
 enum ObsField {
@@ -60,7 +61,6 @@ struct Item {
 struct CellGrid {
     int32_t G, off;
     double h, E, inv_h;
-    double frame;  // neighbour-list path: power-of-two shift S of the split FP32 coordinates
 };
 
 // Derived potential constants.
@@ -147,17 +147,27 @@ struct Dev {
     int32_t nslot;       // list slots (the real atoms, in cell order at the last rebuild)
     float vskin2h;       // (skin / 2)^2
     double vrl2;         // (rcut + skin)^2
-    int32_t* vlist;      // [nslot][kVMax] slots of the neighbours, by (atom mod kVLanes, atom)
-    int32_t* vcount;     // [nslot]
-    int32_t* vsub;       // [nslot][kVLanes] end of each sub-list (the entries j with j mod kVLanes = t)
-    int32_t* vorder;     // [nslot] atom of each slot
+    int32_t* vlist;      // FP64: [nslot][kVMax] slots of the neighbours, by (atom mod kVLanes, atom)
+    int32_t* vcount;     // FP64: [nslot]
+    int32_t* vsub;       // FP64: [nslot][kVLanes] end of each sub-list (the entries j with j mod kVLanes = t)
+    int32_t* vorder;     // [nslot] atom of each slot (MIXED: -1 for the empty slots that pad cells to quads)
     int32_t* vslotof;    // [npad] slot of each atom
-    int32_t* vslot;      // [1] slot counter of a rebuild
-    void* vhi;           // [nslot] V4 by slot: MIXED (hi part of x - o + S, 0); FP64 (x, y, z, 0)
-    float4* vlo;         // [nslot] MIXED: low part of x - o + S
-    void* vposg;         // [nslot] V4 (vhi.xyz, B6 rho^-1/2), written by the density pass
-    double* vxref;       // [3][npad] positions at the last rebuild
+    int32_t* vslot;      // FP64: [1] slot counter of a rebuild
+    void* vhi;           // [nslot] by slot: FP64 double4 (x, y, z, 0); MIXED float4 (offset from the quad's
+                         // reference point, 0)
+    void* vposg;         // [nslot] (vhi.xyz, B6 rho^-1/2), written by the density pass
+    double* vxref;       // [3][nslot] positions at the last rebuild
     uint32_t* vdmax;     // [2] largest squared displacement since the rebuild (float bits), by step parity
+    // MIXED neighbour lists are lists of quads (4 consecutive slots of one cell, in Morton order within
+    // the cell; cells padded to whole quads with empty slots, vorder = -1). nslot = 4 * nqmax there.
+    int32_t nqmax;       // quads allocated
+    int32_t* q_n;        // [1] quads in use since the last rebuild
+    int32_t* cell_base;  // [n_cells] first slot of each cell
+    float4* q_ref;       // [nqmax] reference point of each quad relative to the origin (a multiple of 2^-12 A)
+    float4* q_box;       // [nqmax][2] bounding box (lo, hi) of its atoms at the rebuild, relative to the origin
+    int32_t* q_cell;     // [nqmax] cell of each quad
+    int32_t* q_list;     // [nqmax][kQMax] quads whose boxes lie within rcut + skin of this one's
+    int32_t* q_count;    // [nqmax]
 };
 
 constexpr int kHistFields = 20;  // doubles per history record (see md_obs packing in the API)
@@ -198,6 +208,11 @@ cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s);
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s);
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
+// MIXED quad lists (defined in scmd_quads.cu); launch_v_* dispatch to them for MIXED.
+cudaError_t launch_q_pos(const Dev& d, int k_local, cudaStream_t s);
+cudaError_t launch_q_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
+cudaError_t launch_q_density(const Dev& d, int obs, cudaStream_t s);
+cudaError_t launch_q_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // Structural observables (defined in scmd_structure.cu).
 constexpr int kNbCap = 32;  // neighbours a CNA list stores (the count is exact beyond)
 struct StructBufs {

@@ -1,0 +1,477 @@
+// scmd_quads.cu -- MIXED neighbour lists as lists of atom quads (the pair passes with a strict cutoff).
+//
+// Per-atom lists make every tested pair a gather of a random neighbour, and in FP32 those gathers,
+// not the arithmetic, bound the passes. Here the unit is a quad: 4 consecutive slots of one cell,
+// with a cell's atoms in Morton order (sub-cells of side h/8), so a quad is a compact group. Each
+// quad keeps the list of quads whose bounding boxes (at the last rebuild) lie within rcut + skin of
+// its own. A pass runs one warp per quad: lane l holds atom l % 4 of the (l / 4)-th of 8 listed
+// quads and tests it against the 4 atoms of the warp's own quad, so one warp-wide load brings 32
+// neighbours for 128 pairs. Per step:
+//   k_q_pos    : every slot's offset from its quad's reference point, and the largest squared
+//                displacement since the last rebuild;
+//   rebuild, when that displacement exceeds the trigger (the kernels exit at once otherwise):
+//     the cell build of the cell-list path (clear, bin, sort), then
+//     k_q_scan   : the first slot of every cell (cells padded to whole quads), and the quad count;
+//     k_q_order  : one CTA per cell: its atoms in Morton order into slots; per quad the reference
+//                  point, the bounding box and the offsets;
+//     k_q_list   : one warp per quad: the quads of the 27 cells around it whose boxes are in reach;
+//   k_q_density, k_q_force : one warp per quad; per CTA of 8 quads, one warp then finishes the 32
+//                atoms (the FP64 per-atom work on full warps).
+// Coordinates: a quad's reference point C is its atoms' centroid rounded to a multiple of 2^-12 A,
+// exact in FP32, so C_i - C_j is exact; an atom is stored as its FP32 offset o = x - C (|o| of a
+// few A). A listed atom enters a pair as o_j - (C_i - C_j), rounded once, like the staged positions
+// of the cell-list passes. The self pair gives r^2 = 0 exactly and is masked with the cutoff test.
+// The sums run over quads in list order, which depends on when the lists were built: unlike the
+// FP64 lists, a resumed MIXED run agrees with an uninterrupted one to rounding, not bit for bit.
+// Runs are deterministic: slots follow the cell order and lists the fixed order of the 27 cells.
+#include "scmd_cells.cuh"
+
+namespace scmd {
+
+namespace {
+
+constexpr int kQThreads = 256;  // 8 warps, one quad each
+constexpr float kFar = 1.0e5f;  // coordinate of an empty slot: outside every cutoff of every atom
+
+// Sub-cell (side h/8) of an offset from the cell centre along one axis, clamped to the cell.
+__device__ __forceinline__ uint32_t sub8(float o, float h) {
+    const int k = (int)floorf((o + 0.5f * h) * (8.0f / h));
+    return (uint32_t)min(max(k, 0), 7);
+}
+__device__ __forceinline__ uint32_t morton9(const float4& p, float h) {
+    const uint32_t x = sub8(p.x, h), y = sub8(p.y, h), z = sub8(p.z, h);
+    uint32_t k = 0;
+#pragma unroll
+    for (int b = 2; b >= 0; --b) k = (k << 3) | (((x >> b) & 1u) << 2) | (((y >> b) & 1u) << 1) | ((z >> b) & 1u);
+    return k;
+}
+
+// ---------------------------------------------------------------- every step
+__global__ void __launch_bounds__(kQThreads) k_q_pos(const Dev d, int k_local) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int64_t step = *d.step_base + k_local;
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.vdmax[(step + 1) & 1] = 0u;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float dmax = 0.f;
+    const int i = s < 4 * *d.q_n ? d.vorder[s] : -1;
+    if (i >= 0) {
+        const int np = d.npad, ns = d.nslot;
+        const double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
+        const double* o = d.origin + 3 * d.cl_of_group[i >> 5];
+        const float4 C = d.q_ref[s >> 2];
+        reinterpret_cast<float4*>(d.vhi)[s] = make_float4((float)((x - o[0]) - (double)C.x),
+                                                          (float)((y - o[1]) - (double)C.y),
+                                                          (float)((z - o[2]) - (double)C.z), 0.f);
+        const double ex = x - d.vxref[s], ey = y - d.vxref[ns + s], ez = z - d.vxref[2 * ns + s];
+        dmax = (float)(ex * ex + ey * ey + ez * ez);
+        if (!(dmax <= 3.0e38f)) dmax = 3.0e38f;  // non-finite positions force a rebuild
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.f) atomicMax(d.vdmax + (step & 1), __float_as_uint(dmax));
+}
+
+// ---------------------------------------------------------------- rebuild
+// One CTA: the first slot of every cell (its atoms padded to whole quads), in cell order.
+__global__ void __launch_bounds__(1024) k_q_scan(const Dev d, int cond, int k_local) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    pdl_launch_dependents();
+    pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < d.n_cells; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const int v = c < d.n_cells ? (min(d.cell_count[c], kCellCap) + 3) & ~3 : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            s_warp[lane] = t;  // inclusive prefix over warps
+        }
+        __syncthreads();
+        const int excl = s_carry + (w > 0 ? s_warp[w - 1] : 0) + x - v;
+        if (c < d.n_cells) d.cell_base[c] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_warp[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *d.q_n = s_carry >> 2;
+}
+
+// One CTA per cell: rank its atoms by (Morton key of the sub-cell, index), place them, and set up
+// each of its quads.
+__global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond, int k_local) {
+    __shared__ uint32_t s_key[kCellCap];
+    __shared__ int s_atom[kCellCap];
+    __shared__ int s_sorted[kCellCap];
+    pdl_launch_dependents();
+    pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
+    const int c = blockIdx.x;
+    const int n = min(d.cell_count[c], kCellCap);
+    if (n == 0) return;
+    const int cl = d.cell_cl[c];
+    const float h = (float)d.grid[cl].h;
+    const float4* cp = reinterpret_cast<const float4*>(d.cpos);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        s_key[k] = morton9(cp[(size_t)c * kCellCap + k], h);
+        s_atom[k] = d.cell_atoms[(size_t)c * kCellCap + k];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const uint32_t key = s_key[k];
+        const int a = s_atom[k];
+        int r = 0;
+        for (int m = 0; m < n; ++m) r += (s_key[m] < key) || (s_key[m] == key && s_atom[m] < a);
+        s_sorted[r] = a;
+    }
+    __syncthreads();
+    const int base = d.cell_base[c], n4 = (n + 3) & ~3, ns = d.nslot, np = d.npad;
+    for (int r = threadIdx.x; r < n4; r += blockDim.x) {
+        const int a = r < n ? s_sorted[r] : -1;
+        d.vorder[base + r] = a;
+        if (a >= 0) d.vslotof[a] = base + r;
+    }
+    const double* o = d.origin + 3 * cl;
+    for (int t = threadIdx.x; t < n4 / 4; t += blockDim.x) {
+        const int Q = (base >> 2) + t;
+        double rel[4][3], cen[3] = {0.0, 0.0, 0.0}, lo[3], hi[3];
+        int cnt = 0;
+        for (int u = 0; u < 4; ++u) {
+            const int r = 4 * t + u;
+            if (r >= n) break;
+            const int a = s_sorted[r];
+            for (int q = 0; q < 3; ++q) {
+                rel[u][q] = d.x[q * np + a] - o[q];
+                cen[q] += rel[u][q];
+                lo[q] = cnt == 0 ? rel[u][q] : fmin(lo[q], rel[u][q]);
+                hi[q] = cnt == 0 ? rel[u][q] : fmax(hi[q], rel[u][q]);
+            }
+            ++cnt;
+        }
+        float4 C;
+        C.x = (float)(rint(cen[0] / cnt * 4096.0) * (1.0 / 4096.0));
+        C.y = (float)(rint(cen[1] / cnt * 4096.0) * (1.0 / 4096.0));
+        C.z = (float)(rint(cen[2] / cnt * 4096.0) * (1.0 / 4096.0));
+        C.w = 0.f;
+        d.q_ref[Q] = C;
+        d.q_box[2 * Q] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
+        d.q_box[2 * Q + 1] =
+            make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
+        d.q_cell[Q] = c;
+        for (int u = 0; u < 4; ++u) {
+            const int s = 4 * Q + u;
+            float4 p = make_float4(kFar, kFar, kFar, 0.f);
+            if (u < cnt) {
+                const int a = s_sorted[4 * t + u];
+                p = make_float4((float)(rel[u][0] - (double)C.x), (float)(rel[u][1] - (double)C.y),
+                                (float)(rel[u][2] - (double)C.z), 0.f);
+                d.vxref[s] = d.x[a];
+                d.vxref[ns + s] = d.x[np + a];
+                d.vxref[2 * ns + s] = d.x[2 * np + a];
+            }
+            reinterpret_cast<float4*>(d.vhi)[s] = p;
+        }
+    }
+}
+
+// One warp per quad: the quads of the 27 cells around its cell (fixed order) whose bounding boxes
+// come closer than rcut + skin to its own, appended in that order.
+__global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int k_local) {
+    pdl_launch_dependents();
+    pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
+    const int lane = threadIdx.x & 31;
+    const int Q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (Q >= *d.q_n) return;
+    const int c = d.q_cell[Q];
+    const CellGrid g = d.grid[d.cell_cl[c]];
+    const int loc = c - g.off, cx = loc % g.G, cy = (loc / g.G) % g.G, cz = loc / (g.G * g.G);
+    const float4 lo = d.q_box[2 * Q], hi = d.q_box[2 * Q + 1];
+    const float rl2 = (float)d.vrl2;
+    int* out = d.q_list + (size_t)Q * kQMax;
+    int n = 0;
+    bool overflow = false;
+    for (int nb = 0; nb < 27; ++nb) {
+        const int x = cx + nb % 3 - 1, y = cy + (nb / 3) % 3 - 1, z = cz + nb / 9 - 1;
+        if (x < 0 || x >= g.G || y < 0 || y >= g.G || z < 0 || z >= g.G) continue;
+        const int c2 = g.off + (z * g.G + y) * g.G + x;
+        const int q0 = d.cell_base[c2] >> 2, nq = (min(d.cell_count[c2], kCellCap) + 3) >> 2;
+        for (int t0 = 0; t0 < nq; t0 += 32) {
+            bool in = false;
+            const int J = q0 + t0 + lane;
+            if (t0 + lane < nq) {
+                const float4 l2 = d.q_box[2 * J], h2 = d.q_box[2 * J + 1];
+                const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
+                const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
+                const float ez = fmaxf(0.f, fmaxf(l2.z - hi.z, lo.z - h2.z));
+                in = ex * ex + ey * ey + ez * ez < rl2;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, in);
+            const int pos = n + __popc(b & ((1u << lane) - 1u));
+            if (in) {
+                if (pos < kQMax)
+                    out[pos] = J;
+                else
+                    overflow = true;
+            }
+            n += __popc(b);
+        }
+    }
+    if (lane == 0) d.q_count[Q] = min(n, kQMax);
+    if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(d.status, 4);
+}
+
+// ---------------------------------------------------------------- passes
+// The listed atom of this lane at list position k, as an offset from the warp's quad reference
+// point (or far away past the end of the list).
+__device__ __forceinline__ float4 q_neighbour(const Dev& d, const float4* vp, const int* L, int k, int n, int q,
+                                              const float4& CI) {
+    if (k >= n) return make_float4(kFar, kFar, kFar, 0.f);
+    const int J = L[k];
+    const float4 pj = vp[4 * J + q];
+    const float4 CJ = d.q_ref[J];
+    return make_float4(pj.x - (CI.x - CJ.x), pj.y - (CI.y - CJ.y), pj.z - (CI.z - CJ.z), pj.w);
+}
+
+// The 4 atoms of this warp's quad (far away for a warp past the last quad).
+__device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int nq, float4 oi[4], float4& CI) {
+    if (Q >= nq) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) oi[a] = make_float4(kFar, kFar, kFar, 0.f);
+        CI = make_float4(0.f, 0.f, 0.f, 0.f);
+        return 0;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) oi[a] = vp[4 * Q + a];
+    CI = d.q_ref[Q];
+    return d.q_count[Q];
+}
+
+// Each CTA takes 8 quads (32 slots). The warps sum their quads' pairs; then warp 0 finishes all 32
+// atoms with one lane each, so the FP64 per-atom work runs on full warps.
+template <int SPECIAL, int SHIFT>
+__global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs) {
+    __shared__ double s_sum[32];
+    __shared__ float4 s_own[32];
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 3;
+    const int nq = *d.q_n, Q = blockIdx.x * (kQThreads / 32) + w;
+    if (blockIdx.x * (kQThreads / 32) >= nq) return;  // the whole CTA is past the last quad
+    const float4* vp = reinterpret_cast<const float4*>(d.vhi);
+    float4 oi[4], CI;
+    const int n = q_own(d, vp, Q, nq, oi, CI);
+    const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
+    const float rc2 = (float)d.pot.rcut2;
+    const int mexp = d.pot.m;
+    float tacc[4] = {0.f, 0.f, 0.f, 0.f};
+    int nin[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < n; k0 += 8) {
+        const float4 p = q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const bool in = r2 < rc2 && r2 > 0.f;
+            r2 = in ? r2 : big<float>();
+            if (SHIFT) nin[a] += in;
+            if (SPECIAL) {
+                const float inv = inv_r2(r2);
+                tacc[a] = fmaf(inv * inv, inv, tacc[a]);
+            } else {
+                const float ir = inv_r(r2);
+                tacc[a] += rpow(ir * ir, ir, mexp);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {  // a fixed butterfly over the warp: every lane gets the sums
+        double v = (double)tacc[a];
+        int m = nin[a];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (SHIFT) m += __shfl_xor_sync(0xffffffffu, m, o);
+        }
+        if (lane == a) {
+            s_sum[4 * w + a] = SHIFT ? v - (double)m * d.pot.shm : v;
+            s_own[4 * w + a] = oi[a];
+        }
+    }
+    __syncthreads();
+    if (w != 0 || blockIdx.x * (kQThreads / 32) + (lane >> 2) >= nq) return;
+    const int s = blockIdx.x * kQThreads / 8 + lane, i = d.vorder[s];
+    float4 pg = make_float4(kFar, kFar, kFar, 0.f);
+    if (i >= 0) {
+        const double rho = s_sum[lane] * d.pot.am;
+        d.rho[i] = rho;
+        const float rf = (float)rho;
+        float y = rsqrt_approx(rf);
+        y = y * (1.5f - 0.5f * rf * y * y);  // one Newton step
+        const float4 me = s_own[lane];
+        pg = make_float4(me.x, me.y, me.z, rho > 0.0 ? (float)d.pot.B6 * y : 0.0f);
+        if (obs) d.eatom[2 * i] = -d.pot.eps * d.pot.c * sqrt(rho);
+    }
+    reinterpret_cast<float4*>(d.vposg)[s] = pg;
+}
+
+// mode 0: forces; 1: forces and per-atom pair energies; 2: MD step (second half kick, per-atom
+// observables if due, then the first half of the next step unless last or Berendsen).
+template <int SPECIAL, int ENERGY>
+__global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, int k_local, int last) {
+    __shared__ float s_f[3][32];
+    __shared__ double s_e[ENERGY ? 32 : 1];
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 3;
+    const int nq = *d.q_n, Q = blockIdx.x * (kQThreads / 32) + w;
+    if (blockIdx.x * (kQThreads / 32) >= nq) return;  // the whole CTA is past the last quad
+    const float4* vp = reinterpret_cast<const float4*>(d.vposg);
+    float4 oi[4], CI;
+    const int n = q_own(d, vp, Q, nq, oi, CI);
+    const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
+    const float A = (float)d.pot.A9;
+    const float rc2 = (float)d.pot.rcut2;
+    const int nexp = d.pot.n, mexp = d.pot.m;
+    float fx[4] = {0.f, 0.f, 0.f, 0.f}, fy[4] = {0.f, 0.f, 0.f, 0.f}, fz[4] = {0.f, 0.f, 0.f, 0.f};
+    float se[4] = {0.f, 0.f, 0.f, 0.f};
+    int nin[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < n; k0 += 8) {
+        const float4 p = q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const bool in = r2 < rc2 && r2 > 0.f;
+            r2 = in ? r2 : big<float>();
+            const float ir = inv_r(r2);
+            const float inv = ir * ir;
+            float coef, rn;
+            if (SPECIAL) {
+                const float inv2 = inv * inv, inv4 = inv2 * inv2;
+                coef = inv4 * fmaf(A, inv * ir, -(oi[a].w + p.w));
+                rn = inv4 * ir;
+            } else {
+                rn = rpow(inv, ir, nexp);
+                const float rm = rpow(inv, ir, mexp);
+                coef = inv * (A * rn - (oi[a].w + p.w) * rm);
+            }
+            fx[a] = fmaf(coef, dx, fx[a]);
+            fy[a] = fmaf(coef, dy, fy[a]);
+            fz[a] = fmaf(coef, dz, fz[a]);
+            if (ENERGY) {
+                se[a] += rn;
+                nin[a] += in;
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float x = fx[a], y = fy[a], z = fz[a];
+        double e = ENERGY ? (double)se[a] : 0.0;
+        int m = nin[a];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+            if (ENERGY) {
+                e += __shfl_xor_sync(0xffffffffu, e, o);
+                m += __shfl_xor_sync(0xffffffffu, m, o);
+            }
+        }
+        if (lane == a) {
+            s_f[0][4 * w + a] = x;
+            s_f[1][4 * w + a] = y;
+            s_f[2][4 * w + a] = z;
+            if (ENERGY) s_e[4 * w + a] = e - (d.pot.shift ? (double)m * d.pot.shn : 0.0);
+        }
+    }
+    __syncthreads();
+    if (w != 0 || blockIdx.x * (kQThreads / 32) + (lane >> 2) >= nq) return;
+    const int i = d.vorder[blockIdx.x * kQThreads / 8 + lane];
+    if (i < 0) return;
+    const float Fx = s_f[0][lane], Fy = s_f[1][lane], Fz = s_f[2][lane];
+    const int np = d.npad;
+    float* fo = reinterpret_cast<float*>(d.f);
+    fo[i] = Fx;
+    fo[np + i] = Fy;
+    fo[2 * np + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+    if (ENERGY) d.eatom[2 * i + 1] = s_e[lane];
+    if (mode != 2) return;
+    const Run& r = *d.run;
+    const int cl = d.cl_of_group[i >> 5];
+    const double hs = d.hs[i];
+    const double vx = fma(hs, (double)Fx, d.v[i]);
+    const double vy = fma(hs, (double)Fy, d.v[np + i]);
+    const double vz = fma(hs, (double)Fz, d.v[2 * np + i]);
+    d.v[i] = vx;
+    d.v[np + i] = vy;
+    d.v[2 * np + i] = vz;
+    if (r.kind == 2) return;  // Berendsen: the rescale kernel records and starts the step
+    if (ENERGY) {             // observables at the end of this step, before the next begins
+        for (int k = 0; k < 3; ++k) d.obs_x[3 * i + k] = d.x[k * np + i];
+        d.obs_v[3 * i] = vx;
+        d.obs_v[3 * i + 1] = vy;
+        d.obs_v[3 * i + 2] = vz;
+    }
+    if (!last)
+        begin_step<1>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, (double)Fx, (double)Fy, (double)Fz,
+                      k_local + 1);
+}
+
+int q_pass_grid(const Dev& d) { return (d.nqmax + kQThreads / 32 - 1) / (kQThreads / 32); }
+
+template <int SHIFT> cudaError_t q_density_s(const Dev& d, int obs, cudaStream_t s) {
+    return d.pot.special ? launch_ex(k_q_density<1, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs)
+                         : launch_ex(k_q_density<0, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs);
+}
+
+template <int ENERGY> cudaError_t q_force_e(const Dev& d, int mode, int k, int last, cudaStream_t s) {
+    return d.pot.special ? launch_ex(k_q_force<1, ENERGY>, q_pass_grid(d), kQThreads, 0, 0, s, d, mode, k, last)
+                         : launch_ex(k_q_force<0, ENERGY>, q_pass_grid(d), kQThreads, 0, 0, s, d, mode, k, last);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_q_pos(const Dev& d, int k_local, cudaStream_t s) {
+    return launch_ex(k_q_pos, (d.nslot + kQThreads - 1) / kQThreads, kQThreads, 0, 0, s, d, k_local);
+}
+
+cudaError_t launch_q_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s) {
+    cudaError_t e = launch_ex(k_q_scan, 1, 1024, 0, 0, s, d, cond, k_local);
+    if (e != cudaSuccess) return e;
+    e = launch_ex(k_q_order, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_q_list, q_pass_grid(d), kQThreads, 0, 0, s, d, cond, k_local);
+}
+
+cudaError_t launch_q_density(const Dev& d, int obs, cudaStream_t s) {
+    return d.pot.shift ? q_density_s<1>(d, obs, s) : q_density_s<0>(d, obs, s);
+}
+
+cudaError_t launch_q_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
+    const bool energy = (mode == 1) || (mode == 2 && (flags & 2));
+    const int lst = flags & 1;
+    return energy ? q_force_e<1>(d, mode, k_local, lst, s) : q_force_e<0>(d, mode, k_local, lst, s);
+}
+
+}  // namespace scmd

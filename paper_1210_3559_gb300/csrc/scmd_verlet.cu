@@ -1,4 +1,5 @@
-// scmd_verlet.cu -- the neighbour-list path of the two pair passes (strict cutoff r < rcut).
+// scmd_verlet.cu -- the neighbour-list path of the two pair passes (strict cutoff r < rcut), FP64.
+// (MIXED lists are lists of atom quads: scmd_quads.cu.)
 //
 // Each atom keeps the list of the atoms that were closer than rcut + skin when the lists were last
 // built. As long as no atom has moved more than skin / 2 since, every pair closer than rcut is in
@@ -15,10 +16,7 @@
 //                  their slots, and the ends of the kVLanes sub-lists;
 //     k_v_commit : the pass coordinates in the new slot order and the reference positions;
 //   k_v_density, k_v_force : kVLanes threads per atom, thread t over sub-list t.
-// MIXED pass coordinates are x - o + S split into FP32 high and low parts, S a power of two with
-// every coordinate of the cluster in [32, 2S): the high parts of two atoms less than 16 A apart
-// differ exactly, and dx = (hi_i - hi_j) + (lo_i - lo_j) is within about one rounding of the FP64
-// separation. FP64 passes read the positions themselves.
+// The passes read the positions themselves (by slot).
 // Results do not depend on when the lists were built: what a thread sums is the pairs inside rcut
 // whose j is in its residue class, in ascending j (a pair outside rcut is masked to r2 = inf and
 // adds an exact zero); its pass-precision partial sums are folded every kSpanV pairs inside rcut;
@@ -31,32 +29,14 @@ namespace scmd {
 constexpr int kSpanV = 64;  // pairs inside rcut a thread sums in the pass precision before a fold
 constexpr int kVThreads = 256;
 template <int PREC> struct BuildChunk;  // staged atoms per chunk of the list build (48 KB static limit)
-template <> struct BuildChunk<1> { static constexpr int TJ = 1536; };
 template <> struct BuildChunk<0> { static constexpr int TJ = 768; };
 static_assert(kVLog >= 1 && kVLog <= 4, "an atom's threads must sit in one warp");
 
-// Pass coordinates of atom i at slot s (see the top of the file).
+// Pass coordinates of atom i at slot s.
 template <int PREC>
 __device__ __forceinline__ void v_store(const Dev& d, int s, int i, double x, double y, double z) {
-    if (PREC == 1) {
-        const int cl = d.cl_of_group[i >> 5];
-        const double* o = d.origin + 3 * cl;
-        const double S = d.grid[cl].frame;
-        const double ux = (x - o[0]) + S, uy = (y - o[1]) + S, uz = (z - o[2]) + S;
-        float4 h, l;
-        h.x = (float)ux;
-        h.y = (float)uy;
-        h.z = (float)uz;
-        h.w = 0.f;
-        l.x = (float)(ux - (double)h.x);
-        l.y = (float)(uy - (double)h.y);
-        l.z = (float)(uz - (double)h.z);
-        l.w = 0.f;
-        reinterpret_cast<float4*>(d.vhi)[s] = h;
-        d.vlo[s] = l;
-    } else {
-        reinterpret_cast<double4*>(d.vhi)[s] = make_double4(x, y, z, 0.0);
-    }
+    static_assert(PREC == 0, "MIXED lists are quad lists");
+    reinterpret_cast<double4*>(d.vhi)[s] = make_double4(x, y, z, 0.0);
 }
 
 // ---------------------------------------------------------------- every step
@@ -236,21 +216,14 @@ template <int PREC> __global__ void k_v_commit(const Dev d, int cond, int k_loca
 }
 
 // ---------------------------------------------------------------- passes
-// Separation of the atoms at slots a (coordinates pa, la) and q.
+// Separation of the atoms at slots a (coordinates pa) and q.
 template <int PREC>
-__device__ __forceinline__ void v_sep(const Dev& d, const typename Tr<PREC>::V4& pa, const float4& la,
-                                      const typename Tr<PREC>::V4& pq, int q, typename Tr<PREC>::R& dx,
-                                      typename Tr<PREC>::R& dy, typename Tr<PREC>::R& dz) {
-    if (PREC == 1) {
-        const float4 lq = d.vlo[q];
-        dx = (pa.x - pq.x) + (la.x - lq.x);
-        dy = (pa.y - pq.y) + (la.y - lq.y);
-        dz = (pa.z - pq.z) + (la.z - lq.z);
-    } else {
-        dx = pa.x - pq.x;
-        dy = pa.y - pq.y;
-        dz = pa.z - pq.z;
-    }
+__device__ __forceinline__ void v_sep(const typename Tr<PREC>::V4& pa, const typename Tr<PREC>::V4& pq,
+                                      typename Tr<PREC>::R& dx, typename Tr<PREC>::R& dy,
+                                      typename Tr<PREC>::R& dz) {
+    dx = pa.x - pq.x;
+    dy = pa.y - pq.y;
+    dz = pa.z - pq.z;
 }
 
 // The sum of a double over the kVLanes threads of an atom, in a fixed tree (every thread gets it).
@@ -272,7 +245,6 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     if (s >= d.nslot) return;  // whole atoms leave together
     const V4* vp = reinterpret_cast<const V4*>(d.vhi);
     const V4 pi = vp[s];
-    const float4 li = PREC == 1 ? d.vlo[s] : float4{};
     const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
     const R rc2 = (R)d.pot.rcut2;
     const int mexp = d.pot.m;
@@ -285,7 +257,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
     for (int e = beg; e < end; ++e) {
         const int q = lst[e];
         R dx, dy, dz;
-        v_sep<PREC>(d, pi, li, vp[q], q, dx, dy, dz);
+        v_sep<PREC>(pi, vp[q], dx, dy, dz);
         R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const bool in = r2 < rc2;
         r2 = in ? r2 : big<R>();
@@ -344,7 +316,6 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
     if (s >= d.nslot) return;  // whole atoms leave together
     const V4* vp = reinterpret_cast<const V4*>(d.vposg);
     const V4 pi = vp[s];
-    const float4 li = PREC == 1 ? d.vlo[s] : float4{};
     const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
     const R A = (R)d.pot.A9;
     const R rc2 = (R)d.pot.rcut2;
@@ -358,7 +329,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
         const int q = lst[e];
         const V4 pj = vp[q];
         R dx, dy, dz;
-        v_sep<PREC>(d, pi, li, pj, q, dx, dy, dz);
+        v_sep<PREC>(pi, pj, dx, dy, dz);
         R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const bool in = r2 < rc2;
         r2 = in ? r2 : big<R>();
@@ -431,22 +402,20 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
 }
 
 // ---------------------------------------------------------------- launchers
+// MIXED contexts run the quad lists (scmd_quads.cu).
 cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s) {
-    const int grid = (d.nslot + kVThreads - 1) / kVThreads;
-    return d.prec == 1 ? launch_ex(k_v_pos<1>, grid, kVThreads, 0, 0, s, d, k_local)
-                       : launch_ex(k_v_pos<0>, grid, kVThreads, 0, 0, s, d, k_local);
+    if (d.prec == 1) return launch_q_pos(d, k_local, s);
+    return launch_ex(k_v_pos<0>, (d.nslot + kVThreads - 1) / kVThreads, kVThreads, 0, 0, s, d, k_local);
 }
 
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s) {
-    cudaError_t e = d.prec == 1 ? launch_ex(k_v_build<1>, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local)
-                                : launch_ex(k_v_build<0>, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local);
+    if (d.prec == 1) return launch_q_rebuild(d, cond, k_local, s);
+    cudaError_t e = launch_ex(k_v_build<0>, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
     e = launch_ex(k_v_sort, (d.nslot + kVThreads / 32 - 1) / (kVThreads / 32), kVThreads, 0, 0, s, d, cond,
                   k_local);
     if (e != cudaSuccess) return e;
-    const int grid = (d.nslot + kVThreads - 1) / kVThreads;
-    return d.prec == 1 ? launch_ex(k_v_commit<1>, grid, kVThreads, 0, 0, s, d, cond, k_local)
-                       : launch_ex(k_v_commit<0>, grid, kVThreads, 0, 0, s, d, cond, k_local);
+    return launch_ex(k_v_commit<0>, (d.nslot + kVThreads - 1) / kVThreads, kVThreads, 0, 0, s, d, cond, k_local);
 }
 
 static int v_pass_grid(const Dev& d) {
@@ -454,28 +423,22 @@ static int v_pass_grid(const Dev& d) {
 }
 
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s) {
-    const int grid = v_pass_grid(d);
-    const bool sp = d.pot.special != 0;
-    if (d.prec == 1)
-        return sp ? launch_ex(k_v_density<1, 1>, grid, kVThreads, 0, 0, s, d, obs)
-                  : launch_ex(k_v_density<1, 0>, grid, kVThreads, 0, 0, s, d, obs);
-    return sp ? launch_ex(k_v_density<0, 1>, grid, kVThreads, 0, 0, s, d, obs)
-              : launch_ex(k_v_density<0, 0>, grid, kVThreads, 0, 0, s, d, obs);
+    if (d.prec == 1) return launch_q_density(d, obs, s);
+    return d.pot.special ? launch_ex(k_v_density<0, 1>, v_pass_grid(d), kVThreads, 0, 0, s, d, obs)
+                         : launch_ex(k_v_density<0, 0>, v_pass_grid(d), kVThreads, 0, 0, s, d, obs);
 }
 
-template <int PREC, int ENERGY>
+template <int ENERGY>
 static cudaError_t v_force_e(const Dev& d, int mode, int k, int last, cudaStream_t s) {
-    const int grid = v_pass_grid(d);
-    return d.pot.special ? launch_ex(k_v_force<PREC, 1, ENERGY>, grid, kVThreads, 0, 0, s, d, mode, k, last)
-                         : launch_ex(k_v_force<PREC, 0, ENERGY>, grid, kVThreads, 0, 0, s, d, mode, k, last);
+    return d.pot.special ? launch_ex(k_v_force<0, 1, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d, mode, k, last)
+                         : launch_ex(k_v_force<0, 0, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d, mode, k, last);
 }
 
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
+    if (d.prec == 1) return launch_q_force(d, mode, k_local, flags, s);
     const bool energy = (mode == 1) || (mode == 2 && (flags & 2));
     const int lst = flags & 1;
-    if (d.prec == 1)
-        return energy ? v_force_e<1, 1>(d, mode, k_local, lst, s) : v_force_e<1, 0>(d, mode, k_local, lst, s);
-    return energy ? v_force_e<0, 1>(d, mode, k_local, lst, s) : v_force_e<0, 0>(d, mode, k_local, lst, s);
+    return energy ? v_force_e<1>(d, mode, k_local, lst, s) : v_force_e<0>(d, mode, k_local, lst, s);
 }
 
 }  // namespace scmd

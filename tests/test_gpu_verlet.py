@@ -1,6 +1,8 @@
 """GPU parity of the neighbour-list path (strict cutoff, lists of rcut + 1 A rebuilt after 0.5 A of
-motion) against the FP64 oracle with the same cutoff, and its list-independence: the forces do not
-depend on when the lists were built, so a resumed run matches an uninterrupted one bit for bit.
+motion; per-atom lists in FP64, lists of atom quads in MIXED) against the FP64 oracle with the same
+cutoff. The FP64 forces do not depend on when the lists were built, so a resumed run matches an
+uninterrupted one bit for bit; MIXED sums in list order, so there it agrees to rounding, and repeated
+runs are bitwise identical.
 
 Inputs and tolerances as for the cell-list path (fcc spheres with 0.03 A of disorder, whose pair
 distances keep at least 0.02 A away from rcut = 8.8 A; e_F <= 1e-12 / 1e-5 for FP64 / MIXED).
@@ -43,7 +45,10 @@ def test_verlet_full_size_parity(scmd, prec):
     E, F = scmd.md_energy_forces(ctx)
     check_cluster(F, E[0], scmd.md_get_density(ctx), pos, prec, rcut=RC)
     _, _, tested = scmd.md_time_passes(ctx, 3)
-    assert 224 * 50000 < tested < 600 * 50000  # list entries: ~ (9.8 / 8.8)^3 x the pairs inside rcut
+    if prec == FP64:  # list entries: ~ (9.8 / 8.8)^3 x the pairs inside rcut
+        assert 224 * 50000 < tested < 600 * 50000
+    else:  # 16 pairs per listed quad: about as many as the cell list's octant pairs (~950 per atom)
+        assert 224 * 50000 < tested < 1200 * 50000
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
@@ -95,24 +100,29 @@ def test_verlet_berendsen_trajectory_and_observables(scmd, prec):
     assert hist[-1][0]["epot"] == pytest.approx(ref["epot"], rel=1e-12 if prec == FP64 else 1e-6)
 
 
-def test_verlet_lists_follow_large_motion(scmd):
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_verlet_lists_follow_large_motion(scmd, prec):
     """A hot liquid moves far beyond the skin within the run: the lists must be rebuilt (many
-    times) for the forces of the final state to match the oracle."""
+    times) for the forces of the final state to match the oracle. In a liquid, a few pairs lie within
+    the FP32 rounding of rcut, where MIXED may decide the cutoff differently from the oracle; each
+    such pair moves e_F by about (its pair force at rcut, ~2e-4 eV/A) / |F| ~ 1e-5, hence 5e-5."""
     pos = inputs.fcc_sphere(2000)
     vel = inputs.maxwell_boltzmann(pos, inputs.masses(2000), 3000.0, seed=12)
     th = scmd.thermostat(scmd.MD_LANGEVIN, 3000.0, 3000.0, gamma_per_ps=1.0, seed=5)
-    ctx = make(scmd, [2000], pos, vel, prec=FP64, rcut=RC, path=VERLET, graph_chunk=64)
+    ctx = make(scmd, [2000], pos, vel, prec=prec, rcut=RC, path=VERLET, graph_chunk=64)
     scmd.md_step(ctx, 1000, 2.0, th)
     p, _, _ = scmd.md_get_state(ctx)
     assert np.max(np.linalg.norm(p - pos, axis=1)) > 5.0  # far more than the 0.5 A rebuild trigger
     F = scmd.md_get_forces(ctx)  # the forces the integrator used at the final positions
     _, Fr, _, _ = oracle.energy_forces(p, oracle.params(rcut=RC))
-    assert rel_force_err(F, Fr) <= 1e-11
+    assert rel_force_err(F, Fr) <= (1e-11 if prec == FP64 else 5e-5)
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
-def test_verlet_checkpoint_resume_is_bitwise(scmd, prec):
-    """The resumed context builds its lists at step 60; the uninterrupted one built them elsewhere."""
+def test_verlet_checkpoint_resume(scmd, prec):
+    """The resumed context builds its lists at step 60; the uninterrupted one built them elsewhere.
+    FP64: bit for bit. MIXED: to rounding (the quads and their order depend on the build), while a
+    repeat of the same run is bit for bit."""
     pos = inputs.fcc_sphere(600)
     vel = inputs.maxwell_boltzmann(pos, inputs.masses(600), 1500.0, seed=6)
     th = scmd.thermostat(scmd.MD_LANGEVIN, 1500.0, 1500.0, gamma_per_ps=1.0, seed=7)
@@ -128,12 +138,19 @@ def test_verlet_checkpoint_resume_is_bitwise(scmd, prec):
     scmd.md_step(c, 40, 2.0, th)
     pc, vc, sc = scmd.md_get_state(c)
     assert sa == sc == 100
-    assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+    if prec == FP64:
+        assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+    else:
+        assert np.max(np.abs(pa - pc)) <= 1e-4
+        d = make(scmd, [600], pos, vel, **kw)
+        scmd.md_step(d, 100, 2.0, th)
+        pd, vd, _ = scmd.md_get_state(d)
+        assert np.array_equal(pa, pd) and np.array_equal(va, vd)
 
 
 def test_verlet_matches_cells_bitwise_free(scmd):
-    """Same input, both cutoff paths, MIXED: the same pairs, different coordinate frames (split
-    global coordinates against offsets from cell centres): agreement at the MIXED tolerance."""
+    """Same input, both cutoff paths, MIXED: the same pairs, different coordinate frames (offsets from
+    quad reference points against offsets from cell centres): agreement at the MIXED tolerance."""
     pos = lattice(3000, 34)
     a = make(scmd, [3000], pos, prec=MIXED, rcut=RC, path=VERLET)
     b = make(scmd, [3000], pos, prec=MIXED, rcut=RC, path=CELLS)
