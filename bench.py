@@ -49,8 +49,8 @@ UNIT = "atom-timesteps/s"
 FP32_LANES_PER_SM = 128
 FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n,m) = (9,6)
 # DRAM bytes (read + write) of one force-pass launch, from the ncu captures summarised in
-# profiles/k_force_ni2000_mixed.md and profiles/k_cell_passes_ni50000_mixed.md (cold caches).
-FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 234496, "ni50000": 1277184}
+# profiles/k_force_ni2000_mixed.md and profiles/k_q_passes_ni50000_mixed.md (cold caches).
+FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 234496, "ni50000": None}
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
 
 
@@ -512,7 +512,8 @@ def main():
                          "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": FORCE_DRAM_BYTES_PER_LAUNCH.get(args.config) if prec == "mixed" else None,
                          "kernel": {"cells": "k_cell_force (force pass, cell list)",
-                                    "neighbour lists": "k_v_force (force pass, neighbour lists)"}.get(
+                                    "neighbour lists": "k_q_force (force pass, quad lists)" if prec == "mixed"
+                                    else "k_v_force (force pass, neighbour lists)"}.get(
                                         path_name, "k_force (force pass)"),
                          "ms_per_launch": ms_f,
                          "density_pass_ms_per_launch": ms_d, "pairs_per_launch": alg_pairs,

@@ -65,13 +65,15 @@ typedef enum {
 } md_precision;
 
 typedef enum {
-    MD_PATH_AUTO = 0,     /* when rcut_A > 0 and the largest cluster has >= 8192 atoms
-                             (or the cutoff is shifted): cells in MIXED, neighbour lists
-                             in FP64; else all pairs                                     */
+    MD_PATH_AUTO = 0,     /* neighbour lists when rcut_A > 0 and the largest cluster has
+                             >= 8192 atoms (or the cutoff is shifted); else all pairs    */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
     MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
-    MD_PATH_VERLET = 3    /* per-atom neighbour lists (rcut_A + 1 A) built on the cell grid,
-                             rebuilt when an atom has moved 0.5 A; requires rcut_A > 0     */
+    MD_PATH_VERLET = 3    /* neighbour lists of rcut_A + 1 A built on the cell grid, rebuilt
+                             when an atom has moved 0.5 A; requires rcut_A > 0. FP64: per
+                             atom, forces independent of the rebuild times. MIXED: per quad
+                             of 4 nearby atoms, summed in list order, so a resumed run
+                             (md_set_state) agrees to rounding rather than bit for bit      */
 } md_path;
 
 /* The cell path (not in the paper, which sums every pair and leaves cutoffs to

@@ -680,10 +680,10 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     {
         int maxn = 0;
         for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
-        // automatic: with a cutoff and a large cluster, the cell list in MIXED (its passes read shared
-        // memory) and the neighbour lists in FP64 (whose pipe the tested pairs bound)
+        // automatic: with a cutoff and a large cluster (or a shifted cutoff), the neighbour lists (quad
+        // lists in MIXED, per-atom lists in FP64)
         const bool big = cfg->path == MD_PATH_AUTO && P.rcut > 0 && (maxn >= kAutoCellsMinAtoms || P.shift);
-        const bool verlet = cfg->path == MD_PATH_VERLET || (big && cfg->precision == MD_PREC_FP64);
+        const bool verlet = cfg->path == MD_PATH_VERLET || big;
         const bool cells = verlet || cfg->path == MD_PATH_CELLS || big;
         c->path = verlet ? 2 : (cells ? 1 : 0);
         if (c->path == 2 && c->ntot >= (1 << 26)) {

@@ -166,7 +166,7 @@ struct Dev {
     float4* q_ref;       // [nqmax] reference point of each quad relative to the origin (a multiple of 2^-12 A)
     float4* q_box;       // [nqmax][2] bounding box (lo, hi) of its atoms at the rebuild, relative to the origin
     int32_t* q_cell;     // [nqmax] cell of each quad
-    int32_t* q_list;     // [nqmax][kQMax] quads whose boxes lie within rcut + skin of this one's
+    int32_t* q_list;     // [nqmax][kQMax] quads with an atom within rcut + skin of one of this one's
     int32_t* q_count;    // [nqmax]
 };
 

@@ -3,8 +3,8 @@
 // Per-atom lists make every tested pair a gather of a random neighbour, and in FP32 those gathers,
 // not the arithmetic, bound the passes. Here the unit is a quad: 4 consecutive slots of one cell,
 // with a cell's atoms in Morton order (sub-cells of side h/8), so a quad is a compact group. Each
-// quad keeps the list of quads whose bounding boxes (at the last rebuild) lie within rcut + skin of
-// its own. A pass runs one warp per quad: lane l holds atom l % 4 of the (l / 4)-th of 8 listed
+// quad keeps the list of quads with an atom within rcut + skin of one of its own at the last
+// rebuild. A pass runs one warp per quad: lane l holds atom l % 4 of the (l / 4)-th of 8 listed
 // quads and tests it against the 4 atoms of the warp's own quad, so one warp-wide load brings 32
 // neighbours for 128 pairs. Per step:
 //   k_q_pos    : every slot's offset from its quad's reference point, and the largest squared
@@ -14,7 +14,8 @@
 //     k_q_scan   : the first slot of every cell (cells padded to whole quads), and the quad count;
 //     k_q_order  : one CTA per cell: its atoms in Morton order into slots; per quad the reference
 //                  point, the bounding box and the offsets;
-//     k_q_list   : one warp per quad: the quads of the 27 cells around it whose boxes are in reach;
+//     k_q_list   : one warp per quad: the quads of the 27 cells around it with an atom in reach of
+//                  one of its atoms (boxes tested first);
 //   k_q_density, k_q_force : one warp per quad; per CTA of 8 quads, one warp then finishes the 32
 //                atoms (the FP64 per-atom work on full warps).
 // Coordinates: a quad's reference point C is its atoms' centroid rounded to a multiple of 2^-12 A,
@@ -190,8 +191,9 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
     }
 }
 
-// One warp per quad: the quads of the 27 cells around its cell (fixed order) whose bounding boxes
-// come closer than rcut + skin to its own, appended in that order.
+// One warp per quad: the quads of the 27 cells around its cell (fixed order) with some atom closer
+// than rcut + skin to one of its atoms at the rebuild, appended in that order. The bounding boxes
+// screen the candidates; the 16 atom pairs decide.
 __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int k_local) {
     pdl_launch_dependents();
     pdl_wait();
@@ -204,6 +206,11 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
     const int loc = c - g.off, cx = loc % g.G, cy = (loc / g.G) % g.G, cz = loc / (g.G * g.G);
     const float4 lo = d.q_box[2 * Q], hi = d.q_box[2 * Q + 1];
     const float rl2 = (float)d.vrl2;
+    const float4* vp = reinterpret_cast<const float4*>(d.vhi);
+    float4 oi[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) oi[a] = vp[4 * Q + a];
+    const float4 CI = d.q_ref[Q];
     int* out = d.q_list + (size_t)Q * kQMax;
     int n = 0;
     bool overflow = false;
@@ -220,7 +227,20 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
                 const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
                 const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
                 const float ez = fmaxf(0.f, fmaxf(l2.z - hi.z, lo.z - h2.z));
-                in = ex * ex + ey * ey + ez * ez < rl2;
+                if (ex * ex + ey * ey + ez * ez < rl2) {  // boxes in reach: is some atom pair?
+                    const float4 CJ = d.q_ref[J];
+                    const float Dx = CI.x - CJ.x, Dy = CI.y - CJ.y, Dz = CI.z - CJ.z;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 pj = vp[4 * J + u];
+                        const float px = pj.x - Dx, py = pj.y - Dy, pz = pj.z - Dz;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
+                            in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+                        }
+                    }
+                }
             }
             const unsigned b = __ballot_sync(0xffffffffu, in);
             const int pos = n + __popc(b & ((1u << lane) - 1u));
@@ -282,21 +302,26 @@ __global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs) {
     const int mexp = d.pot.m;
     float tacc[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < n; k0 += 8) {
-        const float4 p = q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI);
+    for (int k0 = 0; k0 < n; k0 += 16) {  // two listed quads per lane and iteration: two loads in flight
+        const float4 pp[2] = {q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI),
+                              q_neighbour(d, vp, L, k0 + 8 + (lane >> 2), n, q, CI)};
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool in = r2 < rc2 && r2 > 0.f;
-            r2 = in ? r2 : big<float>();
-            if (SHIFT) nin[a] += in;
-            if (SPECIAL) {
-                const float inv = inv_r2(r2);
-                tacc[a] = fmaf(inv * inv, inv, tacc[a]);
-            } else {
-                const float ir = inv_r(r2);
-                tacc[a] += rpow(ir * ir, ir, mexp);
+        for (int h = 0; h < 2; ++h) {
+            const float4 p = pp[h];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool in = r2 < rc2 && r2 > 0.f;
+                r2 = in ? r2 : big<float>();
+                if (SHIFT) nin[a] += in;
+                if (SPECIAL) {
+                    const float inv = inv_r2(r2);
+                    tacc[a] = fmaf(inv * inv, inv, tacc[a]);
+                } else {
+                    const float ir = inv_r(r2);
+                    tacc[a] += rpow(ir * ir, ir, mexp);
+                }
             }
         }
     }
@@ -352,32 +377,37 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
     float fx[4] = {0.f, 0.f, 0.f, 0.f}, fy[4] = {0.f, 0.f, 0.f, 0.f}, fz[4] = {0.f, 0.f, 0.f, 0.f};
     float se[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < n; k0 += 8) {
-        const float4 p = q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI);
+    for (int k0 = 0; k0 < n; k0 += 16) {  // two listed quads per lane and iteration: two loads in flight
+        const float4 pp[2] = {q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI),
+                              q_neighbour(d, vp, L, k0 + 8 + (lane >> 2), n, q, CI)};
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool in = r2 < rc2 && r2 > 0.f;
-            r2 = in ? r2 : big<float>();
-            const float ir = inv_r(r2);
-            const float inv = ir * ir;
-            float coef, rn;
-            if (SPECIAL) {
-                const float inv2 = inv * inv, inv4 = inv2 * inv2;
-                coef = inv4 * fmaf(A, inv * ir, -(oi[a].w + p.w));
-                rn = inv4 * ir;
-            } else {
-                rn = rpow(inv, ir, nexp);
-                const float rm = rpow(inv, ir, mexp);
-                coef = inv * (A * rn - (oi[a].w + p.w) * rm);
-            }
-            fx[a] = fmaf(coef, dx, fx[a]);
-            fy[a] = fmaf(coef, dy, fy[a]);
-            fz[a] = fmaf(coef, dz, fz[a]);
-            if (ENERGY) {
-                se[a] += rn;
-                nin[a] += in;
+        for (int h = 0; h < 2; ++h) {
+            const float4 p = pp[h];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool in = r2 < rc2 && r2 > 0.f;
+                r2 = in ? r2 : big<float>();
+                const float ir = inv_r(r2);
+                const float inv = ir * ir;
+                float coef, rn;
+                if (SPECIAL) {
+                    const float inv2 = inv * inv, inv4 = inv2 * inv2;
+                    coef = inv4 * fmaf(A, inv * ir, -(oi[a].w + p.w));
+                    rn = inv4 * ir;
+                } else {
+                    rn = rpow(inv, ir, nexp);
+                    const float rm = rpow(inv, ir, mexp);
+                    coef = inv * (A * rn - (oi[a].w + p.w) * rm);
+                }
+                fx[a] = fmaf(coef, dx, fx[a]);
+                fy[a] = fmaf(coef, dy, fy[a]);
+                fz[a] = fmaf(coef, dz, fz[a]);
+                if (ENERGY) {
+                    se[a] += rn;
+                    nin[a] += in;
+                }
             }
         }
     }

@@ -45,13 +45,13 @@ def test_shifted_energy_forces_density(scmd, path, prec, n):
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_shifted_batch_and_automatic_path(scmd, prec):
     """Unevenly sized clusters (a lone atom, a dimer beyond and one inside rcut, Ni13, Ni300) on the
-    automatic path, which takes the cell list (MIXED) or the lists (FP64) for any size."""
+    automatic path, which takes the neighbour lists for any size when the cutoff is shifted."""
     parts = [np.zeros((1, 3)), np.array([[0.0, 0.0, 0.0], [9.0, 0.0, 0.0]]),
              np.array([[0.0, 0.0, 0.0], [8.0, 0.5, 0.0]]), inputs.fcc_sphere(13), lattice(300, 42)]
     sizes = [len(p) for p in parts]
     pos = np.concatenate([p + 60.0 * b for b, p in enumerate(parts)])
     ctx = make_shift(scmd, sizes, pos, prec=prec)
-    assert scmd.md_get_path(ctx) == (CELLS if prec == MIXED else VERLET)
+    assert scmd.md_get_path(ctx) == VERLET
     E, F = scmd.md_energy_forces(ctx)
     rho = scmd.md_get_density(ctx)
     off = np.concatenate([[0], np.cumsum(sizes)])
