@@ -10,8 +10,8 @@ default --steps 400 covers the whole 2e5-step cooling schedule. L2 is flushed (a
 write) before every timed iteration and that flush is outside the timed events.
 
 Other configs (--config): ni6000, ni20000 (all pairs, MIXED), ni50000 (rcut = 8.8 A on the
-cell list, MIXED), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one context), batched512 (512
-clusters of 55..2000 atoms).
+neighbour lists, MIXED: lists of atom quads), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one
+context), batched512 (512 clusters of 55..2000 atoms).
 
 value  : atom-timesteps/s over all ranks (sum of atoms x MD steps / max rank time).
 e2e    : the same metric through the C ABI with host buffers every iteration
@@ -79,7 +79,7 @@ def workload(name: str, rank: int):
         vel = inputs.maxwell_boltzmann(pos, m, 2000.0, seed=6 + seed_off, dof="3N")
         return dict(sizes=[50000], pos=pos, vel=vel, mass=m, prec="mixed", dt=2.0, melt_steps=2000, melt_T=2000.0,
                     schedule=(2000.0, 300.0, 200000), gamma=1.0, seed=6 + seed_off, rcut=8.8,
-                    desc="Ni~50000 FCC sphere, rcut 8.8 A (2.5 a) on the cell list, Langevin cooling "
+                    desc="Ni~50000 FCC sphere, rcut 8.8 A (2.5 a) on neighbour lists, Langevin cooling "
                          "2000->300 K over 2e5 steps dt=2 fs")
     if name == "ni147":
         pos = inputs.mackay_icosahedron(3, 2.49)
@@ -360,13 +360,13 @@ def main():
 
     # pass timings with CUDA events on the library's stream (same state, same launch shapes)
     ms_d, ms_f, pairs = scmd.md_time_passes(ctx, 50)
-    if cells:  # pairs tested at the final state (octants of the cell list, or list entries)
+    if cells:  # pairs tested at the final state (octants of the cell list, or the listed pairs)
         pairs_per_eval = pairs
     pair_rate = pairs_per_eval * md_steps_total * world / t_max
     peak_clock = (clocks or {}).get("sm_max_mhz", 2070.0)
     peak_ops = 152 * FP32_LANES_PER_SM * peak_clock * 1e6
-    # algorithmic work of a launch: every ordered pair for all pairs; the pairs closer than rcut for the
-    # cell list (the candidates it tests are reported beside)
+    # algorithmic work of a launch: every ordered pair for all pairs; the pairs closer than rcut with a
+    # cutoff (the candidates the cell or neighbour lists test are reported beside)
     useful_pairs = None
     if cells:
         from scipy.spatial import cKDTree

@@ -203,7 +203,9 @@ md_status md_clear_history(md_ctx* ctx);
 /* Checkpoint: copy positions, velocities (host [Ntot][3]) and the step counter
  * out of, or into, the context. md_set_state recomputes the forces. Because the
  * Langevin noise is a pure function of (seed, cluster, atom, step), resuming
- * from a checkpoint reproduces an uninterrupted run bit for bit. */
+ * from a checkpoint reproduces an uninterrupted run bit for bit on every path
+ * but the MIXED neighbour lists, whose sums follow the list order of the last
+ * rebuild; there it agrees to rounding (MD_PATH_CELLS is bitwise in MIXED). */
 md_status md_get_state(md_ctx* ctx, double* pos_A, double* vel_A_per_fs, int64_t* step);
 md_status md_set_state(md_ctx* ctx, const double* pos_A, const double* vel_A_per_fs, int64_t step);
 

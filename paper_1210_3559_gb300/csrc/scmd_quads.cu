@@ -258,16 +258,15 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
 }
 
 // ---------------------------------------------------------------- passes
-// The listed atom of this lane at list position k, as an offset from the warp's quad reference
-// point (or far away past the end of the list).
-__device__ __forceinline__ float4 q_neighbour(const Dev& d, const float4* vp, const int* L, int k, int n, int q,
-                                              const float4& CI) {
-    if (k >= n) return make_float4(kFar, kFar, kFar, 0.f);
-    const int J = L[k];
+// Atom q of listed quad J (J < 0: past the end of the list) as an offset from the warp's quad
+// reference point, or far away.
+__device__ __forceinline__ float4 q_neighbour(const Dev& d, const float4* vp, int J, int q, const float4& CI) {
+    if (J < 0) return make_float4(kFar, kFar, kFar, 0.f);
     const float4 pj = vp[4 * J + q];
     const float4 CJ = d.q_ref[J];
     return make_float4(pj.x - (CI.x - CJ.x), pj.y - (CI.y - CJ.y), pj.z - (CI.z - CJ.z), pj.w);
 }
+__device__ __forceinline__ int q_entry(const int* L, int k, int n) { return k < n ? L[k] : -1; }
 
 // The 4 atoms of this warp's quad (far away for a warp past the last quad).
 __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int nq, float4 oi[4], float4& CI) {
@@ -302,9 +301,13 @@ __global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs) {
     const int mexp = d.pot.m;
     float tacc[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < n; k0 += 16) {  // two listed quads per lane and iteration: two loads in flight
-        const float4 pp[2] = {q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI),
-                              q_neighbour(d, vp, L, k0 + 8 + (lane >> 2), n, q, CI)};
+    // two listed quads per lane and iteration; the list entries of the next iteration are loaded
+    // one iteration ahead
+    int J0 = q_entry(L, lane >> 2, n), J1 = q_entry(L, 8 + (lane >> 2), n);
+    for (int k0 = 0; k0 < n; k0 += 16) {
+        const float4 pp[2] = {q_neighbour(d, vp, J0, q, CI), q_neighbour(d, vp, J1, q, CI)};
+        J0 = q_entry(L, k0 + 16 + (lane >> 2), n);
+        J1 = q_entry(L, k0 + 24 + (lane >> 2), n);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 p = pp[h];
@@ -377,9 +380,13 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
     float fx[4] = {0.f, 0.f, 0.f, 0.f}, fy[4] = {0.f, 0.f, 0.f, 0.f}, fz[4] = {0.f, 0.f, 0.f, 0.f};
     float se[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < n; k0 += 16) {  // two listed quads per lane and iteration: two loads in flight
-        const float4 pp[2] = {q_neighbour(d, vp, L, k0 + (lane >> 2), n, q, CI),
-                              q_neighbour(d, vp, L, k0 + 8 + (lane >> 2), n, q, CI)};
+    // two listed quads per lane and iteration; the list entries of the next iteration are loaded
+    // one iteration ahead
+    int J0 = q_entry(L, lane >> 2, n), J1 = q_entry(L, 8 + (lane >> 2), n);
+    for (int k0 = 0; k0 < n; k0 += 16) {
+        const float4 pp[2] = {q_neighbour(d, vp, J0, q, CI), q_neighbour(d, vp, J1, q, CI)};
+        J0 = q_entry(L, k0 + 16 + (lane >> 2), n);
+        J1 = q_entry(L, k0 + 24 + (lane >> 2), n);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 p = pp[h];
