@@ -243,17 +243,21 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
 /*
  * Mean device time (ms) of one launch of the density pass and of the force
  * pass, timed alone with CUDA events on the context's stream over reps
- * launches after warm-up. Pair-evaluation counts per launch are returned in
- * *pairs (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for
- * the cell path, every atom times the atoms of the 5 x 5 x 5 cell octants around
- * its own, self included, as binned at the current positions). Any output may be NULL.
+ * launches after warm-up (with the neighbour lists in FP64, each pass includes
+ * its gather kernel). Pair-evaluation counts per launch are returned in *pairs
+ * (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for the cell
+ * path, every atom times the atoms of the 5 x 5 x 5 cell octants around its own,
+ * self included, as binned at the current positions; for the MIXED lists, 16
+ * per listed quad; for the FP64 lists, twice the half-list entries). Any output
+ * may be NULL.
  */
 md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* ms_force,
                          double* pairs);
 
-/* Number of GPU kernels issued per md_step step (all pairs: 2, cells: 5, plus
- * one Berendsen kernel, two with cells, and the observable kernels of recorded
- * steps) and per graph replay overhead (launches per chunk), for launch accounting. */
+/* Number of GPU kernels issued per md_step step (all pairs: 2, cells: 5,
+ * neighbour lists: 9 in MIXED, 12 in FP64, plus one Berendsen kernel, two with
+ * cells or lists, and the observable kernels of recorded steps) and per graph
+ * replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);
 
 /* The pair path the context runs (MD_PATH_ALLPAIRS, MD_PATH_CELLS or MD_PATH_VERLET;

@@ -92,7 +92,10 @@ struct md_ctx {
     bool msd_ref = false;
     // neighbour-list path
     int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vsub = nullptr, *d_vorder = nullptr, *d_vslotof = nullptr;
-    int32_t* d_vslot = nullptr;
+    int32_t *d_vslot = nullptr, *d_vrcount = nullptr;
+    uint64_t* d_vrev = nullptr;
+    double *d_hbuf = nullptr, *d_rho_half = nullptr;
+    double4 *d_fbuf = nullptr, *d_fhalf = nullptr;
     void *d_vhi = nullptr, *d_vposg = nullptr;
     int32_t *d_q_n = nullptr, *d_cell_base = nullptr, *d_q_cell = nullptr, *d_q_list = nullptr, *d_q_count = nullptr;
     float4 *d_q_ref = nullptr, *d_q_box = nullptr;
@@ -196,6 +199,12 @@ void fill_dev(md_ctx* c) {
     d.vlist = c->d_vlist;
     d.vcount = c->d_vcount;
     d.vsub = c->d_vsub;
+    d.vrcount = c->d_vrcount;
+    d.vrev = c->d_vrev;
+    d.hbuf = c->d_hbuf;
+    d.fbuf = c->d_fbuf;
+    d.rho_half = c->d_rho_half;
+    d.fhalf = c->d_fhalf;
     d.vorder = c->d_vorder;
     d.vslotof = c->d_vslotof;
     d.vslot = c->d_vslot;
@@ -454,6 +463,7 @@ void free_all(md_ctx* c) {
                     c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
                     c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi,
                     c->d_q_n, c->d_cell_base, c->d_q_cell, c->d_q_list, c->d_q_count, c->d_q_ref, c->d_q_box,
+                    c->d_vrcount, c->d_vrev, c->d_hbuf, c->d_fbuf, c->d_rho_half, c->d_fhalf,
                     c->d_vposg, c->d_vxref, c->d_vdmax,
                     c->sb.com, c->sb.core, c->sb.ncore, c->sb.hist, c->sb.ref, c->sb.ref_com, c->sb.sel, c->sb.msd,
                     c->sb.nsel, c->sb.nb, c->sb.nnb, c->sb.cls, c->sb.counts, c->sb.capped};
@@ -686,9 +696,12 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         const bool verlet = cfg->path == MD_PATH_VERLET || big;
         const bool cells = verlet || cfg->path == MD_PATH_CELLS || big;
         c->path = verlet ? 2 : (cells ? 1 : 0);
-        if (c->path == 2 && c->ntot >= (1 << 26)) {
+        // FP64 lists address a pair's place in 32 bits: nslot * kVMax < 2^32
+        const int64_t vmax_atoms = cfg->precision == MD_PREC_FP64 ? (1 << 23) : (1 << 26);
+        if (c->path == 2 && c->ntot >= vmax_atoms) {
             delete c;
-            return fail(nullptr, MD_ERR_INVALID, "the neighbour-list path takes at most 2^26 atoms");
+            return fail(nullptr, MD_ERR_INVALID, "the neighbour-list path takes fewer than %lld atoms in this precision",
+                        (long long)vmax_atoms);
         }
         // the neighbour lists hold the pairs within rcut + skin, so their cells are sized by that
         if (cells && !make_grids(c, pos, mass, c->path == 2 ? P.rcut + kSkin : P.rcut)) {
@@ -821,6 +834,13 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
             CKC(cudaMalloc(&c->d_vcount, sizeof(int32_t) * ns));
             CKC(cudaMalloc(&c->d_vsub, sizeof(int32_t) * kVLanes * ns));
             CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
+            CKC(cudaMalloc(&c->d_vrcount, sizeof(int32_t) * ns));
+            CKC(cudaMalloc(&c->d_vrev, sizeof(uint64_t) * kVMax * ns));
+            CKC(cudaMalloc(&c->d_hbuf, sizeof(double) * kVMax * ns));
+            CKC(cudaMalloc(&c->d_fbuf, sizeof(double4) * kVMax * ns));
+            CKC(cudaMalloc(&c->d_rho_half, sizeof(double) * ns));
+            CKC(cudaMalloc(&c->d_fhalf, sizeof(double4) * ns));
+            CKC(cudaMemset(c->d_vrcount, 0, sizeof(int32_t) * ns));
             CKC(cudaMemset(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns));
             CKC(cudaMemset(c->d_vcount, 0, sizeof(int32_t) * ns));
             CKC(cudaMemset(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns));
@@ -1172,12 +1192,12 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
         double p = 0;
         for (int q = 0; q < nq && q < c->nqmax; ++q) p += 16.0 * cnt[q];
         *pairs = p;
-    } else if (pairs && vl) {  // list entries (pairs tested per pass)
+    } else if (pairs && vl) {  // half-list entries: each an unordered pair, i.e. two ordered pairs
         std::vector<int32_t> cnt(c->ntot);
         CK(c, cudaMemcpyAsync(cnt.data(), c->d_vcount, sizeof(int32_t) * c->ntot, cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
         double p = 0;
-        for (int32_t n : cnt) p += n;
+        for (int32_t n : cnt) p += 2.0 * n;
         *pairs = p;
     } else if (pairs && !cells) {
         double p = 0;
@@ -1331,7 +1351,9 @@ md_status md_get_path(const md_ctx* c, int32_t* path) {
 
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
-    if (per_step) *per_step = c->path == 2 ? 9 : (c->path == 1 ? 5 : 2);
+    // lists: positions, cell build (3), list build (MIXED scan, order, list; FP64 build, sort, reverse sort,
+    // commit), passes (MIXED 2; FP64 2 + 2 gathers)
+    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 9 : 12) : (c->path == 1 ? 5 : 2);
     if (per_chunk) *per_chunk = 3;
     return MD_OK;
 }

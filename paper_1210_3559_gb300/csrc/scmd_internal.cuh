@@ -150,6 +150,12 @@ struct Dev {
     int32_t* vlist;      // FP64: [nslot][kVMax] slots of the neighbours, by (atom mod kVLanes, atom)
     int32_t* vcount;     // FP64: [nslot]
     int32_t* vsub;       // FP64: [nslot][kVLanes] end of each sub-list (the entries j with j mod kVLanes = t)
+    int32_t* vrcount;    // FP64: [nslot] entries of the reverse list (lower atoms that list this one)
+    uint64_t* vrev;      // FP64: [nslot][kVMax] reverse list: (lower atom << 32 | its entry's place), by atom
+    double* hbuf;        // FP64: [nslot][kVMax] density term of each listed pair, for the partner
+    double4* fbuf;       // FP64: [nslot][kVMax] force on the listing atom and pair energy term of each pair
+    double* rho_half;    // FP64: [nslot] the listing atom's own density sum
+    double4* fhalf;      // FP64: [nslot] the listing atom's own force and pair-energy sums
     int32_t* vorder;     // [nslot] atom of each slot (MIXED: -1 for the empty slots that pad cells to quads)
     int32_t* vslotof;    // [npad] slot of each atom
     int32_t* vslot;      // FP64: [1] slot counter of a rebuild

@@ -1,10 +1,11 @@
 // scmd_verlet.cu -- the neighbour-list path of the two pair passes (strict cutoff r < rcut), FP64.
 // (MIXED lists are lists of atom quads: scmd_quads.cu.)
 //
-// Each atom keeps the list of the atoms that were closer than rcut + skin when the lists were last
-// built. As long as no atom has moved more than skin / 2 since, every pair closer than rcut is in
-// the lists, so each pass tests only those entries (about (rcut + skin)^3 / rcut^3 of the pairs that
-// count, against ~4x for the octants of the cell-list path). Per MD step:
+// Each atom keeps the list of the atoms with a higher index that were closer than rcut + skin when
+// the lists were last built (a half list: every pair once, Newton's third law gives the partner's
+// share). As long as no atom has moved more than skin / 2 since, every pair closer than rcut is in
+// the lists, so each pass computes only those entries (about (rcut + skin)^3 / rcut^3 of the pairs
+// that count, halved, against ~4x for the octants of the cell-list path). Per MD step:
 //   k_v_pos    : every atom's pass coordinates, by list slot, and the largest squared displacement
 //                since the last rebuild;
 //   rebuild, when that displacement exceeds the trigger (the kernels exit at once otherwise):
@@ -13,23 +14,28 @@
 //                  cell-list passes; every atom closer than rcut + skin is appended to the home
 //                  atom's list. The home cell's atoms take consecutive slots (cell order);
 //     k_v_sort   : one warp per list, a bitonic sort by (j mod kVLanes, j), the atoms turned into
-//                  their slots, and the ends of the kVLanes sub-lists;
+//                  their slots, the ends of the kVLanes sub-lists, and each entry appended to the
+//                  partner's reverse list;
+//     k_v_rsort  : one warp per slot, its reverse list sorted by the lower atom;
 //     k_v_commit : the pass coordinates in the new slot order and the reference positions;
-//   k_v_density, k_v_force : kVLanes threads per atom, thread t over sub-list t.
+//   k_v_density, k_v_force : kVLanes threads per atom, thread t over sub-list t; each pair term goes
+//                  into the atom's own sum and into a buffer at the entry's place;
+//   k_v_dgather, k_v_fgather : one thread per atom, its own sum plus (or, for forces, minus) the
+//                  buffered terms of its reverse list; then rho and g, or the integrator step.
 // The passes read the positions themselves (by slot).
 // Results do not depend on when the lists were built: what a thread sums is the pairs inside rcut
 // whose j is in its residue class, in ascending j (a pair outside rcut is masked to r2 = inf and
-// adds an exact zero); its pass-precision partial sums are folded every kSpanV pairs inside rcut;
-// and the kVLanes partials are added in a fixed tree. Resuming from a checkpoint (which rebuilds
-// the lists) therefore reproduces an uninterrupted run bit for bit, as on the other paths.
+// adds an exact zero); its partial sums are folded every kSpanV pairs inside rcut; the kVLanes
+// partials are added in a fixed tree; and the reverse list is summed in ascending order of the
+// lower atom. Resuming from a checkpoint (which rebuilds the lists) therefore reproduces an
+// uninterrupted run bit for bit, as on the other paths.
 #include "scmd_cells.cuh"
 
 namespace scmd {
 
 constexpr int kSpanV = 64;  // pairs inside rcut a thread sums in the pass precision before a fold
 constexpr int kVThreads = 256;
-template <int PREC> struct BuildChunk;  // staged atoms per chunk of the list build (48 KB static limit)
-template <> struct BuildChunk<0> { static constexpr int TJ = 768; };
+constexpr int kBuildTJ = 1536;  // staged atoms per chunk of the list build (float4 + index: 30 KB)
 static_assert(kVLog >= 1 && kVLog <= 4, "an atom's threads must sit in one warp");
 
 // Pass coordinates of atom i at slot s.
@@ -65,12 +71,14 @@ template <int PREC> __global__ void k_v_pos(const Dev d, int k_local) {
 // ---------------------------------------------------------------- rebuild
 // One CTA per home cell (interior first), one warp per home octant; every staged atom closer than
 // rcut + skin goes into the home atom's list. The home cell's atoms take consecutive list slots.
+// The test runs in FP32 on the cell-centre offsets (errors ~1e-6 A); the rebuild trigger keeps a
+// 1e-3 A margin, so a pair that can come within rcut before the next rebuild is always listed.
 template <int PREC>
 __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int cond, int k_local) {
     using V4 = typename Tr<PREC>::V4;
-    using R = typename Tr<PREC>::R;
-    constexpr int TJ = BuildChunk<PREC>::TJ;
-    __shared__ V4 spos[TJ];
+    using R = float;
+    constexpr int TJ = kBuildTJ;
+    __shared__ float4 spos[TJ];
     __shared__ int sidx[TJ];
     __shared__ int s_src[kBoxN], s_cnt[kBoxN], s_pref[kBoxN + 1];
     __shared__ int2 s_runs[8][25];
@@ -93,15 +101,17 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
         const int a = d.cell_atoms[(size_t)c * kCellCap + k];
         d.vorder[base + k] = a;
         d.vslotof[a] = base + k;
+        d.vrcount[base + k] = 0;
     }
-    const R rl2 = (R)d.vrl2, h = (R)g.h;
+    const R rl2 = (R)d.vrl2;
     const int nblk = oct_blocks(d, c), w = threadIdx.x >> 5;
     bool overflow = false;
     for (int blk = 0; blk < nblk; ++blk) {
         const OctWarp q = oct_warp(d, c, blk * 32);
         const int k_home = q.s0 + blk * 32 + q.is;  // the home atom's place in its cell
-        const V4 pi = q.nb > 0 ? cp[(size_t)c * kCellCap + k_home] : V4{};
-        const int self = s_pref[q.home_t] + blk * 32 + q.is;
+        const V4 pd = q.nb > 0 ? cp[(size_t)c * kCellCap + k_home] : V4{};
+        const float4 pi = make_float4((float)pd.x, (float)pd.y, (float)pd.z, 0.f);
+        const int me = q.nb > 0 ? d.cell_atoms[(size_t)c * kCellCap + k_home] : 0;
         int* list = d.vlist + (size_t)(base + k_home) * kVMax;
         for (int e0 = 0; e0 < M; e0 += TJ) {
             const int ne = min(TJ, M - e0);
@@ -109,30 +119,26 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_v_build(const Dev d, int co
             for (int t = threadIdx.x; t < kBoxN; t += blockDim.x) {  // stage atoms, shifted to the home cell
                 const int a = max(s_pref[t], e0), b = min(s_pref[t + 1], e0 + ne);
                 const int dx = (t % kBox) / 2 - 1, dy = ((t / kBox) % kBox) / 2 - 1, dz = (t / (kBox * kBox)) / 2 - 1;
-                const R sx = (R)dx * h, sy = (R)dy * h, sz = (R)dz * h;
+                const double sx = dx * g.h, sy = dy * g.h, sz = dz * g.h;
                 for (int e = a; e < b; ++e) {
                     const int src = s_src[t] + (e - s_pref[t]);
-                    V4 p = cp[src];
-                    p.x += sx;
-                    p.y += sy;
-                    p.z += sz;
-                    spos[e - e0] = p;
+                    const V4 p = cp[src];
+                    spos[e - e0] = make_float4((float)(p.x + sx), (float)(p.y + sy), (float)(p.z + sz), 0.f);
                     sidx[e - e0] = d.cell_atoms[src];
                 }
             }
             __syncthreads();
             oct_runs(s_pref, q.o, e0, ne, s_runs[w]);
             if (!q.act) continue;
-            const int selfl = self - e0;
             for (int run = 0; run < 25; ++run) {
                 const int2 ab = s_runs[w][run];
                 const int L = ab.y - ab.x, per = (L + q.J - 1) / q.J;
                 const int lo = ab.x + min(L, q.jg * per), hi = ab.x + min(L, q.jg * per + per);
                 for (int e = lo; e < hi; ++e) {
-                    const V4 p = spos[e];
+                    const float4 p = spos[e];
                     const R dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
-                    const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    if (r2 < rl2 && e != selfl) {
+                    const R r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (r2 < rl2 && sidx[e] > me) {  // half list: each pair once, at its lower atom
                         const int slot = atomicAdd(&s_len[k_home], 1);
                         if (slot < kVMax)
                             list[slot] = sidx[e];
@@ -183,10 +189,18 @@ __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int
             }
             __syncwarp();
         }
+    const uint64_t ai = (uint64_t)(uint32_t)d.vorder[s];
     for (int e = lane; e < n; e += 32) {
         const uint32_t key = b[e];
         const uint32_t j = ((key & ((1u << HB) - 1)) << kVLog) | (key >> HB);
-        row[e] = d.vslotof[j];
+        const int sj = d.vslotof[j];
+        row[e] = sj;
+        // the partner's reverse list: (this atom, this entry's place), sorted by atom in k_v_rsort
+        const int r = atomicAdd(d.vrcount + sj, 1);
+        if (r < kVMax)
+            d.vrev[(size_t)sj * kVMax + r] = (ai << 32) | (uint32_t)((size_t)s * kVMax + e);
+        else
+            atomicOr(d.status, 4);
     }
     if (lane < kVLanes) {  // end of class `lane`: the first key of a higher class
         const uint32_t bound = (uint32_t)(lane + 1) << HB;
@@ -198,6 +212,40 @@ __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int
         }
         d.vsub[(size_t)s * kVLanes + lane] = lo;
     }
+}
+
+// One warp per slot: its reverse list (the entries of lower atoms that name it) sorted by atom, a
+// bitonic sort of (atom << 32 | entry place).
+__global__ void __launch_bounds__(kVThreads) k_v_rsort(const Dev d, int cond, int k_local) {
+    __shared__ uint64_t buf[kVThreads / 32][kVMax];
+    pdl_launch_dependents();
+    pdl_wait();
+    if (cond && !vlist_rebuild_due(d, k_local)) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (kVThreads / 32) + w;
+    if (s >= d.nslot) return;
+    const int n = min(d.vrcount[s], kVMax);
+    int P = 32;
+    while (P < n) P <<= 1;
+    uint64_t* b = buf[w];
+    uint64_t* rv = d.vrev + (size_t)s * kVMax;
+    for (int e = lane; e < P; e += 32) b[e] = e < n ? rv[e] : ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int e = lane; e < P; e += 32) {
+                const int f = e ^ j;
+                if (f > e) {
+                    const uint64_t x = b[e], y = b[f];
+                    if ((x > y) == ((e & k) == 0)) {
+                        b[e] = y;
+                        b[f] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    for (int e = lane; e < n; e += 32) rv[e] = b[e];
 }
 
 // Pass coordinates in the new slot order and the positions the next displacements are measured from.
@@ -216,16 +264,6 @@ template <int PREC> __global__ void k_v_commit(const Dev d, int cond, int k_loca
 }
 
 // ---------------------------------------------------------------- passes
-// Separation of the atoms at slots a (coordinates pa) and q.
-template <int PREC>
-__device__ __forceinline__ void v_sep(const typename Tr<PREC>::V4& pa, const typename Tr<PREC>::V4& pq,
-                                      typename Tr<PREC>::R& dx, typename Tr<PREC>::R& dy,
-                                      typename Tr<PREC>::R& dz) {
-    dx = pa.x - pq.x;
-    dy = pa.y - pq.y;
-    dz = pa.z - pq.z;
-}
-
 // The sum of a double over the kVLanes threads of an atom, in a fixed tree (every thread gets it).
 __device__ __forceinline__ double v_group_sum(double v) {
     const unsigned mask = ((1u << kVLanes) - 1u) << (threadIdx.x & 31 & ~(kVLanes - 1));
@@ -234,146 +272,163 @@ __device__ __forceinline__ double v_group_sum(double v) {
     return v;
 }
 
-template <int PREC, int SPECIAL>
-__global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d, int obs) {
-    using R = typename Tr<PREC>::R;
-    using V4 = typename Tr<PREC>::V4;
+// Half lists: atom i lists its partners j > i only. A pass computes each pair once; the term goes
+// into i's own sum (registers, by residue class of j in ascending j as before) and is written at the
+// entry's place for j. The gather kernels then add, for every atom, the terms of its reverse list
+// in ascending order of the lower atom. Both orders are fixed by the positions alone, so the passes
+// still do not depend on when the lists were built.
+template <int SPECIAL>
+__global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d) {
     pdl_launch_dependents();
     pdl_wait();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = gt >> kVLog, t = gt & (kVLanes - 1);
     if (s >= d.nslot) return;  // whole atoms leave together
-    const V4* vp = reinterpret_cast<const V4*>(d.vhi);
-    const V4 pi = vp[s];
+    const double4* vp = reinterpret_cast<const double4*>(d.vhi);
+    const double4 pi = vp[s];
     const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
-    const R rc2 = (R)d.pot.rcut2;
+    const double rc2 = d.pot.rcut2, shm = d.pot.shift ? d.pot.shm : 0.0;
     const int mexp = d.pot.m;
     const int* lst = d.vlist + (size_t)s * kVMax;
-    f2sum facc = {0.f, 0.f};
-    double racc = 0.0;
-    R tacc = R(0);
+    double* hb = d.hbuf + (size_t)s * kVMax;
+    double racc = 0.0, tacc = 0.0;
     int cnt = 0, nfold = 0;  // pairs inside rcut: nfold * kSpanV + cnt
 #pragma unroll 4
     for (int e = beg; e < end; ++e) {
-        const int q = lst[e];
-        R dx, dy, dz;
-        v_sep<PREC>(pi, vp[q], dx, dy, dz);
-        R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double4 pj = vp[lst[e]];
+        const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const bool in = r2 < rc2;
-        r2 = in ? r2 : big<R>();
+        r2 = in ? r2 : big<double>();
+        double term;
         if (SPECIAL) {
-            const R inv = inv_r2(r2);
-            tacc = fma(inv * inv, inv, tacc);
+            const double inv = inv_r2(r2);
+            term = inv * inv * inv;
         } else {
-            const R ir = inv_r(r2);
-            tacc += rpow(ir * ir, ir, mexp);
+            const double ir = inv_r(r2);
+            term = rpow(ir * ir, ir, mexp);
         }
+        tacc += term;
+        hb[e] = in ? term - shm : 0.0;
         cnt += in;
         if (cnt == kSpanV) {
-            if (PREC == 1)
-                facc = f2_add(facc, (float)tacc);
-            else
-                racc += (double)tacc;
-            tacc = R(0);
+            racc += tacc;
+            tacc = 0.0;
             cnt = 0;
             ++nfold;
         }
     }
-    if (PREC == 1) {
-        facc = f2_add(facc, (float)tacc);
-        racc = (double)facc.hi + (double)facc.lo;
-    } else {
-        racc += (double)tacc;
-    }
-    if (d.pot.shift) racc -= (double)(nfold * kSpanV + cnt) * d.pot.shm;
-    const double rho = v_group_sum(racc) * d.pot.am;
-    if (t != 0) return;
+    racc += tacc;
+    racc -= (double)(nfold * kSpanV + cnt) * shm;
+    racc = v_group_sum(racc);
+    if (t == 0) d.rho_half[s] = racc;
+}
+
+// One thread per slot: rho from the atom's own sum and its reverse list; g = B6 rho^-1/2.
+__global__ void __launch_bounds__(kVThreads) k_v_dgather(const Dev d, int obs) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.nslot) return;
+    double r = d.rho_half[s];
+    const int n = min(d.vrcount[s], kVMax);
+    const uint64_t* rv = d.vrev + (size_t)s * kVMax;
+#pragma unroll 8
+    for (int k = 0; k < n; ++k) r += d.hbuf[(uint32_t)rv[k]];  // loads run ahead, the adds stay in order
+    const double rho = r * d.pot.am;
     const int i = d.vorder[s];
     d.rho[i] = rho;
-    V4 p = pi;
-    if (PREC == 1) {
-        const float rf = (float)rho;
-        float y = rsqrt_approx(rf);
-        y = y * (1.5f - 0.5f * rf * y * y);  // one Newton step
-        p.w = rho > 0.0 ? (float)d.pot.B6 * y : 0.0f;
-    } else {
-        p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
-    }
-    reinterpret_cast<V4*>(d.vposg)[s] = p;
+    double4 p = reinterpret_cast<const double4*>(d.vhi)[s];
+    p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
+    reinterpret_cast<double4*>(d.vposg)[s] = p;
     if (obs) d.eatom[2 * i] = -d.pot.eps * d.pot.c * sqrt(rho);
 }
 
-// mode 0: forces; 1: forces and per-atom pair energies; 2: MD step (second half kick, per-atom
-// observables if due, then the first half of the next step unless last or Berendsen).
-template <int PREC, int SPECIAL, int ENERGY>
-__global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, int k_local, int last) {
-    using R = typename Tr<PREC>::R;
-    using V4 = typename Tr<PREC>::V4;
+template <int SPECIAL, int ENERGY>
+__global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d) {
     pdl_launch_dependents();
     pdl_wait();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = gt >> kVLog, t = gt & (kVLanes - 1);
     if (s >= d.nslot) return;  // whole atoms leave together
-    const V4* vp = reinterpret_cast<const V4*>(d.vposg);
-    const V4 pi = vp[s];
+    const double4* vp = reinterpret_cast<const double4*>(d.vposg);
+    const double4 pi = vp[s];
     const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
-    const R A = (R)d.pot.A9;
-    const R rc2 = (R)d.pot.rcut2;
+    const double A = d.pot.A9, rc2 = d.pot.rcut2, shn = d.pot.shift ? d.pot.shn : 0.0;
     const int nexp = d.pot.n, mexp = d.pot.m;
     const int* lst = d.vlist + (size_t)s * kVMax;
-    R fx = R(0), fy = R(0), fz = R(0), sx = R(0), sy = R(0), sz = R(0), se = R(0);
-    double ea = 0.0;
+    double4* fb = d.fbuf + (size_t)s * kVMax;
+    double fx = 0.0, fy = 0.0, fz = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, se = 0.0, ea = 0.0;
     int cnt = 0, nfold = 0;  // pairs inside rcut: nfold * kSpanV + cnt
 #pragma unroll 4
     for (int e = beg; e < end; ++e) {
-        const int q = lst[e];
-        const V4 pj = vp[q];
-        R dx, dy, dz;
-        v_sep<PREC>(pi, pj, dx, dy, dz);
-        R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double4 pj = vp[lst[e]];
+        const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const bool in = r2 < rc2;
-        r2 = in ? r2 : big<R>();
-        const R ir = inv_r(r2);
-        const R inv = ir * ir;
-        R coef, rn;
+        r2 = in ? r2 : big<double>();
+        const double ir = inv_r(r2);
+        const double inv = ir * ir;
+        double coef, rn;
         if (SPECIAL) {
-            const R inv2 = inv * inv, inv4 = inv2 * inv2;
+            const double inv2 = inv * inv, inv4 = inv2 * inv2;
             coef = inv4 * fma(A, inv * ir, -(pi.w + pj.w));
             rn = inv4 * ir;
         } else {
             rn = rpow(inv, ir, nexp);
-            const R rm = rpow(inv, ir, mexp);
+            const double rm = rpow(inv, ir, mexp);
             coef = inv * (A * rn - (pi.w + pj.w) * rm);
         }
-        sx = fma(coef, dx, sx);
-        sy = fma(coef, dy, sy);
-        sz = fma(coef, dz, sz);
+        const double ux = coef * dx, uy = coef * dy, uz = coef * dz;  // the force on i from j
+        sx += ux;
+        sy += uy;
+        sz += uz;
         if (ENERGY) se += rn;
+        fb[e] = make_double4(ux, uy, uz, ENERGY ? (in ? rn - shn : 0.0) : 0.0);
         cnt += in;
         if (cnt == kSpanV) {
             fx += sx;
             fy += sy;
             fz += sz;
-            sx = sy = sz = R(0);
+            sx = sy = sz = 0.0;
             if (ENERGY) {
-                ea += (double)se;
-                se = R(0);
+                ea += se;
+                se = 0.0;
             }
             cnt = 0;
             ++nfold;
         }
     }
-    const double gx = v_group_sum((double)(fx + sx));
-    const double gy = v_group_sum((double)(fy + sy));
-    const double gz = v_group_sum((double)(fz + sz));
-    const double Ep =
-        ENERGY ? v_group_sum(ea + (double)se - (d.pot.shift ? (double)(nfold * kSpanV + cnt) * d.pot.shn : 0.0))
-               : 0.0;
-    if (t != 0) return;
-    const R Fx = (R)gx, Fy = (R)gy, Fz = (R)gz;
+    const double gx = v_group_sum(fx + sx), gy = v_group_sum(fy + sy), gz = v_group_sum(fz + sz);
+    const double Ep = ENERGY ? v_group_sum(ea + se - (double)(nfold * kSpanV + cnt) * shn) : 0.0;
+    if (t == 0) d.fhalf[s] = make_double4(gx, gy, gz, Ep);
+}
+
+// One thread per slot: the force (and pair energy) from the atom's own sum and its reverse list,
+// less each lower partner's term (Newton's third law), then the per-atom work of the mode:
+// 0 forces; 1 forces and per-atom pair energies; 2 MD step (second half kick, per-atom observables
+// if due, then the first half of the next step unless last or Berendsen).
+template <int ENERGY>
+__global__ void __launch_bounds__(kVThreads) k_v_fgather(const Dev d, int mode, int k_local, int last) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.nslot) return;
+    const double4 h = d.fhalf[s];
+    double Fx = h.x, Fy = h.y, Fz = h.z, Ep = h.w;
+    const int n = min(d.vrcount[s], kVMax);
+    const uint64_t* rv = d.vrev + (size_t)s * kVMax;
+#pragma unroll 8
+    for (int k = 0; k < n; ++k) {  // loads run ahead, the subtractions stay in order
+        const double4 u = d.fbuf[(uint32_t)rv[k]];
+        Fx -= u.x;
+        Fy -= u.y;
+        Fz -= u.z;
+        if (ENERGY) Ep += u.w;
+    }
     const int i = d.vorder[s];
     const int np = d.npad;
-    R* fo = reinterpret_cast<R*>(d.f);
+    double* fo = reinterpret_cast<double*>(d.f);
     fo[i] = Fx;
     fo[np + i] = Fy;
     fo[2 * np + i] = Fz;
@@ -383,9 +438,9 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
     const Run& r = *d.run;
     const int cl = d.cl_of_group[i >> 5];
     const double hs = d.hs[i];
-    const double vx = fma(hs, (double)Fx, d.v[i]);
-    const double vy = fma(hs, (double)Fy, d.v[np + i]);
-    const double vz = fma(hs, (double)Fz, d.v[2 * np + i]);
+    const double vx = fma(hs, Fx, d.v[i]);
+    const double vy = fma(hs, Fy, d.v[np + i]);
+    const double vz = fma(hs, Fz, d.v[2 * np + i]);
     d.v[i] = vx;
     d.v[np + i] = vy;
     d.v[2 * np + i] = vz;
@@ -396,9 +451,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d, int mode, in
         d.obs_v[3 * i + 1] = vy;
         d.obs_v[3 * i + 2] = vz;
     }
-    if (!last)
-        begin_step<PREC>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, (double)Fx, (double)Fy,
-                         (double)Fz, k_local + 1);
+    if (!last) begin_step<0>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, Fx, Fy, Fz, k_local + 1);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -410,10 +463,10 @@ cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s) {
 
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s) {
     if (d.prec == 1) return launch_q_rebuild(d, cond, k_local, s);
+    const int wgrid = (d.nslot + kVThreads / 32 - 1) / (kVThreads / 32);  // one warp per slot
     cudaError_t e = launch_ex(k_v_build<0>, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local);
-    if (e != cudaSuccess) return e;
-    e = launch_ex(k_v_sort, (d.nslot + kVThreads / 32 - 1) / (kVThreads / 32), kVThreads, 0, 0, s, d, cond,
-                  k_local);
+    if (e == cudaSuccess) e = launch_ex(k_v_sort, wgrid, kVThreads, 0, 0, s, d, cond, k_local);
+    if (e == cudaSuccess) e = launch_ex(k_v_rsort, wgrid, kVThreads, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
     return launch_ex(k_v_commit<0>, (d.nslot + kVThreads - 1) / kVThreads, kVThreads, 0, 0, s, d, cond, k_local);
 }
@@ -421,17 +474,22 @@ cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s
 static int v_pass_grid(const Dev& d) {
     return (int)(((int64_t)d.nslot * kVLanes + kVThreads - 1) / kVThreads);
 }
+static int v_atom_grid(const Dev& d) { return (d.nslot + kVThreads - 1) / kVThreads; }
 
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s) {
     if (d.prec == 1) return launch_q_density(d, obs, s);
-    return d.pot.special ? launch_ex(k_v_density<0, 1>, v_pass_grid(d), kVThreads, 0, 0, s, d, obs)
-                         : launch_ex(k_v_density<0, 0>, v_pass_grid(d), kVThreads, 0, 0, s, d, obs);
+    cudaError_t e = d.pot.special ? launch_ex(k_v_density<1>, v_pass_grid(d), kVThreads, 0, 0, s, d)
+                                  : launch_ex(k_v_density<0>, v_pass_grid(d), kVThreads, 0, 0, s, d);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_v_dgather, v_atom_grid(d), kVThreads, 0, 0, s, d, obs);
 }
 
 template <int ENERGY>
 static cudaError_t v_force_e(const Dev& d, int mode, int k, int last, cudaStream_t s) {
-    return d.pot.special ? launch_ex(k_v_force<0, 1, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d, mode, k, last)
-                         : launch_ex(k_v_force<0, 0, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d, mode, k, last);
+    cudaError_t e = d.pot.special ? launch_ex(k_v_force<1, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d)
+                                  : launch_ex(k_v_force<0, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_v_fgather<ENERGY>, v_atom_grid(d), kVThreads, 0, 0, s, d, mode, k, last);
 }
 
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
