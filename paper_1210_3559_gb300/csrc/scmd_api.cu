@@ -385,10 +385,11 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
         const bool last = k == M - 1;
         const int flags = (last ? 1 : 0) | (obs ? 2 : 0);
         if (c->path == 2) {
-            CK(c, launch_v_pos(d, k, c->stream));
+            // MIXED lists: within a chunk (not Berendsen) the previous force pass did the position kernel's work
+            if (c->nqmax == 0 || k == 0 || kind == MD_BERENDSEN) CK(c, launch_v_pos(d, k, c->stream));
             CK(c, launch_cell_build(d, c->stream, 1, k));
             CK(c, launch_v_rebuild(d, 1, k, c->stream));
-            CK(c, launch_v_density(d, obs ? 1 : 0, c->stream));
+            CK(c, launch_v_density(d, obs ? 1 : 0, c->stream, k));
             CK(c, launch_v_force(d, 2, k, flags, c->stream));
             if (obs) CK(c, launch_cell_obs(d, kind == MD_BERENDSEN ? 1 : 0, kind == MD_BERENDSEN ? 0 : 1, c->stream));
             if (kind == MD_BERENDSEN) CK(c, launch_cell_ke(d, c->stream));
@@ -1353,8 +1354,9 @@ md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chun
     if (!c) return MD_ERR_INVALID;
     // lists: positions, cell build (3), list build (MIXED scan, order, list; FP64 build, sort, reverse sort,
     // commit), passes (MIXED 2; FP64 2 + 2 gathers)
-    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 9 : 12) : (c->path == 1 ? 5 : 2);
-    if (per_chunk) *per_chunk = 3;
+    // (MIXED: the position kernel runs once per chunk, and every step with Berendsen)
+    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 8 : 12) : (c->path == 1 ? 5 : 2);
+    if (per_chunk) *per_chunk = c->path == 2 && c->nqmax > 0 ? 4 : 3;
     return MD_OK;
 }
 

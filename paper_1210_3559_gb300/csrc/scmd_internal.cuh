@@ -212,12 +212,12 @@ cudaError_t launch_cell_ke(const Dev& d, cudaStream_t s);
 // Neighbour-list path (defined in scmd_verlet.cu).
 cudaError_t launch_v_pos(const Dev& d, int k_local, cudaStream_t s);
 cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
-cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s);
+cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s, int k_local = -1);  // k_local: MD step
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // MIXED quad lists (defined in scmd_quads.cu); launch_v_* dispatch to them for MIXED.
 cudaError_t launch_q_pos(const Dev& d, int k_local, cudaStream_t s);
 cudaError_t launch_q_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s);  // after the cell build
-cudaError_t launch_q_density(const Dev& d, int obs, cudaStream_t s);
+cudaError_t launch_q_density(const Dev& d, int obs, int k_local, cudaStream_t s);  // k_local < 0: outside a step
 cudaError_t launch_q_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // Structural observables (defined in scmd_structure.cu).
 constexpr int kNbCap = 32;  // neighbours a CNA list stores (the count is exact beyond)

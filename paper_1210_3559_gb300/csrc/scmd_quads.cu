@@ -8,7 +8,8 @@
 // quads and tests it against the 4 atoms of the warp's own quad, so one warp-wide load brings 32
 // neighbours for 128 pairs. Per step:
 //   k_q_pos    : every slot's offset from its quad's reference point, and the largest squared
-//                displacement since the last rebuild;
+//                displacement since the last rebuild (at a chunk's first step and with Berendsen;
+//                otherwise the previous step's force pass, which moved the atoms, did this);
 //   rebuild, when that displacement exceeds the trigger (the kernels exit at once otherwise):
 //     the cell build of the cell-list path (clear, bin, sort), then
 //     k_q_scan   : the first slot of every cell (cells padded to whole quads), and the quad count;
@@ -25,6 +26,8 @@
 // The sums run over quads in list order, which depends on when the lists were built: unlike the
 // FP64 lists, a resumed MIXED run agrees with an uninterrupted one to rounding, not bit for bit.
 // Runs are deterministic: slots follow the cell order and lists the fixed order of the 27 cells.
+#include <algorithm>
+
 #include "scmd_cells.cuh"
 
 namespace scmd {
@@ -123,70 +126,73 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
     pdl_launch_dependents();
     pdl_wait();
     if (cond && !vlist_rebuild_due(d, k_local)) return;
-    const int c = blockIdx.x;
-    const int n = min(d.cell_count[c], kCellCap);
-    if (n == 0) return;
-    const int cl = d.cell_cl[c];
-    const float h = (float)d.grid[cl].h;
-    const float4* cp = reinterpret_cast<const float4*>(d.cpos);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        s_key[k] = morton9(cp[(size_t)c * kCellCap + k], h);
-        s_atom[k] = d.cell_atoms[(size_t)c * kCellCap + k];
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const uint32_t key = s_key[k];
-        const int a = s_atom[k];
-        int r = 0;
-        for (int m = 0; m < n; ++m) r += (s_key[m] < key) || (s_key[m] == key && s_atom[m] < a);
-        s_sorted[r] = a;
-    }
-    __syncthreads();
-    const int base = d.cell_base[c], n4 = (n + 3) & ~3, ns = d.nslot, np = d.npad;
-    for (int r = threadIdx.x; r < n4; r += blockDim.x) {
-        const int a = r < n ? s_sorted[r] : -1;
-        d.vorder[base + r] = a;
-        if (a >= 0) d.vslotof[a] = base + r;
-    }
-    const double* o = d.origin + 3 * cl;
-    for (int t = threadIdx.x; t < n4 / 4; t += blockDim.x) {
-        const int Q = (base >> 2) + t;
-        double rel[4][3], cen[3] = {0.0, 0.0, 0.0}, lo[3], hi[3];
-        int cnt = 0;
-        for (int u = 0; u < 4; ++u) {
-            const int r = 4 * t + u;
-            if (r >= n) break;
-            const int a = s_sorted[r];
-            for (int q = 0; q < 3; ++q) {
-                rel[u][q] = d.x[q * np + a] - o[q];
-                cen[q] += rel[u][q];
-                lo[q] = cnt == 0 ? rel[u][q] : fmin(lo[q], rel[u][q]);
-                hi[q] = cnt == 0 ? rel[u][q] : fmax(hi[q], rel[u][q]);
-            }
-            ++cnt;
+    for (int c = blockIdx.x; c < d.n_cells; c += gridDim.x) {  // a small grid: cheap when no rebuild is due
+        __syncthreads();  // the previous cell's shared arrays are no longer read
+        const int n = min(d.cell_count[c], kCellCap);
+        if (n == 0) continue;
+        const int cl = d.cell_cl[c];
+        const float h = (float)d.grid[cl].h;
+        const float4* cp = reinterpret_cast<const float4*>(d.cpos);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            s_key[k] = morton9(cp[(size_t)c * kCellCap + k], h);
+            s_atom[k] = d.cell_atoms[(size_t)c * kCellCap + k];
         }
-        float4 C;
-        C.x = (float)(rint(cen[0] / cnt * 4096.0) * (1.0 / 4096.0));
-        C.y = (float)(rint(cen[1] / cnt * 4096.0) * (1.0 / 4096.0));
-        C.z = (float)(rint(cen[2] / cnt * 4096.0) * (1.0 / 4096.0));
-        C.w = 0.f;
-        d.q_ref[Q] = C;
-        d.q_box[2 * Q] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
-        d.q_box[2 * Q + 1] =
-            make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
-        d.q_cell[Q] = c;
-        for (int u = 0; u < 4; ++u) {
-            const int s = 4 * Q + u;
-            float4 p = make_float4(kFar, kFar, kFar, 0.f);
-            if (u < cnt) {
-                const int a = s_sorted[4 * t + u];
-                p = make_float4((float)(rel[u][0] - (double)C.x), (float)(rel[u][1] - (double)C.y),
-                                (float)(rel[u][2] - (double)C.z), 0.f);
-                d.vxref[s] = d.x[a];
-                d.vxref[ns + s] = d.x[np + a];
-                d.vxref[2 * ns + s] = d.x[2 * np + a];
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const uint32_t key = s_key[k];
+            const int a = s_atom[k];
+            int r = 0;
+            for (int m = 0; m < n; ++m) r += (s_key[m] < key) || (s_key[m] == key && s_atom[m] < a);
+            s_sorted[r] = a;
+        }
+        __syncthreads();
+        const int base = d.cell_base[c], n4 = (n + 3) & ~3, ns = d.nslot, np = d.npad;
+        for (int r = threadIdx.x; r < n4; r += blockDim.x) {
+            const int a = r < n ? s_sorted[r] : -1;
+            d.vorder[base + r] = a;
+            if (a >= 0) d.vslotof[a] = base + r;
+        }
+        const double* o = d.origin + 3 * cl;
+        for (int t = threadIdx.x; t < n4 / 4; t += blockDim.x) {
+            const int Q = (base >> 2) + t;
+            double rel[4][3], cen[3] = {0.0, 0.0, 0.0}, lo[3], hi[3];
+            int cnt = 0;
+            for (int u = 0; u < 4; ++u) {
+                const int r = 4 * t + u;
+                if (r >= n) break;
+                const int a = s_sorted[r];
+                for (int q = 0; q < 3; ++q) {
+                    rel[u][q] = d.x[q * np + a] - o[q];
+                    cen[q] += rel[u][q];
+                    lo[q] = cnt == 0 ? rel[u][q] : fmin(lo[q], rel[u][q]);
+                    hi[q] = cnt == 0 ? rel[u][q] : fmax(hi[q], rel[u][q]);
+                }
+                ++cnt;
             }
-            reinterpret_cast<float4*>(d.vhi)[s] = p;
+            float4 C;
+            C.x = (float)(rint(cen[0] / cnt * 4096.0) * (1.0 / 4096.0));
+            C.y = (float)(rint(cen[1] / cnt * 4096.0) * (1.0 / 4096.0));
+            C.z = (float)(rint(cen[2] / cnt * 4096.0) * (1.0 / 4096.0));
+            C.w = 0.f;
+            d.q_ref[Q] = C;
+            d.q_box[2 * Q] =
+                make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
+            d.q_box[2 * Q + 1] =
+                make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
+            d.q_cell[Q] = c;
+            for (int u = 0; u < 4; ++u) {
+                const int s = 4 * Q + u;
+                float4 p = make_float4(kFar, kFar, kFar, 0.f);
+                if (u < cnt) {
+                    const int a = s_sorted[4 * t + u];
+                    p = make_float4((float)(rel[u][0] - (double)C.x), (float)(rel[u][1] - (double)C.y),
+                                    (float)(rel[u][2] - (double)C.z), 0.f);
+                    d.vxref[s] = d.x[a];
+                    d.vxref[ns + s] = d.x[np + a];
+                    d.vxref[2 * ns + s] = d.x[2 * np + a];
+                }
+                reinterpret_cast<float4*>(d.vhi)[s] = p;
+            }
         }
     }
 }
@@ -198,63 +204,63 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
     pdl_launch_dependents();
     pdl_wait();
     if (cond && !vlist_rebuild_due(d, k_local)) return;
-    const int lane = threadIdx.x & 31;
-    const int Q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (Q >= *d.q_n) return;
-    const int c = d.q_cell[Q];
-    const CellGrid g = d.grid[d.cell_cl[c]];
-    const int loc = c - g.off, cx = loc % g.G, cy = (loc / g.G) % g.G, cz = loc / (g.G * g.G);
-    const float4 lo = d.q_box[2 * Q], hi = d.q_box[2 * Q + 1];
-    const float rl2 = (float)d.vrl2;
-    const float4* vp = reinterpret_cast<const float4*>(d.vhi);
-    float4 oi[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) oi[a] = vp[4 * Q + a];
-    const float4 CI = d.q_ref[Q];
-    int* out = d.q_list + (size_t)Q * kQMax;
-    int n = 0;
-    bool overflow = false;
-    for (int nb = 0; nb < 27; ++nb) {
-        const int x = cx + nb % 3 - 1, y = cy + (nb / 3) % 3 - 1, z = cz + nb / 9 - 1;
-        if (x < 0 || x >= g.G || y < 0 || y >= g.G || z < 0 || z >= g.G) continue;
-        const int c2 = g.off + (z * g.G + y) * g.G + x;
-        const int q0 = d.cell_base[c2] >> 2, nq = (min(d.cell_count[c2], kCellCap) + 3) >> 2;
-        for (int t0 = 0; t0 < nq; t0 += 32) {
-            bool in = false;
-            const int J = q0 + t0 + lane;
-            if (t0 + lane < nq) {
-                const float4 l2 = d.q_box[2 * J], h2 = d.q_box[2 * J + 1];
-                const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
-                const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
-                const float ez = fmaxf(0.f, fmaxf(l2.z - hi.z, lo.z - h2.z));
-                if (ex * ex + ey * ey + ez * ez < rl2) {  // boxes in reach: is some atom pair?
-                    const float4 CJ = d.q_ref[J];
-                    const float Dx = CI.x - CJ.x, Dy = CI.y - CJ.y, Dz = CI.z - CJ.z;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float4 pj = vp[4 * J + u];
-                        const float px = pj.x - Dx, py = pj.y - Dy, pz = pj.z - Dz;
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
-                            in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+    const int lane = threadIdx.x & 31, nq = *d.q_n;
+    for (int Q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; Q < nq; Q += (gridDim.x * blockDim.x) >> 5) {
+        const int c = d.q_cell[Q];
+        const CellGrid g = d.grid[d.cell_cl[c]];
+        const int loc = c - g.off, cx = loc % g.G, cy = (loc / g.G) % g.G, cz = loc / (g.G * g.G);
+        const float4 lo = d.q_box[2 * Q], hi = d.q_box[2 * Q + 1];
+        const float rl2 = (float)d.vrl2;
+        const float4* vp = reinterpret_cast<const float4*>(d.vhi);
+        float4 oi[4];
+    #pragma unroll
+        for (int a = 0; a < 4; ++a) oi[a] = vp[4 * Q + a];
+        const float4 CI = d.q_ref[Q];
+        int* out = d.q_list + (size_t)Q * kQMax;
+        int n = 0;
+        bool overflow = false;
+        for (int nb = 0; nb < 27; ++nb) {
+            const int x = cx + nb % 3 - 1, y = cy + (nb / 3) % 3 - 1, z = cz + nb / 9 - 1;
+            if (x < 0 || x >= g.G || y < 0 || y >= g.G || z < 0 || z >= g.G) continue;
+            const int c2 = g.off + (z * g.G + y) * g.G + x;
+            const int q0 = d.cell_base[c2] >> 2, nq = (min(d.cell_count[c2], kCellCap) + 3) >> 2;
+            for (int t0 = 0; t0 < nq; t0 += 32) {
+                bool in = false;
+                const int J = q0 + t0 + lane;
+                if (t0 + lane < nq) {
+                    const float4 l2 = d.q_box[2 * J], h2 = d.q_box[2 * J + 1];
+                    const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
+                    const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
+                    const float ez = fmaxf(0.f, fmaxf(l2.z - hi.z, lo.z - h2.z));
+                    if (ex * ex + ey * ey + ez * ez < rl2) {  // boxes in reach: is some atom pair?
+                        const float4 CJ = d.q_ref[J];
+                        const float Dx = CI.x - CJ.x, Dy = CI.y - CJ.y, Dz = CI.z - CJ.z;
+    #pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 pj = vp[4 * J + u];
+                            const float px = pj.x - Dx, py = pj.y - Dy, pz = pj.z - Dz;
+    #pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
+                                in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+                            }
                         }
                     }
                 }
+                const unsigned b = __ballot_sync(0xffffffffu, in);
+                const int pos = n + __popc(b & ((1u << lane) - 1u));
+                if (in) {
+                    if (pos < kQMax)
+                        out[pos] = J;
+                    else
+                        overflow = true;
+                }
+                n += __popc(b);
             }
-            const unsigned b = __ballot_sync(0xffffffffu, in);
-            const int pos = n + __popc(b & ((1u << lane) - 1u));
-            if (in) {
-                if (pos < kQMax)
-                    out[pos] = J;
-                else
-                    overflow = true;
-            }
-            n += __popc(b);
         }
+        if (lane == 0) d.q_count[Q] = min(n, kQMax);
+        if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(d.status, 4);
     }
-    if (lane == 0) d.q_count[Q] = min(n, kQMax);
-    if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(d.status, 4);
 }
 
 // ---------------------------------------------------------------- passes
@@ -285,11 +291,13 @@ __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int 
 // Each CTA takes 8 quads (32 slots). The warps sum their quads' pairs; then warp 0 finishes all 32
 // atoms with one lane each, so the FP64 per-atom work runs on full warps.
 template <int SPECIAL, int SHIFT>
-__global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs) {
+__global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs, int k_local) {
     __shared__ double s_sum[32];
     __shared__ float4 s_own[32];
     pdl_launch_dependents();
     pdl_wait();
+    // in an MD step: clear the displacement record the force pass fills for the next step
+    if (k_local >= 0 && blockIdx.x == 0 && threadIdx.x == 0) d.vdmax[(*d.step_base + k_local + 1) & 1] = 0u;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 3;
     const int nq = *d.q_n, Q = blockIdx.x * (kQThreads / 32) + w;
     if (blockIdx.x * (kQThreads / 32) >= nq) return;  // the whole CTA is past the last quad
@@ -441,44 +449,70 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
         }
     }
     __syncthreads();
-    if (w != 0 || blockIdx.x * (kQThreads / 32) + (lane >> 2) >= nq) return;
-    const int i = d.vorder[blockIdx.x * kQThreads / 8 + lane];
-    if (i < 0) return;
-    const float Fx = s_f[0][lane], Fy = s_f[1][lane], Fz = s_f[2][lane];
-    const int np = d.npad;
-    float* fo = reinterpret_cast<float*>(d.f);
-    fo[i] = Fx;
-    fo[np + i] = Fy;
-    fo[2 * np + i] = Fz;
-    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
-    if (ENERGY) d.eatom[2 * i + 1] = s_e[lane];
-    if (mode != 2) return;
+    if (w != 0) return;
+    // warp 0: one lane per slot of the CTA's 8 quads
+    const int sl = blockIdx.x * kQThreads / 8 + lane;
+    const int i = blockIdx.x * (kQThreads / 32) + (lane >> 2) < nq ? d.vorder[sl] : -1;
     const Run& r = *d.run;
-    const int cl = d.cl_of_group[i >> 5];
-    const double hs = d.hs[i];
-    const double vx = fma(hs, (double)Fx, d.v[i]);
-    const double vy = fma(hs, (double)Fy, d.v[np + i]);
-    const double vz = fma(hs, (double)Fz, d.v[2 * np + i]);
-    d.v[i] = vx;
-    d.v[np + i] = vy;
-    d.v[2 * np + i] = vz;
-    if (r.kind == 2) return;  // Berendsen: the rescale kernel records and starts the step
-    if (ENERGY) {             // observables at the end of this step, before the next begins
-        for (int k = 0; k < 3; ++k) d.obs_x[3 * i + k] = d.x[k * np + i];
-        d.obs_v[3 * i] = vx;
-        d.obs_v[3 * i + 1] = vy;
-        d.obs_v[3 * i + 2] = vz;
+    // in an MD step (not the chunk's last, not Berendsen) this kernel starts the next step, so it also
+    // does the position kernel's work for it: the slot's offset and the displacement since the rebuild
+    const bool next = mode == 2 && !last && r.kind != 2;
+    float dmax = 0.f;
+    if (i >= 0) {
+        const float Fx = s_f[0][lane], Fy = s_f[1][lane], Fz = s_f[2][lane];
+        const int np = d.npad;
+        float* fo = reinterpret_cast<float*>(d.f);
+        fo[i] = Fx;
+        fo[np + i] = Fy;
+        fo[2 * np + i] = Fz;
+        if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+        if (ENERGY) d.eatom[2 * i + 1] = s_e[lane];
+        if (mode == 2) {
+            const int cl = d.cl_of_group[i >> 5];
+            const double hs = d.hs[i];
+            const double vx = fma(hs, (double)Fx, d.v[i]);
+            const double vy = fma(hs, (double)Fy, d.v[np + i]);
+            const double vz = fma(hs, (double)Fz, d.v[2 * np + i]);
+            d.v[i] = vx;
+            d.v[np + i] = vy;
+            d.v[2 * np + i] = vz;
+            if (r.kind != 2) {  // Berendsen: the rescale kernel records and starts the step
+                if (ENERGY) {   // observables at the end of this step, before the next begins
+                    for (int k = 0; k < 3; ++k) d.obs_x[3 * i + k] = d.x[k * np + i];
+                    d.obs_v[3 * i] = vx;
+                    d.obs_v[3 * i + 1] = vy;
+                    d.obs_v[3 * i + 2] = vz;
+                }
+                if (!last) {
+                    begin_step<1>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, (double)Fx, (double)Fy,
+                                  (double)Fz, k_local + 1);
+                    const double x = d.x[i], y = d.x[np + i], z = d.x[2 * np + i];
+                    const double* o = d.origin + 3 * cl;
+                    const float4 C = d.q_ref[sl >> 2];
+                    reinterpret_cast<float4*>(d.vhi)[sl] =
+                        make_float4((float)((x - o[0]) - (double)C.x), (float)((y - o[1]) - (double)C.y),
+                                    (float)((z - o[2]) - (double)C.z), 0.f);
+                    const int ns = d.nslot;
+                    const double ex = x - d.vxref[sl], ey = y - d.vxref[ns + sl], ez = z - d.vxref[2 * ns + sl];
+                    dmax = (float)(ex * ex + ey * ey + ez * ez);
+                    if (!(dmax <= 3.0e38f)) dmax = 3.0e38f;  // non-finite positions force a rebuild
+                }
+            }
+        }
     }
-    if (!last)
-        begin_step<1>(d, r, i, cl, i - d.poff[cl], *d.step_base + k_local + 1, (double)Fx, (double)Fy, (double)Fz,
-                      k_local + 1);
+    if (next) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (lane == 0 && dmax > 0.f)
+            atomicMax(d.vdmax + ((*d.step_base + k_local + 1) & 1), __float_as_uint(dmax));
+    }
 }
 
 int q_pass_grid(const Dev& d) { return (d.nqmax + kQThreads / 32 - 1) / (kQThreads / 32); }
 
-template <int SHIFT> cudaError_t q_density_s(const Dev& d, int obs, cudaStream_t s) {
-    return d.pot.special ? launch_ex(k_q_density<1, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs)
-                         : launch_ex(k_q_density<0, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs);
+template <int SHIFT> cudaError_t q_density_s(const Dev& d, int obs, int k_local, cudaStream_t s) {
+    return d.pot.special ? launch_ex(k_q_density<1, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs, k_local)
+                         : launch_ex(k_q_density<0, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs, k_local);
 }
 
 template <int ENERGY> cudaError_t q_force_e(const Dev& d, int mode, int k, int last, cudaStream_t s) {
@@ -496,13 +530,14 @@ cudaError_t launch_q_pos(const Dev& d, int k_local, cudaStream_t s) {
 cudaError_t launch_q_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s) {
     cudaError_t e = launch_ex(k_q_scan, 1, 1024, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
-    e = launch_ex(k_q_order, d.n_cells, kCellThreads, 0, 0, s, d, cond, k_local);
+    // grid-stride kernels on about 4 CTAs per SM: most steps they only check that no rebuild is due
+    e = launch_ex(k_q_order, std::min(d.n_cells, 608), kCellThreads, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
-    return launch_ex(k_q_list, q_pass_grid(d), kQThreads, 0, 0, s, d, cond, k_local);
+    return launch_ex(k_q_list, std::min(q_pass_grid(d), 608), kQThreads, 0, 0, s, d, cond, k_local);
 }
 
-cudaError_t launch_q_density(const Dev& d, int obs, cudaStream_t s) {
-    return d.pot.shift ? q_density_s<1>(d, obs, s) : q_density_s<0>(d, obs, s);
+cudaError_t launch_q_density(const Dev& d, int obs, int k_local, cudaStream_t s) {
+    return d.pot.shift ? q_density_s<1>(d, obs, k_local, s) : q_density_s<0>(d, obs, k_local, s);
 }
 
 cudaError_t launch_q_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {

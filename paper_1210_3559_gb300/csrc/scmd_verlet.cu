@@ -476,8 +476,8 @@ static int v_pass_grid(const Dev& d) {
 }
 static int v_atom_grid(const Dev& d) { return (d.nslot + kVThreads - 1) / kVThreads; }
 
-cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s) {
-    if (d.prec == 1) return launch_q_density(d, obs, s);
+cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s, int k_local) {
+    if (d.prec == 1) return launch_q_density(d, obs, k_local, s);
     cudaError_t e = d.pot.special ? launch_ex(k_v_density<1>, v_pass_grid(d), kVThreads, 0, 0, s, d)
                                   : launch_ex(k_v_density<0>, v_pass_grid(d), kVThreads, 0, 0, s, d);
     if (e != cudaSuccess) return e;
