@@ -92,7 +92,7 @@ struct md_ctx {
     bool msd_ref = false;
     // neighbour-list path
     int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vsub = nullptr, *d_vorder = nullptr, *d_vslotof = nullptr;
-    int32_t *d_vslot = nullptr, *d_vrcount = nullptr;
+    int32_t *d_vslot = nullptr, *d_vrcount = nullptr, *d_vrsub = nullptr;
     uint64_t* d_vrev = nullptr;
     double *d_hbuf = nullptr, *d_rho_half = nullptr;
     double4 *d_fbuf = nullptr, *d_fhalf = nullptr;
@@ -201,6 +201,7 @@ void fill_dev(md_ctx* c) {
     d.vsub = c->d_vsub;
     d.vrcount = c->d_vrcount;
     d.vrev = c->d_vrev;
+    d.vrsub = c->d_vrsub;
     d.hbuf = c->d_hbuf;
     d.fbuf = c->d_fbuf;
     d.rho_half = c->d_rho_half;
@@ -464,7 +465,7 @@ void free_all(md_ctx* c) {
                     c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
                     c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi,
                     c->d_q_n, c->d_cell_base, c->d_q_cell, c->d_q_list, c->d_q_count, c->d_q_ref, c->d_q_box,
-                    c->d_vrcount, c->d_vrev, c->d_hbuf, c->d_fbuf, c->d_rho_half, c->d_fhalf,
+                    c->d_vrcount, c->d_vrev, c->d_vrsub, c->d_hbuf, c->d_fbuf, c->d_rho_half, c->d_fhalf,
                     c->d_vposg, c->d_vxref, c->d_vdmax,
                     c->sb.com, c->sb.core, c->sb.ncore, c->sb.hist, c->sb.ref, c->sb.ref_com, c->sb.sel, c->sb.msd,
                     c->sb.nsel, c->sb.nb, c->sb.nnb, c->sb.cls, c->sb.counts, c->sb.capped};
@@ -837,6 +838,8 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
             CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
             CKC(cudaMalloc(&c->d_vrcount, sizeof(int32_t) * ns));
             CKC(cudaMalloc(&c->d_vrev, sizeof(uint64_t) * kVMax * ns));
+            CKC(cudaMalloc(&c->d_vrsub, sizeof(int32_t) * kVLanes * ns));
+            CKC(cudaMemset(c->d_vrsub, 0, sizeof(int32_t) * kVLanes * ns));
             CKC(cudaMalloc(&c->d_hbuf, sizeof(double) * kVMax * ns));
             CKC(cudaMalloc(&c->d_fbuf, sizeof(double4) * kVMax * ns));
             CKC(cudaMalloc(&c->d_rho_half, sizeof(double) * ns));

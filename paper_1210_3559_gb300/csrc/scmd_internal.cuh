@@ -151,7 +151,8 @@ struct Dev {
     int32_t* vcount;     // FP64: [nslot]
     int32_t* vsub;       // FP64: [nslot][kVLanes] end of each sub-list (the entries j with j mod kVLanes = t)
     int32_t* vrcount;    // FP64: [nslot] entries of the reverse list (lower atoms that list this one)
-    uint64_t* vrev;      // FP64: [nslot][kVMax] reverse list: (lower atom << 32 | its entry's place), by atom
+    uint64_t* vrev;      // FP64: [nslot][kVMax] reverse list: (lower atom's residue and index, its entry's place)
+    int32_t* vrsub;      // FP64: [nslot][kVLanes] end of each residue class of the reverse list
     double* hbuf;        // FP64: [nslot][kVMax] density term of each listed pair, for the partner
     double4* fbuf;       // FP64: [nslot][kVMax] force on the listing atom and pair energy term of each pair
     double* rho_half;    // FP64: [nslot] the listing atom's own density sum

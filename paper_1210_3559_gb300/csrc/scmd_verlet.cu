@@ -16,19 +16,20 @@
 //     k_v_sort   : one warp per list, a bitonic sort by (j mod kVLanes, j), the atoms turned into
 //                  their slots, the ends of the kVLanes sub-lists, and each entry appended to the
 //                  partner's reverse list;
-//     k_v_rsort  : one warp per slot, its reverse list sorted by the lower atom;
+//     k_v_rsort  : one warp per slot, its reverse list sorted by (lower atom mod kVLanes, lower atom);
 //     k_v_commit : the pass coordinates in the new slot order and the reference positions;
 //   k_v_density, k_v_force : kVLanes threads per atom, thread t over sub-list t; each pair term goes
 //                  into the atom's own sum and into a buffer at the entry's place;
-//   k_v_dgather, k_v_fgather : one thread per atom, its own sum plus (or, for forces, minus) the
-//                  buffered terms of its reverse list; then rho and g, or the integrator step.
+//   k_v_dgather, k_v_fgather : kVLanes threads per atom, its own sum plus (or, for forces, minus)
+//                  the buffered terms of its reverse list; then, one warp per 32 atoms, rho and g, or
+//                  the integrator step.
 // The passes read the positions themselves (by slot).
 // Results do not depend on when the lists were built: what a thread sums is the pairs inside rcut
 // whose j is in its residue class, in ascending j (a pair outside rcut is masked to r2 = inf and
 // adds an exact zero); its partial sums are folded every kSpanV pairs inside rcut; the kVLanes
 // partials are added in a fixed tree; and the reverse list is summed in ascending order of the
-// lower atom. Resuming from a checkpoint (which rebuilds the lists) therefore reproduces an
-// uninterrupted run bit for bit, as on the other paths.
+// lower atom, split by its residue class in the same way. Resuming from a checkpoint (which rebuilds
+// the lists) therefore reproduces an uninterrupted run bit for bit, as on the other paths.
 #include "scmd_cells.cuh"
 
 namespace scmd {
@@ -195,10 +196,12 @@ __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int
         const uint32_t j = ((key & ((1u << HB) - 1)) << kVLog) | (key >> HB);
         const int sj = d.vslotof[j];
         row[e] = sj;
-        // the partner's reverse list: (this atom, this entry's place), sorted by atom in k_v_rsort
+        // the partner's reverse list: (this atom, this entry's place), sorted in k_v_rsort by (atom mod
+        // kVLanes, atom): the key's top kVLog bits hold the residue
         const int r = atomicAdd(d.vrcount + sj, 1);
         if (r < kVMax)
-            d.vrev[(size_t)sj * kVMax + r] = (ai << 32) | (uint32_t)((size_t)s * kVMax + e);
+            d.vrev[(size_t)sj * kVMax + r] = (((ai & (kVLanes - 1)) << (64 - kVLog)) | ((ai >> kVLog) << 32)) |
+                                             (uint32_t)((size_t)s * kVMax + e);
         else
             atomicOr(d.status, 4);
     }
@@ -214,8 +217,8 @@ __global__ void __launch_bounds__(kVThreads) k_v_sort(const Dev d, int cond, int
     }
 }
 
-// One warp per slot: its reverse list (the entries of lower atoms that name it) sorted by atom, a
-// bitonic sort of (atom << 32 | entry place).
+// One warp per slot: its reverse list (the entries of lower atoms that name it) sorted by (atom mod
+// kVLanes, atom), a bitonic sort of the 64-bit keys; then the end of each residue class.
 __global__ void __launch_bounds__(kVThreads) k_v_rsort(const Dev d, int cond, int k_local) {
     __shared__ uint64_t buf[kVThreads / 32][kVMax];
     pdl_launch_dependents();
@@ -246,6 +249,16 @@ __global__ void __launch_bounds__(kVThreads) k_v_rsort(const Dev d, int cond, in
             __syncwarp();
         }
     for (int e = lane; e < n; e += 32) rv[e] = b[e];
+    if (lane < kVLanes) {  // end of class `lane`: the first key of a higher class
+        const uint64_t bound = (uint64_t)(lane + 1) << (64 - kVLog);
+        int lo = 0, hi = n;
+        if (lane == kVLanes - 1) lo = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (b[mid] < bound) lo = mid + 1; else hi = mid;
+        }
+        d.vrsub[(size_t)s * kVLanes + lane] = lo;
+    }
 }
 
 // Pass coordinates in the new slot order and the positions the next displacements are measured from.
@@ -324,23 +337,33 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d) {
     if (t == 0) d.rho_half[s] = racc;
 }
 
-// One thread per slot: rho from the atom's own sum and its reverse list; g = B6 rho^-1/2.
+// kVLanes threads per slot (thread t over the reverse-list entries of lower atoms a = t mod kVLanes,
+// in ascending a), summed in a fixed tree and added to the atom's own sum; then one warp per CTA
+// finishes its 32 atoms: rho and g.
 __global__ void __launch_bounds__(kVThreads) k_v_dgather(const Dev d, int obs) {
+    __shared__ double s_r[kVThreads / kVLanes];
     pdl_launch_dependents();
     pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.nslot) return;
-    double r = d.rho_half[s];
-    const int n = min(d.vrcount[s], kVMax);
-    const uint64_t* rv = d.vrev + (size_t)s * kVMax;
-#pragma unroll 8
-    for (int k = 0; k < n; ++k) r += d.hbuf[(uint32_t)rv[k]];  // loads run ahead, the adds stay in order
-    const double rho = r * d.pot.am;
-    const int i = d.vorder[s];
+    const int a = threadIdx.x >> kVLog, t = threadIdx.x & (kVLanes - 1);
+    const int s = blockIdx.x * (kVThreads / kVLanes) + a;
+    double r = 0.0;
+    if (s < d.nslot) {
+        const int beg = t ? d.vrsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vrsub[(size_t)s * kVLanes + t];
+        const uint64_t* rv = d.vrev + (size_t)s * kVMax;
+#pragma unroll 4
+        for (int k = beg; k < end; ++k) r += d.hbuf[(uint32_t)rv[k]];
+    }
+    r = v_group_sum(r);
+    if (t == 0 && s < d.nslot) s_r[a] = d.rho_half[s] + r;
+    __syncthreads();
+    const int sl = blockIdx.x * (kVThreads / kVLanes) + threadIdx.x;
+    if (threadIdx.x >= 32 || sl >= d.nslot) return;
+    const double rho = s_r[threadIdx.x] * d.pot.am;
+    const int i = d.vorder[sl];
     d.rho[i] = rho;
-    double4 p = reinterpret_cast<const double4*>(d.vhi)[s];
+    double4 p = reinterpret_cast<const double4*>(d.vhi)[sl];
     p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
-    reinterpret_cast<double4*>(d.vposg)[s] = p;
+    reinterpret_cast<double4*>(d.vposg)[sl] = p;
     if (obs) d.eatom[2 * i] = -d.pot.eps * d.pot.c * sqrt(rho);
 }
 
@@ -404,36 +427,52 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d) {
     if (t == 0) d.fhalf[s] = make_double4(gx, gy, gz, Ep);
 }
 
-// One thread per slot: the force (and pair energy) from the atom's own sum and its reverse list,
-// less each lower partner's term (Newton's third law), then the per-atom work of the mode:
-// 0 forces; 1 forces and per-atom pair energies; 2 MD step (second half kick, per-atom observables
-// if due, then the first half of the next step unless last or Berendsen).
+// kVLanes threads per slot: the force (and pair energy) terms of the reverse list, by residue class
+// of the lower atom as in k_v_dgather, subtracted from (added to) the atom's own sums (Newton's third
+// law); then one warp per CTA does the per-atom work of the mode for its 32 atoms: 0 forces;
+// 1 forces and per-atom pair energies; 2 MD step (second half kick, per-atom observables if due,
+// then the first half of the next step unless last or Berendsen).
 template <int ENERGY>
 __global__ void __launch_bounds__(kVThreads) k_v_fgather(const Dev d, int mode, int k_local, int last) {
+    __shared__ double4 s_f[kVThreads / kVLanes];
     pdl_launch_dependents();
     pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.nslot) return;
-    const double4 h = d.fhalf[s];
-    double Fx = h.x, Fy = h.y, Fz = h.z, Ep = h.w;
-    const int n = min(d.vrcount[s], kVMax);
-    const uint64_t* rv = d.vrev + (size_t)s * kVMax;
-#pragma unroll 8
-    for (int k = 0; k < n; ++k) {  // loads run ahead, the subtractions stay in order
-        const double4 u = d.fbuf[(uint32_t)rv[k]];
-        Fx -= u.x;
-        Fy -= u.y;
-        Fz -= u.z;
-        if (ENERGY) Ep += u.w;
+    const int a = threadIdx.x >> kVLog, t = threadIdx.x & (kVLanes - 1);
+    const int s = blockIdx.x * (kVThreads / kVLanes) + a;
+    double ux = 0.0, uy = 0.0, uz = 0.0, ue = 0.0;
+    if (s < d.nslot) {
+        const int beg = t ? d.vrsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vrsub[(size_t)s * kVLanes + t];
+        const uint64_t* rv = d.vrev + (size_t)s * kVMax;
+#pragma unroll 4
+        for (int k = beg; k < end; ++k) {
+            const double4 u = d.fbuf[(uint32_t)rv[k]];
+            ux += u.x;
+            uy += u.y;
+            uz += u.z;
+            if (ENERGY) ue += u.w;
+        }
     }
-    const int i = d.vorder[s];
+    ux = v_group_sum(ux);
+    uy = v_group_sum(uy);
+    uz = v_group_sum(uz);
+    if (ENERGY) ue = v_group_sum(ue);
+    if (t == 0 && s < d.nslot) {
+        const double4 h = d.fhalf[s];
+        s_f[a] = make_double4(h.x - ux, h.y - uy, h.z - uz, h.w + ue);
+    }
+    __syncthreads();
+    const int sl = blockIdx.x * (kVThreads / kVLanes) + threadIdx.x;
+    if (threadIdx.x >= 32 || sl >= d.nslot) return;
+    const double4 F = s_f[threadIdx.x];
+    const double Fx = F.x, Fy = F.y, Fz = F.z;
+    const int i = d.vorder[sl];
     const int np = d.npad;
     double* fo = reinterpret_cast<double*>(d.f);
     fo[i] = Fx;
     fo[np + i] = Fy;
     fo[2 * np + i] = Fz;
     if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
-    if (ENERGY) d.eatom[2 * i + 1] = Ep;
+    if (ENERGY) d.eatom[2 * i + 1] = F.w;
     if (mode != 2) return;
     const Run& r = *d.run;
     const int cl = d.cl_of_group[i >> 5];
@@ -474,14 +513,16 @@ cudaError_t launch_v_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s
 static int v_pass_grid(const Dev& d) {
     return (int)(((int64_t)d.nslot * kVLanes + kVThreads - 1) / kVThreads);
 }
-static int v_atom_grid(const Dev& d) { return (d.nslot + kVThreads - 1) / kVThreads; }
+static int v_gather_grid(const Dev& d) {  // kVLanes threads per slot
+    return (d.nslot + kVThreads / kVLanes - 1) / (kVThreads / kVLanes);
+}
 
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s, int k_local) {
     if (d.prec == 1) return launch_q_density(d, obs, k_local, s);
     cudaError_t e = d.pot.special ? launch_ex(k_v_density<1>, v_pass_grid(d), kVThreads, 0, 0, s, d)
                                   : launch_ex(k_v_density<0>, v_pass_grid(d), kVThreads, 0, 0, s, d);
     if (e != cudaSuccess) return e;
-    return launch_ex(k_v_dgather, v_atom_grid(d), kVThreads, 0, 0, s, d, obs);
+    return launch_ex(k_v_dgather, v_gather_grid(d), kVThreads, 0, 0, s, d, obs);
 }
 
 template <int ENERGY>
@@ -489,7 +530,7 @@ static cudaError_t v_force_e(const Dev& d, int mode, int k, int last, cudaStream
     cudaError_t e = d.pot.special ? launch_ex(k_v_force<1, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d)
                                   : launch_ex(k_v_force<0, ENERGY>, v_pass_grid(d), kVThreads, 0, 0, s, d);
     if (e != cudaSuccess) return e;
-    return launch_ex(k_v_fgather<ENERGY>, v_atom_grid(d), kVThreads, 0, 0, s, d, mode, k, last);
+    return launch_ex(k_v_fgather<ENERGY>, v_gather_grid(d), kVThreads, 0, 0, s, d, mode, k, last);
 }
 
 cudaError_t launch_v_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
