@@ -158,3 +158,22 @@ def test_verlet_matches_cells_bitwise_free(scmd):
     Eb, Fb = scmd.md_energy_forces(b)
     assert rel_force_err(Fa, Fb) <= TOL[MIXED]["eF"]
     assert abs(Ea[0] - Eb[0]) <= TOL[MIXED]["E"] * abs(Eb[0])
+
+
+def test_verlet_list_overflow_is_reported(scmd):
+    """A dense simple-cubic blob (spacing 1.6 A): each cell holds fewer than its 256 atoms, but the
+    atom at the centre, listed first, has ~960 higher-indexed partners within rcut + skin, more than
+    a list holds (512). The overflow is detected on the device and reported; nothing is written out
+    of bounds (a full list drops the extra entries), and the GPU stays usable."""
+    g = (np.arange(12) - 5.5) * 1.6
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    blob = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    blob = blob[np.argsort(np.linalg.norm(blob, axis=1), kind="stable")]  # the centre atoms first
+    with pytest.raises(scmd.ScmdError) as e:
+        make(scmd, [len(blob)], blob, prec=FP64, rcut=RC, path=VERLET)
+    assert e.value.status == scmd.MD_ERR_STATE
+    assert "neighbour list" in scmd.md_last_error()
+    pos = lattice(700, 36)
+    ctx = make(scmd, [700], pos, prec=FP64, rcut=RC, path=VERLET)
+    E, F = scmd.md_energy_forces(ctx)
+    check_cluster(F, E[0], scmd.md_get_density(ctx), pos, FP64, rcut=RC)
