@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d) {
 }
 
 // kVLanes threads per slot (thread t over the reverse-list entries of lower atoms a = t mod kVLanes,
-// in ascending a), summed in a fixed tree and added to the atom's own sum; then one warp per CTA
-// finishes its 32 atoms: rho and g.
+// in ascending a), summed in a fixed tree and added to the atom's own sum; then the CTA's first
+// threads finish its atoms, one each: rho and g.
 __global__ void __launch_bounds__(kVThreads) k_v_dgather(const Dev d, int obs) {
     __shared__ double s_r[kVThreads / kVLanes];
     pdl_launch_dependents();
@@ -356,8 +356,8 @@ __global__ void __launch_bounds__(kVThreads) k_v_dgather(const Dev d, int obs) {
     r = v_group_sum(r);
     if (t == 0 && s < d.nslot) s_r[a] = d.rho_half[s] + r;
     __syncthreads();
-    const int sl = blockIdx.x * (kVThreads / kVLanes) + threadIdx.x;
-    if (threadIdx.x >= 32 || sl >= d.nslot) return;
+    const int sl = blockIdx.x * (kVThreads / kVLanes) + threadIdx.x;  // one thread per atom of the CTA
+    if (threadIdx.x >= kVThreads / kVLanes || sl >= d.nslot) return;
     const double rho = s_r[threadIdx.x] * d.pot.am;
     const int i = d.vorder[sl];
     d.rho[i] = rho;
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d) {
 
 // kVLanes threads per slot: the force (and pair energy) terms of the reverse list, by residue class
 // of the lower atom as in k_v_dgather, subtracted from (added to) the atom's own sums (Newton's third
-// law); then one warp per CTA does the per-atom work of the mode for its 32 atoms: 0 forces;
+// law); then the CTA's first threads do the per-atom work of the mode, one atom each: 0 forces;
 // 1 forces and per-atom pair energies; 2 MD step (second half kick, per-atom observables if due,
 // then the first half of the next step unless last or Berendsen).
 template <int ENERGY>
@@ -461,8 +461,8 @@ __global__ void __launch_bounds__(kVThreads) k_v_fgather(const Dev d, int mode, 
         s_f[a] = make_double4(h.x - ux, h.y - uy, h.z - uz, h.w + ue);
     }
     __syncthreads();
-    const int sl = blockIdx.x * (kVThreads / kVLanes) + threadIdx.x;
-    if (threadIdx.x >= 32 || sl >= d.nslot) return;
+    const int sl = blockIdx.x * (kVThreads / kVLanes) + threadIdx.x;  // one thread per atom of the CTA
+    if (threadIdx.x >= kVThreads / kVLanes || sl >= d.nslot) return;
     const double4 F = s_f[threadIdx.x];
     const double Fx = F.x, Fy = F.y, Fz = F.z;
     const int i = d.vorder[sl];
