@@ -255,7 +255,7 @@ md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* 
                          double* pairs);
 
 /* Number of GPU kernels issued per md_step step (all pairs: 2, cells: 5,
- * neighbour lists: 9 in MIXED, 12 in FP64, plus one Berendsen kernel, two with
+ * neighbour lists: 8 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
  * cells or lists, and the observable kernels of recorded steps) and per graph
  * replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);

@@ -92,7 +92,9 @@ struct md_ctx {
     bool msd_ref = false;
     // neighbour-list path
     int32_t *d_vlist = nullptr, *d_vcount = nullptr, *d_vsub = nullptr, *d_vorder = nullptr, *d_vslotof = nullptr;
-    int32_t *d_vslot = nullptr, *d_vrcount = nullptr, *d_vrsub = nullptr;
+    int32_t *d_vslot = nullptr, *d_vrcount = nullptr, *d_vrsub = nullptr, *d_vcn = nullptr;
+    int2* d_vcl = nullptr;
+    uint8_t* d_vflag = nullptr;
     uint64_t* d_vrev = nullptr;
     double *d_hbuf = nullptr, *d_rho_half = nullptr;
     double4 *d_fbuf = nullptr, *d_fhalf = nullptr;
@@ -202,6 +204,9 @@ void fill_dev(md_ctx* c) {
     d.vrcount = c->d_vrcount;
     d.vrev = c->d_vrev;
     d.vrsub = c->d_vrsub;
+    d.vcl = c->d_vcl;
+    d.vcn = c->d_vcn;
+    d.vflag = c->d_vflag;
     d.hbuf = c->d_hbuf;
     d.fbuf = c->d_fbuf;
     d.rho_half = c->d_rho_half;
@@ -466,6 +471,7 @@ void free_all(md_ctx* c) {
                     c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi,
                     c->d_q_n, c->d_cell_base, c->d_q_cell, c->d_q_list, c->d_q_count, c->d_q_ref, c->d_q_box,
                     c->d_vrcount, c->d_vrev, c->d_vrsub, c->d_hbuf, c->d_fbuf, c->d_rho_half, c->d_fhalf,
+                    c->d_vcl, c->d_vcn, c->d_vflag,
                     c->d_vposg, c->d_vxref, c->d_vdmax,
                     c->sb.com, c->sb.core, c->sb.ncore, c->sb.hist, c->sb.ref, c->sb.ref_com, c->sb.sel, c->sb.msd,
                     c->sb.nsel, c->sb.nb, c->sb.nnb, c->sb.cls, c->sb.counts, c->sb.capped};
@@ -839,6 +845,10 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
             CKC(cudaMalloc(&c->d_vrcount, sizeof(int32_t) * ns));
             CKC(cudaMalloc(&c->d_vrev, sizeof(uint64_t) * kVMax * ns));
             CKC(cudaMalloc(&c->d_vrsub, sizeof(int32_t) * kVLanes * ns));
+            CKC(cudaMalloc(&c->d_vcl, sizeof(int2) * kVMax * ns));
+            CKC(cudaMalloc(&c->d_vcn, sizeof(int32_t) * ns));
+            CKC(cudaMalloc(&c->d_vflag, (size_t)kVMax * ns));
+            CKC(cudaMemset(c->d_vflag, 0, (size_t)kVMax * ns));
             CKC(cudaMemset(c->d_vrsub, 0, sizeof(int32_t) * kVLanes * ns));
             CKC(cudaMalloc(&c->d_hbuf, sizeof(double) * kVMax * ns));
             CKC(cudaMalloc(&c->d_fbuf, sizeof(double4) * kVMax * ns));
@@ -1356,9 +1366,9 @@ md_status md_get_path(const md_ctx* c, int32_t* path) {
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
     // lists: positions, cell build (3), list build (MIXED scan, order, list; FP64 build, sort, reverse sort,
-    // commit), passes (MIXED 2; FP64 2 + 2 gathers)
+    // commit), passes (MIXED 2; FP64 compaction, 2 passes, 2 gathers)
     // (MIXED: the position kernel runs once per chunk, and every step with Berendsen)
-    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 8 : 12) : (c->path == 1 ? 5 : 2);
+    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 8 : 13) : (c->path == 1 ? 5 : 2);
     if (per_chunk) *per_chunk = c->path == 2 && c->nqmax > 0 ? 4 : 3;
     return MD_OK;
 }

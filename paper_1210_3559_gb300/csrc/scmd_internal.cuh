@@ -155,6 +155,9 @@ struct Dev {
     int32_t* vrsub;      // FP64: [nslot][kVLanes] end of each residue class of the reverse list
     double* hbuf;        // FP64: [nslot][kVMax] density term of each listed pair, for the partner
     double4* fbuf;       // FP64: [nslot][kVMax] force on the listing atom and pair energy term of each pair
+    int2* vcl;           // FP64: [nslot][kVMax] entries inside rcut this step, in list order: (partner, place)
+    int32_t* vcn;        // FP64: [nslot] their number
+    uint8_t* vflag;      // FP64: [nslot][kVMax] 1 where the list entry's pair is inside rcut this step
     double* rho_half;    // FP64: [nslot] the listing atom's own density sum
     double4* fhalf;      // FP64: [nslot] the listing atom's own force and pair-energy sums
     int32_t* vorder;     // [nslot] atom of each slot (MIXED: -1 for the empty slots that pad cells to quads)

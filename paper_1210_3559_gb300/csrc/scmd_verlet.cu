@@ -18,17 +18,20 @@
 //                  partner's reverse list;
 //     k_v_rsort  : one warp per slot, its reverse list sorted by (lower atom mod kVLanes, lower atom);
 //     k_v_commit : the pass coordinates in the new slot order and the reference positions;
-//   k_v_density, k_v_force : kVLanes threads per atom, thread t over sub-list t; each pair term goes
-//                  into the atom's own sum and into a buffer at the entry's place;
+//   k_v_compact : one warp per atom, every step: the list entries inside rcut now, in list order;
+//   k_v_density, k_v_force : kVLanes threads per atom, thread t over compacted entries t, t + kVLanes,
+//                  ...; each pair term goes into the atom's own sum and into a buffer at the entry's
+//                  place;
 //   k_v_dgather, k_v_fgather : kVLanes threads per atom, its own sum plus (or, for forces, minus)
 //                  the buffered terms of its reverse list; then, one warp per 32 atoms, rho and g, or
 //                  the integrator step.
 // The passes read the positions themselves (by slot).
-// Results do not depend on when the lists were built: what a thread sums is the pairs inside rcut
-// whose j is in its residue class, in ascending j (a pair outside rcut is masked to r2 = inf and
-// adds an exact zero); its partial sums are folded every kSpanV pairs inside rcut; the kVLanes
-// partials are added in a fixed tree; and the reverse list is summed in ascending order of the
-// lower atom, split by its residue class in the same way. Resuming from a checkpoint (which rebuilds
+// Results do not depend on when the lists were built: the compacted entries are the pairs inside
+// rcut in the order of the keys (j mod kVLanes, j), a function of the positions alone, so which
+// thread takes an entry and in which order is fixed too; partial sums are folded every kSpanV
+// entries; the kVLanes partials are added in a fixed tree; and the reverse list is summed in
+// ascending order of the lower atom, split by its residue class in the same way (entries outside
+// rcut this step are skipped by their flag). Resuming from a checkpoint (which rebuilds
 // the lists) therefore reproduces an uninterrupted run bit for bit, as on the other paths.
 #include "scmd_cells.cuh"
 
@@ -286,10 +289,48 @@ __device__ __forceinline__ double v_group_sum(double v) {
 }
 
 // Half lists: atom i lists its partners j > i only. A pass computes each pair once; the term goes
-// into i's own sum (registers, by residue class of j in ascending j as before) and is written at the
-// entry's place for j. The gather kernels then add, for every atom, the terms of its reverse list
-// in ascending order of the lower atom. Both orders are fixed by the positions alone, so the passes
-// still do not depend on when the lists were built.
+// into i's own sum (registers) and is written at the entry's place for j. The gather kernels then
+// add, for every atom, the terms of its reverse list in ascending order of the lower atom. Both
+// orders are fixed by the positions alone, so the passes still do not depend on when the lists were
+// built.
+
+// One warp per atom, every MD step: the entries of its half list whose pair lies inside rcut now, in
+// list order (a function of the positions alone), with a flag per list entry for the gathers.
+__global__ void __launch_bounds__(kVThreads) k_v_compact(const Dev d) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= d.nslot) return;
+    const double4* vp = reinterpret_cast<const double4*>(d.vhi);
+    const double4 pi = vp[s];
+    const double rc2 = d.pot.rcut2;
+    const int n = d.vcount[s];
+    const int* lst = d.vlist + (size_t)s * kVMax;
+    int2* out = d.vcl + (size_t)s * kVMax;
+    uint8_t* flag = d.vflag + (size_t)s * kVMax;
+    int m = 0;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+        const int e = e0 + lane;
+        bool in = false;
+        int q = 0;
+        if (e < n) {
+            q = lst[e];
+            const double4 pj = vp[q];
+            const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            in = fma(dx, dx, fma(dy, dy, dz * dz)) < rc2;
+            flag[e] = in ? 1 : 0;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        if (in) out[m + __popc(b & ((1u << lane) - 1u))] = make_int2(q, e);
+        m += __popc(b);
+    }
+    if (lane == 0) d.vcn[s] = m;
+}
+
+// kVLanes threads per atom over its compacted entries (thread t takes entries t, t + kVLanes, ...),
+// each pair inside rcut by construction. Each term goes into the atom's own sum and, for the
+// partner, at the entry's place in the list.
 template <int SPECIAL>
 __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d) {
     pdl_launch_dependents();
@@ -299,20 +340,19 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d) {
     if (s >= d.nslot) return;  // whole atoms leave together
     const double4* vp = reinterpret_cast<const double4*>(d.vhi);
     const double4 pi = vp[s];
-    const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
-    const double rc2 = d.pot.rcut2, shm = d.pot.shift ? d.pot.shm : 0.0;
+    const int n = d.vcn[s];
+    const double shm = d.pot.shift ? d.pot.shm : 0.0;
     const int mexp = d.pot.m;
-    const int* lst = d.vlist + (size_t)s * kVMax;
+    const int2* cl = d.vcl + (size_t)s * kVMax;
     double* hb = d.hbuf + (size_t)s * kVMax;
     double racc = 0.0, tacc = 0.0;
-    int cnt = 0, nfold = 0;  // pairs inside rcut: nfold * kSpanV + cnt
+    int cnt = 0, mine = 0;
 #pragma unroll 4
-    for (int e = beg; e < end; ++e) {
-        const double4 pj = vp[lst[e]];
+    for (int k = t; k < n; k += kVLanes) {
+        const int2 qe = cl[k];
+        const double4 pj = vp[qe.x];
         const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const bool in = r2 < rc2;
-        r2 = in ? r2 : big<double>();
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         double term;
         if (SPECIAL) {
             const double inv = inv_r2(r2);
@@ -322,17 +362,16 @@ __global__ void __launch_bounds__(kVThreads) k_v_density(const Dev d) {
             term = rpow(ir * ir, ir, mexp);
         }
         tacc += term;
-        hb[e] = in ? term - shm : 0.0;
-        cnt += in;
-        if (cnt == kSpanV) {
+        hb[qe.y] = term - shm;
+        ++mine;
+        if (++cnt == kSpanV) {
             racc += tacc;
             tacc = 0.0;
             cnt = 0;
-            ++nfold;
         }
     }
     racc += tacc;
-    racc -= (double)(nfold * kSpanV + cnt) * shm;
+    racc -= (double)mine * shm;
     racc = v_group_sum(racc);
     if (t == 0) d.rho_half[s] = racc;
 }
@@ -351,7 +390,10 @@ __global__ void __launch_bounds__(kVThreads) k_v_dgather(const Dev d, int obs) {
         const int beg = t ? d.vrsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vrsub[(size_t)s * kVLanes + t];
         const uint64_t* rv = d.vrev + (size_t)s * kVMax;
 #pragma unroll 4
-        for (int k = beg; k < end; ++k) r += d.hbuf[(uint32_t)rv[k]];
+        for (int k = beg; k < end; ++k) {  // entries outside rcut this step carry stale terms: skipped
+            const uint32_t pos = (uint32_t)rv[k];
+            if (d.vflag[pos]) r += d.hbuf[pos];
+        }
     }
     r = v_group_sum(r);
     if (t == 0 && s < d.nslot) s_r[a] = d.rho_half[s] + r;
@@ -376,20 +418,19 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d) {
     if (s >= d.nslot) return;  // whole atoms leave together
     const double4* vp = reinterpret_cast<const double4*>(d.vposg);
     const double4 pi = vp[s];
-    const int beg = t ? d.vsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vsub[(size_t)s * kVLanes + t];
-    const double A = d.pot.A9, rc2 = d.pot.rcut2, shn = d.pot.shift ? d.pot.shn : 0.0;
+    const int n = d.vcn[s];
+    const double A = d.pot.A9, shn = d.pot.shift ? d.pot.shn : 0.0;
     const int nexp = d.pot.n, mexp = d.pot.m;
-    const int* lst = d.vlist + (size_t)s * kVMax;
+    const int2* cl = d.vcl + (size_t)s * kVMax;
     double4* fb = d.fbuf + (size_t)s * kVMax;
     double fx = 0.0, fy = 0.0, fz = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, se = 0.0, ea = 0.0;
-    int cnt = 0, nfold = 0;  // pairs inside rcut: nfold * kSpanV + cnt
+    int cnt = 0, mine = 0;
 #pragma unroll 4
-    for (int e = beg; e < end; ++e) {
-        const double4 pj = vp[lst[e]];
+    for (int k = t; k < n; k += kVLanes) {
+        const int2 qe = cl[k];
+        const double4 pj = vp[qe.x];
         const double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const bool in = r2 < rc2;
-        r2 = in ? r2 : big<double>();
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double ir = inv_r(r2);
         const double inv = ir * ir;
         double coef, rn;
@@ -407,9 +448,9 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d) {
         sy += uy;
         sz += uz;
         if (ENERGY) se += rn;
-        fb[e] = make_double4(ux, uy, uz, ENERGY ? (in ? rn - shn : 0.0) : 0.0);
-        cnt += in;
-        if (cnt == kSpanV) {
+        fb[qe.y] = make_double4(ux, uy, uz, ENERGY ? rn - shn : 0.0);
+        ++mine;
+        if (++cnt == kSpanV) {
             fx += sx;
             fy += sy;
             fz += sz;
@@ -419,11 +460,10 @@ __global__ void __launch_bounds__(kVThreads) k_v_force(const Dev d) {
                 se = 0.0;
             }
             cnt = 0;
-            ++nfold;
         }
     }
     const double gx = v_group_sum(fx + sx), gy = v_group_sum(fy + sy), gz = v_group_sum(fz + sz);
-    const double Ep = ENERGY ? v_group_sum(ea + se - (double)(nfold * kSpanV + cnt) * shn) : 0.0;
+    const double Ep = ENERGY ? v_group_sum(ea + se - (double)mine * shn) : 0.0;
     if (t == 0) d.fhalf[s] = make_double4(gx, gy, gz, Ep);
 }
 
@@ -444,8 +484,10 @@ __global__ void __launch_bounds__(kVThreads) k_v_fgather(const Dev d, int mode, 
         const int beg = t ? d.vrsub[(size_t)s * kVLanes + t - 1] : 0, end = d.vrsub[(size_t)s * kVLanes + t];
         const uint64_t* rv = d.vrev + (size_t)s * kVMax;
 #pragma unroll 4
-        for (int k = beg; k < end; ++k) {
-            const double4 u = d.fbuf[(uint32_t)rv[k]];
+        for (int k = beg; k < end; ++k) {  // entries outside rcut this step carry stale terms: skipped
+            const uint32_t pos = (uint32_t)rv[k];
+            if (!d.vflag[pos]) continue;
+            const double4 u = d.fbuf[pos];
             ux += u.x;
             uy += u.y;
             uz += u.z;
@@ -519,8 +561,10 @@ static int v_gather_grid(const Dev& d) {  // kVLanes threads per slot
 
 cudaError_t launch_v_density(const Dev& d, int obs, cudaStream_t s, int k_local) {
     if (d.prec == 1) return launch_q_density(d, obs, k_local, s);
-    cudaError_t e = d.pot.special ? launch_ex(k_v_density<1>, v_pass_grid(d), kVThreads, 0, 0, s, d)
-                                  : launch_ex(k_v_density<0>, v_pass_grid(d), kVThreads, 0, 0, s, d);
+    cudaError_t e = launch_ex(k_v_compact, (d.nslot + kVThreads / 32 - 1) / (kVThreads / 32), kVThreads, 0, 0, s, d);
+    if (e != cudaSuccess) return e;
+    e = d.pot.special ? launch_ex(k_v_density<1>, v_pass_grid(d), kVThreads, 0, 0, s, d)
+                      : launch_ex(k_v_density<0>, v_pass_grid(d), kVThreads, 0, 0, s, d);
     if (e != cudaSuccess) return e;
     return launch_ex(k_v_dgather, v_gather_grid(d), kVThreads, 0, 0, s, d, obs);
 }
