@@ -177,3 +177,36 @@ def test_verlet_list_overflow_is_reported(scmd):
     ctx = make(scmd, [700], pos, prec=FP64, rcut=RC, path=VERLET)
     E, F = scmd.md_energy_forces(ctx)
     check_cluster(F, E[0], scmd.md_get_density(ctx), pos, FP64, rcut=RC)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_verlet_chunking_does_not_change_the_trajectory(scmd, prec):
+    """Graph chunks of 7 and of 60 steps give the same trajectory bit for bit. In MIXED the position
+    kernel runs only at a chunk's first step (the force pass that moves the atoms writes their offsets
+    within a chunk), so this checks that both routes write the same offsets and displacement record."""
+    pos = inputs.fcc_sphere(900)
+    vel = inputs.maxwell_boltzmann(pos, inputs.masses(900), 2500.0, seed=13)
+    th = scmd.thermostat(scmd.MD_LANGEVIN, 2500.0, 2500.0, gamma_per_ps=1.0, seed=14)
+    out = []
+    for chunk in (7, 60):
+        ctx = make(scmd, [900], pos, vel, prec=prec, rcut=RC, path=VERLET, graph_chunk=chunk)
+        scmd.md_step(ctx, 120, 2.0, th)
+        out.append(scmd.md_get_state(ctx)[:2])
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_verlet_many_clusters(scmd, prec):
+    """30 clusters of 1 to 500 atoms in one context on the lists: every cluster against the oracle."""
+    rng = np.random.default_rng(15)
+    sizes = [int(x) for x in rng.integers(1, 501, 30)]
+    parts = [inputs.jitter(inputs.fcc_sphere(n), 0.03, 40 + b) if n > 1 else np.zeros((1, 3))
+             for b, n in enumerate(sizes)]
+    pos = np.concatenate([p + 70.0 * b for b, p in enumerate(parts)])
+    ctx = make(scmd, sizes, pos, prec=prec, rcut=RC, path=VERLET)
+    E, F = scmd.md_energy_forces(ctx)
+    rho = scmd.md_get_density(ctx)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for b in range(len(sizes)):
+        s, e = off[b], off[b + 1]
+        check_cluster(F[s:e], E[b], rho[s:e], pos[s:e], prec, rcut=RC)
