@@ -313,6 +313,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+// CTA barrier 1 over the first n threads (n a multiple of 32); barrier 0 is __syncthreads.
+__device__ __forceinline__ void bar_sync_first(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
 
 // The work item of this CTA: a table entry, or (one cluster per context) computed in place.
 template <int BI> __device__ __forceinline__ Item load_item(const Dev& d, const Item* items, int C) {

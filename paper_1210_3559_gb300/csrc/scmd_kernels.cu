@@ -356,6 +356,17 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
             }
         }
     }
+    // MIXED steps that go on to the next step: the step coefficients for the split epilogue
+    // below, loaded here so that their latency hides behind the reductions.
+    int kind0 = 2;
+    double c_h = 0.0, c_hk = 0.0, c_c1 = 0.0, c_dt = 0.0;
+    if (PREC == 1 && integrate && !last && rank == 0) {
+        kind0 = run->kind;
+        c_h = run->h;
+        c_hk = run->hk;
+        c_c1 = run->c1;
+        c_dt = run->dt;
+    }
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int sidx = warp * BI + q * 32 + lane;
@@ -384,26 +395,81 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     }
     cluster_arrive_release();
     cluster_wait();
-    if (!owner) return;
+    // Split epilogue (MIXED, NVE or Langevin, not the chunk's last step). FP64 runs at 1/64 of
+    // the FP32 rate here and a warp instruction holds its sub-partition's FP64 unit for ~68
+    // cycles, so one warp integrating all three components of its 32 atoms is ~27 FP64
+    // instructions in a row at the end of the pass. The components are independent, so each of
+    // up to 3 * IPT warps (on different sub-partitions) takes one component of 32 atoms, with
+    // the same operations in the same order as the one-warp form below.
+    constexpr int NT = 3 * IPT;
+    const int NW = W < NT ? W : NT;
+    const bool split = PREC == 1 && integrate && !last && kind0 != 2;
+    if (!owner && !(split && rank == 0 && warp < NW)) return;
     R Fx = R(0), Fy = R(0), Fz = R(0);
     double Ep = 0.0;
-    for (int r = 0; r < C; ++r) {
-        const R* rf = inboxf + 3 * (r * BI + threadIdx.x);
-        Fx += rf[0];
-        Fy += rf[1];
-        Fz += rf[2];
-        if (ENERGY) Ep += inboxe[r * BI + threadIdx.x];
-    }
     const int i = io, np = d.npad;
     const bool real = oreal;
-    R* fo = reinterpret_cast<R*>(d.f);
-    if (real) {
-        fo[i] = Fx;
-        fo[np + i] = Fy;
-        fo[2 * np + i] = Fz;
-        if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
-    }
     const int group = i >> 5;
+    if (owner) {
+        for (int r = 0; r < C; ++r) {
+            const R* rf = inboxf + 3 * (r * BI + threadIdx.x);
+            Fx += rf[0];
+            Fy += rf[1];
+            Fz += rf[2];
+            if (ENERGY) Ep += inboxe[r * BI + threadIdx.x];
+        }
+        R* fo = reinterpret_cast<R*>(d.f);
+        if (real) {
+            fo[i] = Fx;
+            fo[np + i] = Fy;
+            fo[2 * np + i] = Fz;
+            if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+        }
+    }
+    if (split) {
+        R* fsh = redf;  // free again after the cluster barrier: F by component, [3][BI]
+        const EpiSlot* slots = reinterpret_cast<const EpiSlot*>(slot0);
+        if (owner) {
+            fsh[threadIdx.x] = Fx;
+            fsh[BI + threadIdx.x] = Fy;
+            fsh[2 * BI + threadIdx.x] = Fz;
+            cp_async_wait_all();
+            if (ENERGY) {  // observables are due at step + 1: the owner warp sums them as below
+                const double hs = slot->hs, m = real ? slot->m : 0.0;
+                const double vx = fma(hs, (double)Fx, slot->v[0]), vy = fma(hs, (double)Fy, slot->v[1]),
+                             vz = fma(hs, (double)Fz, slot->v[2]);
+                const double e = warp_sum(real ? Ep : 0.0);
+                if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
+                obs_position_partials(d, group, real, m, slot->x[0], slot->x[1], slot->x[2], lane);
+                obs_velocity_partials(d, group, real, m, slot->x[0], slot->x[1], slot->x[2], vx, vy, vz, lane);
+            }
+        }
+        bar_sync_first(NW * 32);  // F and every owner's epilogue slot are in shared memory
+        float* mirf = reinterpret_cast<float*>(d.mirror);
+        for (int task = warp; task < NT; task += NW) {
+            const int c = task / IPT, t = (task - c * IPT) * 32 + lane;
+            if (t >= it.ni) continue;
+            const int ia = it.i0 + t;
+            const EpiSlot* s = slots + t;
+            const double F = (double)fsh[c * BI + t];
+            const double hs = s->hs;
+            const double vv = fma(hs, F, s->v[c]);  // end of this step (second half kick)
+            double u = fma(hs, F, vv);              // next step: first half kick
+            double x;
+            if (kind0 == 1) {  // A O A
+                const double nzc = (double)(s->sig0 * reinterpret_cast<const float*>(&s->nz)[c]);
+                x = fma(c_hk, u, fma(c_h, nzc, s->x[c]));
+                u = fma(c_c1, u, nzc);
+            } else {  // A A
+                x = fma(c_dt, u, s->x[c]);
+            }
+            mirf[4 * ia + c] = (float)(x - s->o[c]);  // the .w of the mirror stays 0
+            d.v[c * np + ia] = u;
+            d.x[c * np + ia] = x;
+            if (!(finite_bits(x) && finite_bits(u))) atomicOr(d.status, 1);
+        }
+        return;
+    }
     if (mode == 1) {
         // fresh evaluation: all observable partials at the current (x, v)
         const double mm = real ? d.mass[i] : 0.0;
