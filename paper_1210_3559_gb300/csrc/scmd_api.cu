@@ -691,6 +691,7 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     P.ecoef = 0.5 * P.eps * std::pow(P.a, P.n);
     P.A9f = (float)P.A9;
     P.rcut2f = (float)P.rcut2;
+    P.gsf = (float)(P.B6 / std::sqrt(P.am));
     P.special = (P.n == 9 && P.m == 6) ? 1 : 0;
     P.shift = prm->cutoff_shift;
     P.shm = P.shift ? std::pow(P.rcut, -(double)P.m) : 0.0;

@@ -278,6 +278,23 @@ __device__ __forceinline__ f2sum f2_add(f2sum a, f2sum b) {
     const float hi = t.hi + lo;
     return {hi, lo - (hi - t.hi)};
 }
+// Sum of K (a power of two) double-float partials p[0], p[s], ..., p[(K - 1) s] as a balanced
+// tree: log2(K) dependent additions instead of K - 1, in an order fixed by K.
+template <int K> __device__ __forceinline__ f2sum f2_tree(const f2sum* p, int s) {
+    if constexpr (K == 1)
+        return p[0];
+    else
+        return f2_add(f2_tree<K / 2>(p, s), f2_tree<K / 2>(p + (K / 2) * s, s));
+}
+__device__ __forceinline__ f2sum f2_tree_sum(const f2sum* p, int k, int s) {  // k in {1, 2, 4, 8, 16}
+    switch (k) {
+        case 16: return f2_tree<16>(p, s);
+        case 8: return f2_tree<8>(p, s);
+        case 4: return f2_tree<4>(p, s);
+        case 2: return f2_tree<2>(p, s);
+        default: return p[0];
+    }
+}
 // Pin a loaded value in a register at this point: the load must complete here, so the
 // compiler cannot sink it to its use after the pair loop (where its latency would show).
 __device__ __forceinline__ void pin(double v) { asm volatile("" ::"d"(v)); }

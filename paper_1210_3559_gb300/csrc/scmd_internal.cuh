@@ -72,6 +72,7 @@ struct Pot {
     double am;   // a^m                  (density scale)
     double ecoef;// 1/2 eps a^n          (pair energy scale)
     float A9f, rcut2f;
+    float gsf;   // B6 / sqrt(a^m) in FP32: g_i = gsf * (sum_j r_ij^-m)^-1/2 without forming rho
     int special; // 1 when (n, m) = (9, 6): compile-time exponents
     int shift;   // 1: every pair term inside rcut less its value at rcut
     double shm;  // rcut^-m: the density shift per pair (rho = a^m (sum r^-m - shm * pairs))

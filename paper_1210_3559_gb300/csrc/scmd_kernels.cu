@@ -153,8 +153,7 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     cluster_wait();  // every CTA of the cluster has started: its shared memory may be written
     if (threadIdx.x < BI) {
         if (PREC == 1) {
-            f2sum s2 = red2[threadIdx.x];
-            for (int w = 1; w < W; ++w) s2 = f2_add(s2, red2[w * BI + threadIdx.x]);
+            const f2sum s2 = f2_tree_sum(red2 + threadIdx.x, W, BI);
             *cluster.map_shared_rank(inbox2 + rank * BI + threadIdx.x, 0) = s2;
         } else {
             double s = 0.0;
@@ -166,10 +165,11 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     cluster_wait();
     if (rank != 0 || threadIdx.x >= BI) return;
     double tot;
+    float sf = 0.f;  // MIXED: the density sum in FP32 (the high word of its double-float form)
     if (PREC == 1) {
-        f2sum t2 = inbox2[threadIdx.x];
-        for (int r = 1; r < C; ++r) t2 = f2_add(t2, inbox2[r * BI + threadIdx.x]);
+        const f2sum t2 = f2_tree_sum(inbox2 + threadIdx.x, C, BI);
         tot = (double)t2.hi + (double)t2.lo;
+        sf = t2.hi;
     } else {
         tot = 0.0;
         for (int r = 0; r < C; ++r) tot += inbox[r * BI + threadIdx.x];
@@ -185,10 +185,11 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
         p.z = (q == 0) ? zi[0] : zi[IPT - 1];
         d.rho[i] = rho;
         if (PREC == 1) {
-            const float rf = (float)rho;
-            float y = rsqrt_approx(rf);
-            y = y * (1.5f - 0.5f * rf * y * y);  // one Newton step
-            p.w = rho > 0.0 ? (float)d.pot.B6 * y : 0.0f;
+            // g = B6 rho^-1/2 = gsf sum^-1/2 on the FP32 pipe, so the FP64 work above (rho for
+            // the density output) does not hold up posg; sum > 0 exactly when rho > 0
+            float y = rsqrt_approx(sf);
+            y = y * (1.5f - 0.5f * sf * y * y);  // one Newton step
+            p.w = sf > 0.f ? d.pot.gsf * y : 0.0f;
         } else {
             p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
         }
