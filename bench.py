@@ -51,7 +51,7 @@ FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n
 # DRAM bytes (read + write) of one force-pass launch, from the ncu captures summarised in
 # profiles/k_force_ni2000_mixed.md and profiles/k_q_passes_ni50000_mixed.md (cold caches; the latter on the
 # same 50000-atom sphere with 0.1 A of disorder, whose lists are within 3 % of the timed state's).
-FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 234496, "ni50000": 11193856}
+FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 249344, "ni50000": 11197440}
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
 
 

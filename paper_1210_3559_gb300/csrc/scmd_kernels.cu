@@ -359,9 +359,10 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     }
     // MIXED steps that go on to the next step: the step coefficients for the split epilogue
     // below, loaded here so that their latency hides behind the reductions.
+    constexpr bool kSplit = PREC == 1 && IPT == 1;
     int kind0 = 2;
     double c_h = 0.0, c_hk = 0.0, c_c1 = 0.0, c_dt = 0.0;
-    if (PREC == 1 && integrate && !last && rank == 0) {
+    if (kSplit && integrate && !last && rank == 0) {
         kind0 = run->kind;
         c_h = run->h;
         c_hk = run->hk;
@@ -401,10 +402,13 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     // cycles, so one warp integrating all three components of its 32 atoms is ~27 FP64
     // instructions in a row at the end of the pass. The components are independent, so each of
     // up to 3 * IPT warps (on different sub-partitions) takes one component of 32 atoms, with
-    // the same operations in the same order as the one-warp form below.
+    // the same operations in the same order as the one-warp form below. This pays where a
+    // launch is one short wave (small clusters, IPT = 1). The IPT = 2 shapes serve large N,
+    // where many CTAs share each SM and the epilogue hides behind other CTAs' pair loops; there
+    // the split measured slower (its extra loads and barrier), so it is compiled in for IPT = 1.
     constexpr int NT = 3 * IPT;
     const int NW = W < NT ? W : NT;
-    const bool split = PREC == 1 && integrate && !last && kind0 != 2;
+    const bool split = kSplit && integrate && !last && kind0 != 2;
     if (!owner && !(split && rank == 0 && warp < NW)) return;
     R Fx = R(0), Fy = R(0), Fz = R(0);
     double Ep = 0.0;
