@@ -44,3 +44,18 @@ def test_reference_arm_two_ranks_gloo():
     lines = _json_lines(out.stdout)
     assert len(lines) == 1  # rank 0 only
     assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_replica_workloads_per_rank_share_the_shape_and_differ_in_seeds():
+    """Under torchrun each rank runs an independent replica: the same clusters and sizes (so the work per GPU
+    is fixed as N grows, weak scaling), with velocities and Langevin noise from rank-specific seeds."""
+    import numpy as np
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    for name in ("ni2000", "ni147", "ni147x64"):
+        w0, w1 = bench.workload(name, 0), bench.workload(name, 1)
+        assert w0["sizes"] == w1["sizes"] and w0["prec"] == w1["prec"] and w0["dt"] == w1["dt"]
+        assert np.array_equal(w0["pos"], w1["pos"]) and np.array_equal(w0["mass"], w1["mass"])
+        assert w0["seed"] != w1["seed"]
+        assert not np.allclose(w0["vel"], w1["vel"])
