@@ -1,0 +1,96 @@
+"""The solidification-kinetics analysis (kinetics.py) against what the paper prints and what probability fixes:
+Table I's own summary rows, the rate fit of Eq. rate3 against the table, the inverse of that fit, the censored
+exponential rate, and the coverage of the rate-ratio interval."""
+import numpy as np
+import pytest
+
+from paper_1210_3559_gb300 import kinetics as K
+
+pytest.importorskip("scipy.stats")
+
+
+def test_table_i_transcription_against_its_printed_summary_rows():
+    # 15 runs at 780 and 800 K, 12 at 820 K, 10 at 830 and 835 K (the table's caption)
+    assert {T: len(v) for T, v in K.TABLE_I.items()} == {780: 15, 800: 15, 820: 12, 830: 10, 835: 10}
+    for T, v in K.TABLE_I.items():
+        assert v == sorted(v)  # each column is listed in increasing order
+        # the kappa row is 1e5 / (printed mean) to the printed digits
+        assert 1e5 / K.TABLE_I_MEAN_PS[T] == pytest.approx(K.TABLE_I_KAPPA_1E5[T], rel=4e-3)
+    means = {T: float(np.mean(v)) for T, v in K.TABLE_I.items()}
+    for T in (780, 800, 835):  # the listed lifetimes give the printed means
+        assert abs(means[T] - K.TABLE_I_MEAN_PS[T]) <= 0.5
+    # the two columns whose printed means the listed lifetimes do not give (misprints read as such)
+    assert means[830] == pytest.approx(18701.0) and K.TABLE_I_MEAN_PS[830] == 18731
+    assert means[820] == pytest.approx(7018.33, abs=0.01) and K.TABLE_I_MEAN_PS[820] == 6440
+
+
+def test_rate_fit_in_ps_reproduces_the_table_and_the_precursor_frequency():
+    # e^a is the precursor formation frequency, which the paper states as 3.5 per ps
+    assert np.exp(K.FIT_A) == pytest.approx(3.5, rel=0.02)
+    # the fit against the table's kappa row: 780 K within 1 %, every temperature within 20 %
+    assert K.kappa_fit(780) == pytest.approx(1.99e-3, rel=0.01)
+    for T, k in K.TABLE_I_KAPPA_1E5.items():
+        assert K.kappa_fit(T) == pytest.approx(1e-5 * k, rel=0.2)
+    # read literally (kappa in fs^-1), the fit would be 1000 times faster than the table
+    for T, k in K.TABLE_I_KAPPA_1E5.items():
+        assert K.kappa_fit(T) * 1e3 / (1e-5 * k) > 500
+
+
+@pytest.mark.parametrize("T", [500.0, 700.0, 780.0, 835.0, 950.0, 1000.0])
+def test_temperature_for_kappa_inverts_the_fit(T):
+    assert K.temperature_for_kappa(float(K.kappa_fit(T))) == pytest.approx(T, abs=1e-6)
+
+
+def test_rate_is_monotonic_on_the_supercooled_branch():
+    # up to 1000 K (closer to T0 the rate underflows: ln kappa < -700)
+    T = np.linspace(K.FIT_T0_K / 3 + 1, 1000.0, 500)
+    assert np.all(np.diff(np.log(K.kappa_fit(T))) < 0)
+
+
+def test_rate_mle_with_censoring():
+    k, d, risk = K.rate_mle([1.0, 2.0, 3.0], n_censored=2, horizon_ps=10.0)
+    assert (d, risk) == (3, 26.0) and k == pytest.approx(3 / 26)
+    assert K.rate_mle([4.0, 6.0])[0] == pytest.approx(0.2)  # no censoring: 1 / mean
+
+
+def test_rate_ratio_interval_covers_the_true_ratio_at_its_level():
+    rng = np.random.default_rng(3)
+    true_ratio, na, nb, reps = 2.0, 24, 15, 4000
+    below = above = 0
+    for _ in range(reps):
+        a = rng.exponential(1.0 / true_ratio, na)
+        b = rng.exponential(1.0, nb)
+        r, lo, hi = K.rate_ratio(na, a.sum(), nb, b.sum())
+        below += true_ratio < lo
+        above += true_ratio > hi
+    # each tail misses 2.5 % (binomial s.e. 0.25 %); the F degrees of freedom in the wrong order give
+    # tails of about 1.5 % and 3.5 % with these unequal sample sizes
+    assert below / reps == pytest.approx(0.025, abs=0.0075)
+    assert above / reps == pytest.approx(0.025, abs=0.0075)
+
+
+def test_comparison_of_a_table_column_with_itself():
+    for T in (780, 800):
+        c = K.compare_with_table1(T, K.TABLE_I[T])
+        assert c["rate_ratio"] == pytest.approx(1.0) and c["ks_p"] == pytest.approx(1.0)
+        lo, hi = c["rate_ratio_ci95"]
+        assert lo < 1.0 < hi
+        assert c["fit_temperature_for_our_kappa_K"] == pytest.approx(
+            K.temperature_for_kappa(1.0 / np.mean(K.TABLE_I[T])))
+
+
+def test_compare_ensembles_on_synthetic_quench_outputs():
+    rng = np.random.default_rng(4)
+
+    def run(rate, n=60, horizon=300.0):
+        t = rng.exponential(1.0 / rate, n)
+        per = [{"n": 300, "t_nuc_ps": float(x) if x < horizon else None, "crystalline_end": float(rng.uniform(0, .3))}
+               for x in t]
+        return {"per_cluster": per, "horizon_ps": horizon}
+
+    c = K.compare_ensembles(run(5e-3), run(5e-3))
+    assert set(c) >= {"solidified", "fisher_p", "ks_p", "kappa_mle_per_ps", "rate_ratio", "rate_ratio_ci95",
+                      "crystalline_end_mean", "crystalline_end_mannwhitney_p"}
+    assert 0.0 <= c["fisher_p"] <= 1.0 and c["rate_ratio_ci95"][0] < c["rate_ratio"] < c["rate_ratio_ci95"][1]
+    fast = K.compare_ensembles(run(5e-2), run(2e-3))
+    assert fast["rate_ratio_ci95"][0] > 1.0 and fast["fisher_p"] < 1e-3
