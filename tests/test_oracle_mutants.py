@@ -1,17 +1,22 @@
 """The oracle's pins catch plausible mistakes in it.
 
-Each mutant below is the oracle's C source with one plausible slip planted in it: a dropped
-factor, a flipped sign, a wrong exponent, a transposed operand, a one-sided embedding term. The
-mutant is compiled on its own (CPU only) and run against pins that come from outside the
-oracle: the closed-form dimer of Eq. 1 and Eq. 2, central finite differences of its own energy,
-and the vanishing net force and torque of pairwise central forces. Every mutant must fail at
-least one pin, and the unmodified source must pass all of them, so a mistake of these kinds
-cannot hide in the oracle the CUDA path is checked against.
+Each mutant below is the oracle's C source with one plausible slip planted in it. The energy and
+force mutants (a dropped factor, a flipped sign, a wrong exponent, a transposed operand, a one-sided
+embedding term) are compiled on their own (CPU only) and run against the closed-form dimer of Eq. 1
+and Eq. 2, central finite differences of the mutant's own energy, and the vanishing net force and
+torque of pairwise central forces. The dynamics mutants (a wrong kick or drift, Langevin friction or
+noise variance, ramp, Berendsen factor, kinetic energy, Philox rounds, Box-Muller) are run through
+the pin tests of test_oracle.py themselves: the harmonic period of the dimer, the dt^2 energy
+fluctuation, the exact variance recursion of free atoms under the Langevin ramp, the closed-form
+Berendsen relaxation, the published Philox known-answer vectors and the normals' moments and
+layout. Every mutant must fail at least one pin, and the unmodified source must pass all of them,
+so a mistake of these kinds cannot hide in the oracle the CUDA path is checked against.
 """
 import ctypes
 import os
 import shutil
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -122,3 +127,90 @@ def test_planted_mistake_fails_a_pin(source, tmp_path, name, old, new):
     L = _compile(source.replace(old, new), str(tmp_path), "mutant")
     failed = [pin.__name__ for pin in PINS if not pin(L)]
     assert failed, f"no pin catches the mutant '{name}'"
+
+
+# ------------------------------------------------------------------- dynamics
+# (name, text in sc_oracle.c, replacement); each text occurs exactly once in the source
+DYN_MUTANTS = [
+    ("first half kick over the full step",
+     "vel[3 * i + c] += h * forces[3 * i + c] * conv / mass[i];\n        if (th->kind == 1) {",
+     "vel[3 * i + c] += dt * forces[3 * i + c] * conv / mass[i];\n        if (th->kind == 1) {"),
+    ("NVE drift over half the step",
+     "pos[3 * i + c] += dt * vel[3 * i + c];", "pos[3 * i + c] += h * vel[3 * i + c];"),
+    ("second half kick with the unit conversion inverted",
+     "vel[3 * i + c] += h * forces[3 * i + c] * conv / mass[i];\n        if (th->kind == 2",
+     "vel[3 * i + c] += h * forces[3 * i + c] / conv / mass[i];\n        if (th->kind == 2"),
+    ("Langevin friction over half the step",
+     "double c1 = exp(-th->gamma_ps * 1.0e-3 * dt);", "double c1 = exp(-th->gamma_ps * 1.0e-3 * h);"),
+    ("Langevin noise variance without 1 - c1^2",
+     "sqrt((1.0 - c1 * c1) * ORC_KB_EV_PER_K * T_target * conv / mass[i])",
+     "sqrt(ORC_KB_EV_PER_K * T_target * conv / mass[i])"),
+    ("Langevin noise at the ramp's start temperature",
+     "sqrt((1.0 - c1 * c1) * ORC_KB_EV_PER_K * T_target * conv / mass[i])",
+     "sqrt((1.0 - c1 * c1) * ORC_KB_EV_PER_K * th->T0 * conv / mass[i])"),
+    ("ramp one step ahead",
+     "(th->T1 - th->T0) * (double)k / (double)nsteps", "(th->T1 - th->T0) * (double)(k + 1) / (double)nsteps"),
+    ("Berendsen factor without the square root",
+     "? sqrt(1.0 + (dt / (th->tau_ps * 1.0e3)) * (T_target / T_inst - 1.0))",
+     "? (1.0 + (dt / (th->tau_ps * 1.0e3)) * (T_target / T_inst - 1.0))"),
+    ("kinetic energy without 1/2",
+     "ke += 0.5 * mass[i] *", "ke += mass[i] *"),
+    ("Philox key schedule without the second Weyl increment",
+     "if (round > 0) { k0 += W0; k1 += W1; }", "if (round > 0) { k0 += W0; }"),
+    ("Philox multipliers swapped",
+     "const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;", "const uint32_t M0 = 0xCD9E8D57u, M1 = 0xD2511F53u;"),
+    ("Box-Muller radius without the factor 2",
+     "double r1 = sqrt(-2.0 * log(u01(w[0])));", "double r1 = sqrt(-log(u01(w[0])));"),
+    ("second normal from the other radius",
+     "z[1] = r1 * sin(two_pi * u01(w[1]));", "z[1] = r2 * sin(two_pi * u01(w[1]));"),
+]
+
+
+def _dyn_pins():
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle as T
+
+    def philox_kat():
+        for ctr, key, expect in T.kat_vectors():
+            T.test_philox_known_answer_vectors(ctr, key, expect)
+
+    # cheapest first; the Ornstein-Uhlenbeck test (12 s) is left out, the others cover its terms
+    return [philox_kat, T.test_box_muller_normals_moments_and_counter_layout,
+            T.test_berendsen_free_atoms_follow_closed_form_relaxation,
+            T.test_dimer_small_oscillation_period_matches_harmonic_closed_form,
+            T.test_nve_energy_fluctuation_scales_as_dt_squared_and_conserves_momenta,
+            T.test_langevin_ramp_follows_variance_recursion]
+
+
+def _use_oracle_library(monkeypatch, src_text, out_dir, name):
+    """Build the oracle from src_text (with the unchanged structure source) and make the oracle module load it."""
+    src = os.path.join(out_dir, name + ".c")
+    lib = os.path.join(out_dir, name + ".so")
+    with open(src, "w") as f:
+        f.write(src_text)
+    other = os.path.join(os.path.dirname(SRC), "structure_oracle.c")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", src, other,
+                    "-o", lib, "-lm"], check=True)
+    monkeypatch.setattr(oracle, "_lib", None)
+    monkeypatch.setattr(oracle, "build", lambda force=False: lib)
+
+
+def _first_failing_pin(pins):
+    for pin in pins:
+        try:
+            pin()
+        except Exception:  # an assertion, or a non-finite value the pin cannot digest
+            return pin.__name__
+    return None
+
+
+def test_unmodified_oracle_passes_every_dynamics_pin(source, tmp_path, monkeypatch):
+    _use_oracle_library(monkeypatch, source, str(tmp_path), "control_dyn")
+    assert _first_failing_pin(_dyn_pins()) is None
+
+
+@pytest.mark.parametrize("name,old,new", DYN_MUTANTS, ids=[m[0] for m in DYN_MUTANTS])
+def test_planted_dynamics_mistake_fails_a_pin(source, tmp_path, monkeypatch, name, old, new):
+    assert source.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+    _use_oracle_library(monkeypatch, source.replace(old, new), str(tmp_path), "mutant_dyn")
+    assert _first_failing_pin(_dyn_pins()) is not None, f"no pin catches the mutant '{name}'"
