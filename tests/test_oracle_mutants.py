@@ -9,8 +9,11 @@ noise variance, ramp, Berendsen factor, kinetic energy, Philox rounds, Box-Mulle
 the pin tests of test_oracle.py themselves: the harmonic period of the dimer, the dt^2 energy
 fluctuation, the exact variance recursion of free atoms under the Langevin ramp, the closed-form
 Berendsen relaxation, the published Philox known-answer vectors and the normals' moments and
-layout. Every mutant must fail at least one pin, and the unmodified source must pass all of them,
-so a mistake of these kinds cannot hide in the oracle the CUDA path is checked against.
+layout. The structure mutants (neighbour cutoff, bond counting, the longest bond chain, the hcp rule,
+self pairs in the pair-distance histogram, the displacement's centre-of-mass correction and average)
+run through the pin tests of test_oracle_structure.py. Every mutant must fail at least one pin, and
+the unmodified sources must pass all of them, so a mistake of these kinds cannot hide in the oracle
+the CUDA path is checked against.
 """
 import ctypes
 import os
@@ -25,6 +28,7 @@ import oracle
 from paper_1210_3559_gb300 import inputs
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sc_oracle.c")
+STRUCT_SRC = os.path.join(os.path.dirname(oracle.__file__), "structure_oracle.c")
 EPS, C, A, NN, MM = 1.5707e-2, 39.432, 3.52, 9, 6
 
 # (name, text in sc_oracle.c, replacement); each text occurs exactly once in the source
@@ -182,14 +186,20 @@ def _dyn_pins():
             T.test_langevin_ramp_follows_variance_recursion]
 
 
-def _use_oracle_library(monkeypatch, src_text, out_dir, name):
-    """Build the oracle from src_text (with the unchanged structure source) and make the oracle module load it."""
-    src = os.path.join(out_dir, name + ".c")
+def _use_oracle_library(monkeypatch, src_text, out_dir, name, structure_text=None):
+    """Build the oracle from src_text and structure_text (the unchanged sources where None) and make the
+    oracle module load it."""
+    srcs = []
+    for text, base in ((src_text, SRC), (structure_text, STRUCT_SRC)):
+        if text is None:
+            with open(base) as f:
+                text = f.read()
+        path = os.path.join(out_dir, name + "_" + os.path.basename(base))
+        with open(path, "w") as f:
+            f.write(text)
+        srcs.append(path)
     lib = os.path.join(out_dir, name + ".so")
-    with open(src, "w") as f:
-        f.write(src_text)
-    other = os.path.join(os.path.dirname(SRC), "structure_oracle.c")
-    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", src, other,
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", *srcs,
                     "-o", lib, "-lm"], check=True)
     monkeypatch.setattr(oracle, "_lib", None)
     monkeypatch.setattr(oracle, "build", lambda force=False: lib)
@@ -214,3 +224,53 @@ def test_planted_dynamics_mistake_fails_a_pin(source, tmp_path, monkeypatch, nam
     assert source.count(old) == 1, f"mutation site not unique or missing: {old!r}"
     _use_oracle_library(monkeypatch, source.replace(old, new), str(tmp_path), "mutant_dyn")
     assert _first_failing_pin(_dyn_pins()) is not None, f"no pin catches the mutant '{name}'"
+
+
+# ---------------------------------------------------------- structural observables
+# (name, text in structure_oracle.c, replacement); each text occurs exactly once in the source
+STRUCT_MUTANTS = [
+    ("neighbour cutoff compared with r^2 unsquared",
+     "const double rn2 = r_nb * r_nb;", "const double rn2 = r_nb;"),
+    ("bonds among the common neighbours counted twice",
+     "for (int y = x + 1; y < k; ++y)", "for (int y = 0; y < k; ++y)"),
+    ("longest bond chain replaced by a flag",
+     "per_set[find_root(parent, bond_a[e])] += 1;", "per_set[find_root(parent, bond_a[e])] = 1;"),
+    ("hcp required to be 12 x 422",
+     "else if (n421 == 6 && n422 == 6)", "else if (n422 == 12)"),
+    ("pair-distance histogram counts an atom with itself",
+     "            if (j == c) continue;\n            const double r = sqrt(r2_of(pos, c, j));",
+     "            const double r = sqrt(r2_of(pos, c, j));"),
+    ("displacement without removing the centre-of-mass motion",
+     "const double d = (pos[3 * i + q] - X[q]) - (ref[3 * i + q] - X0[q]);",
+     "const double d = pos[3 * i + q] - ref[3 * i + q];"),
+    ("displacement averaged over all atoms instead of the selection",
+     "return n > 0 ? s / n : 0.0;", "return n > 0 ? s / N : 0.0;"),
+]
+
+
+def _struct_pins():
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle_structure as S
+    return [S.test_cna_signatures_fcc_hcp_icosahedron, S.test_cna_classes_of_ideal_structures,
+            S.test_cna_invariances, S.test_rdf_of_the_centre_atom_is_the_fcc_shell_count,
+            S.test_rdf_counts_every_core_pair_once, S.test_msd_closed_forms]
+
+
+@pytest.fixture(scope="module")
+def structure_source():
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    with open(STRUCT_SRC) as f:
+        return f.read()
+
+
+def test_unmodified_structure_oracle_passes_every_pin(structure_source, tmp_path, monkeypatch):
+    _use_oracle_library(monkeypatch, None, str(tmp_path), "control_struct", structure_source)
+    assert _first_failing_pin(_struct_pins()) is None
+
+
+@pytest.mark.parametrize("name,old,new", STRUCT_MUTANTS, ids=[m[0] for m in STRUCT_MUTANTS])
+def test_planted_structure_mistake_fails_a_pin(structure_source, tmp_path, monkeypatch, name, old, new):
+    assert structure_source.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+    _use_oracle_library(monkeypatch, None, str(tmp_path), "mutant_struct", structure_source.replace(old, new))
+    assert _first_failing_pin(_struct_pins()) is not None, f"no pin catches the mutant '{name}'"
