@@ -9,7 +9,8 @@ noise variance, ramp, Berendsen factor, kinetic energy, Philox rounds, Box-Mulle
 the pin tests of test_oracle.py themselves: the harmonic period of the dimer, the dt^2 energy
 fluctuation, the exact variance recursion of free atoms under the Langevin ramp, the closed-form
 Berendsen relaxation, the published Philox known-answer vectors and the normals' moments and
-layout. The structure mutants (neighbour cutoff, bond counting, the longest bond chain, the hcp rule,
+layout. The cutoff mutants (inclusive, ignored, shifted with the wrong exponent or sign) run through
+its cutoff and shifted-cutoff pins. The structure mutants (neighbour cutoff, bond counting, the longest bond chain, the hcp rule,
 self pairs in the pair-distance histogram, the displacement's centre-of-mass correction and average)
 run through the pin tests of test_oracle_structure.py. Every mutant must fail at least one pin, and
 the unmodified sources must pass all of them, so a mistake of these kinds cannot hide in the oracle
@@ -274,3 +275,39 @@ def test_planted_structure_mistake_fails_a_pin(structure_source, tmp_path, monke
     assert structure_source.count(old) == 1, f"mutation site not unique or missing: {old!r}"
     _use_oracle_library(monkeypatch, None, str(tmp_path), "mutant_struct", structure_source.replace(old, new))
     assert _first_failing_pin(_struct_pins()) is not None, f"no pin catches the mutant '{name}'"
+
+
+# ------------------------------------------------------------------- cutoff forms
+# (name, text in sc_oracle.c, replacement); each text occurs exactly once in the source
+CUTOFF_MUTANTS = [
+    ("cutoff inclusive (r <= rc)", "return !(p->rcut > 0.0) || r < p->rcut;", "return !(p->rcut > 0.0) || r <= p->rcut;"),
+    ("cutoff ignored", "return !(p->rcut > 0.0) || r < p->rcut;", "return 1;"),
+    ("every term shifted with the repulsive exponent",
+     "t - pow(p->a / p->rcut, k)", "t - pow(p->a / p->rcut, p->n)"),
+    ("shift added instead of subtracted", "t - pow(p->a / p->rcut, k)", "t + pow(p->a / p->rcut, k)"),
+]
+
+
+def _cutoff_pins():
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle as T
+
+    def shifted_dimer():
+        for r in (2.3, 2.6, 4.0, 8.0):
+            T.test_shifted_dimer_closed_form(r)
+
+    return [T.test_cutoff_pairs_beyond_range_vanish_and_isolated_atom_is_zero, shifted_dimer,
+            T.test_forces_with_cutoff_match_central_differences, T.test_shifted_forces_match_central_differences,
+            T.test_shifted_energy_is_continuous_at_the_cutoff]
+
+
+def test_unmodified_oracle_passes_every_cutoff_pin(source, tmp_path, monkeypatch):
+    _use_oracle_library(monkeypatch, source, str(tmp_path), "control_cut")
+    assert _first_failing_pin(_cutoff_pins()) is None
+
+
+@pytest.mark.parametrize("name,old,new", CUTOFF_MUTANTS, ids=[m[0] for m in CUTOFF_MUTANTS])
+def test_planted_cutoff_mistake_fails_a_pin(source, tmp_path, monkeypatch, name, old, new):
+    assert source.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+    _use_oracle_library(monkeypatch, source.replace(old, new), str(tmp_path), "mutant_cut")
+    assert _first_failing_pin(_cutoff_pins()) is not None, f"no pin catches the mutant '{name}'"
