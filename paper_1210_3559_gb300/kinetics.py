@@ -92,7 +92,8 @@ def rate_ratio(d_a: int, at_risk_a: float, d_b: int, at_risk_b: float, level: fl
 
 
 def compare_with_table1(T: int, lifetimes_ps, n_censored: int = 0, horizon_ps: float = 0.0) -> dict:
-    """This build's lifetimes at temperature T against the paper's Table I column for T."""
+    """Measured lifetimes at temperature T (runs still liquid at the horizon counted as censored) against the
+    paper's Table I column for T."""
     from scipy.stats import ks_2samp
     paper = np.asarray(TABLE_I[T], dtype=np.float64)
     ours = np.asarray(lifetimes_ps, dtype=np.float64)
