@@ -70,6 +70,35 @@ def test_dimer_minimum():
     assert oracle.energy([[0, 0, 0], [r0 * 0.999, 0, 0]]) > U
 
 
+
+def symmetric_closed_form(k, r):
+    """k + 1 atoms at mutual distance r (k = 2: equilateral triangle, k = 3: regular tetrahedron).
+    Each atom has k neighbours at r, so rho = k s^m and U = (k + 1) eps [(k/2) s^n - c sqrt(k) s^(m/2)]
+    with s = a/r; the embedding's sqrt(k) is what a pairwise form cannot give."""
+    s = A / r
+    U = (k + 1) * EPS * (0.5 * k * s ** NN - C * np.sqrt(k) * s ** (MM / 2))
+    dUdr = (k + 1) * EPS * (-0.5 * k * NN * s ** NN + C * np.sqrt(k) * (MM / 2) * s ** (MM / 2)) / r
+    return U, dUdr, k * s ** MM
+
+
+@pytest.mark.parametrize("r", [2.3, 2.49, 3.0, 4.5])
+def test_trimer_and_tetramer_closed_forms(r):
+    tri = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0], [0.5 * r, 0.5 * np.sqrt(3.0) * r, 0.0]])
+    tet = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=np.float64) * r / (2 * np.sqrt(2.0))
+    for k, pos in ((2, tri), (3, tet)):
+        U_ref, dUdr, rho_ref = symmetric_closed_form(k, r)
+        U, F, (e_pair, e_emb), rho = oracle.energy_forces(pos)
+        assert U == pytest.approx(U_ref, rel=1e-13)
+        assert e_emb == pytest.approx(-(k + 1) * EPS * C * np.sqrt(rho_ref), rel=1e-13)
+        assert np.allclose(rho, rho_ref, rtol=1e-14, atol=0)
+        # forces are radial from the centroid, all of one magnitude f; the virial of a uniform dilation,
+        # sum_i F_i . (r_i - R) = -r dU/dr, fixes f
+        d = pos - pos.mean(axis=0)
+        R = np.linalg.norm(d[0])
+        f = -r * dUdr / ((k + 1) * R)
+        assert np.allclose(F, f * d / R, rtol=1e-12, atol=1e-14 * abs(f) + 1e-16)
+
+
 # ------------------------------------------------------------ bulk lattice
 def fcc_lattice_sums(kmax=36):
     """S_k = sum over FCC sites R != 0 of (a/|R|)^k, with an r^-3 continuum tail for S_6."""

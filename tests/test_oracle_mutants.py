@@ -311,3 +311,42 @@ def test_planted_cutoff_mistake_fails_a_pin(source, tmp_path, monkeypatch, name,
     assert source.count(old) == 1, f"mutation site not unique or missing: {old!r}"
     _use_oracle_library(monkeypatch, source.replace(old, new), str(tmp_path), "mutant_cut")
     assert _first_failing_pin(_cutoff_pins()) is not None, f"no pin catches the mutant '{name}'"
+
+
+# ------------------------------------------------------------- many-body embedding
+# Three coordinated edits make the embedding pairwise while rho stays right: every pair adds
+# -2 c (a/r)^(m/2) to the pair sum, the sqrt-of-density term is dropped, and the force is the matching
+# pairwise one. Energy and force stay consistent, rho_i = sum (a/r)^m is untouched and the dimer is
+# unchanged (one pair: sqrt of the sum equals the sum of the sqrt), so only a closed form with several
+# neighbours per atom tells this from the paper's sqrt of the summed density (Eq. 1).
+PAIRWISE_EMBEDDING = [
+    ("acc += term(r, p->n, p);\n            }\n            pair_i[i] = acc;",
+     "acc += term(r, p->n, p) - 2.0 * p->c * sqrt(term(r, p->m, p));\n            }\n            pair_i[i] = acc;"),
+    ("e_emb += -p->eps * p->c * sqrt(rho[i]);", "e_emb += 0.0;"),
+    ("kemb * (g[i] + g[j]) * pow(s, p->m)) / (r * r);", "kemb * 2.0 * pow(s, 0.5 * p->m)) / (r * r);"),
+]
+
+
+def test_pairwise_embedding_is_caught_only_by_the_many_neighbour_closed_forms(source, tmp_path, monkeypatch):
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle as T
+    text = source
+    for old, new in PAIRWISE_EMBEDDING:
+        assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+        text = text.replace(old, new)
+    _use_oracle_library(monkeypatch, text, str(tmp_path), "mutant_pairwise")
+
+    def dimer():
+        for r in (1.9, 2.041345, 2.3, 2.49, 3.1):
+            T.test_dimer_energy_and_force_closed_form(r)
+
+    def finite_differences():
+        for n, seed in ((3, 1), (13, 2)):
+            T.test_forces_match_central_differences(n, seed)
+
+    def trimer_tetramer():
+        for r in (2.3, 2.49, 3.0, 4.5):
+            T.test_trimer_and_tetramer_closed_forms(r)
+
+    assert _first_failing_pin([dimer, finite_differences, T.test_net_force_and_torque_vanish]) is None
+    assert _first_failing_pin([trimer_tetramer]) == "trimer_tetramer"
