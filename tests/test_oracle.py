@@ -262,6 +262,26 @@ def test_dimer_small_oscillation_period_matches_harmonic_closed_form():
     assert measured == pytest.approx(period, rel=2e-3)
 
 
+
+def test_observables_of_a_spinning_dimer_closed_forms():
+    # two atoms of unequal mass, centre of mass X moving at V, spinning at omega about z through X:
+    # P = M V, L (about X) = mu r^2 omega, E_kin = 1/2 M V^2 + 1/2 mu r^2 omega^2 (Koenig), U = dimer(r)
+    m1, m2, r = inputs.NI_MASS_AMU, 2.0 * inputs.NI_MASS_AMU, 2.49
+    M, mu = m1 + m2, m1 * m2 / (m1 + m2)
+    X, V, w = np.array([1.0, -2.0, 0.5]), np.array([0.01, 0.002, -0.003]), 0.004
+    pos = np.array([X - (m2 / M) * r * np.array([1.0, 0, 0]), X + (m1 / M) * r * np.array([1.0, 0, 0])])
+    vel = V + np.cross(np.array([0, 0, w]), pos - X)
+    o = oracle.observables(pos, vel, [m1, m2])
+    assert np.allclose(o["com"], X, rtol=0, atol=1e-14)
+    assert np.allclose(o["mom"], M * V, rtol=1e-13, atol=1e-16)
+    assert np.allclose(o["angmom"], [0.0, 0.0, mu * r * r * w], rtol=1e-12, atol=1e-15)
+    ekin = (0.5 * M * V @ V + 0.5 * mu * r * r * w * w) / conv()
+    assert o["ekin"] == pytest.approx(ekin, rel=1e-13)
+    assert o["T"] == pytest.approx(2 * ekin / (3 * 2 * oracle.kb()), rel=1e-13)
+    assert o["epot"] == pytest.approx(dimer_closed_form(r)[0], rel=1e-13)
+    assert o["etot"] == pytest.approx(o["epot"] + o["ekin"], rel=1e-15)
+
+
 def nve_fluct(dt, nsteps):
     pos = inputs.mackay_icosahedron(2, 2.49)
     m = inputs.masses(len(pos))

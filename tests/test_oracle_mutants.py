@@ -5,8 +5,9 @@ force mutants (a dropped factor, a flipped sign, a wrong exponent, a transposed 
 embedding term) are compiled on their own (CPU only) and run against the closed-form dimer of Eq. 1
 and Eq. 2, central finite differences of the mutant's own energy, and the vanishing net force and
 torque of pairwise central forces. The dynamics mutants (a wrong kick or drift, Langevin friction or
-noise variance, ramp, Berendsen factor, kinetic energy, Philox rounds, Box-Muller) are run through
-the pin tests of test_oracle.py themselves: the harmonic period of the dimer, the dt^2 energy
+noise variance, ramp, Berendsen factor, kinetic energy, Philox rounds, Box-Muller, the observables'
+centre of mass, angular momentum and temperature) are run through the pin tests of test_oracle.py
+themselves: the observables of a spinning dimer, the harmonic period of the dimer, the dt^2 energy
 fluctuation, the exact variance recursion of free atoms under the Langevin ramp, the closed-form
 Berendsen relaxation, the published Philox known-answer vectors and the normals' moments and
 layout. The cutoff mutants (inclusive, ignored, shifted with the wrong exponent or sign) run through
@@ -168,6 +169,15 @@ DYN_MUTANTS = [
      "double r1 = sqrt(-2.0 * log(u01(w[0])));", "double r1 = sqrt(-log(u01(w[0])));"),
     ("second normal from the other radius",
      "z[1] = r1 * sin(two_pi * u01(w[1]));", "z[1] = r2 * sin(two_pi * u01(w[1]));"),
+    ("angular momentum about the origin",
+     "double r[3] = {pos[3 * i] - o->com[0], pos[3 * i + 1] - o->com[1], pos[3 * i + 2] - o->com[2]};",
+     "double r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};"),
+    ("centre of mass unweighted", "o->com[k] += mass[i] * pos[3 * i + k];", "o->com[k] += pos[3 * i + k];"),
+    ("angular momentum z with the cross product reversed",
+     "o->angmom[2] += mass[i] * (r[0] * v[1] - r[1] * v[0]);", "o->angmom[2] += mass[i] * (r[1] * v[0] - r[0] * v[1]);"),
+    ("temperature from 3N - 6 degrees of freedom",
+     "o->T = N > 0 ? 2.0 * o->ekin / (3.0 * N * ORC_KB_EV_PER_K) : 0.0;",
+     "o->T = N > 2 ? 2.0 * o->ekin / ((3.0 * N - 6.0) * ORC_KB_EV_PER_K) : 0.0;"),
 ]
 
 
@@ -180,7 +190,8 @@ def _dyn_pins():
             T.test_philox_known_answer_vectors(ctr, key, expect)
 
     # cheapest first; the Ornstein-Uhlenbeck test (12 s) is left out, the others cover its terms
-    return [philox_kat, T.test_box_muller_normals_moments_and_counter_layout,
+    return [T.test_observables_of_a_spinning_dimer_closed_forms, philox_kat,
+            T.test_box_muller_normals_moments_and_counter_layout,
             T.test_berendsen_free_atoms_follow_closed_form_relaxation,
             T.test_dimer_small_oscillation_period_matches_harmonic_closed_form,
             T.test_nve_energy_fluctuation_scales_as_dt_squared_and_conserves_momenta,
