@@ -361,3 +361,42 @@ def test_pairwise_embedding_is_caught_only_by_the_many_neighbour_closed_forms(so
 
     assert _first_failing_pin([dimer, finite_differences, T.test_net_force_and_torque_vanish]) is None
     assert _first_failing_pin([trimer_tetramer]) == "trimer_tetramer"
+
+
+# ---------------------------------------------------------------- Langevin splitting
+_AOA = """                    pos[3 * i + c] += h * vel[3 * i + c];
+                    vel[3 * i + c] = c1 * vel[3 * i + c] + sigma * z[c];
+                    pos[3 * i + c] += h * vel[3 * i + c];"""
+_O_AT_END = """        if (th->kind == 1) {
+            double c1 = exp(-th->gamma_ps * 1.0e-3 * dt);
+            for (int i = 0; i < N; ++i) {
+                double z[3];
+                orc_langevin_normals(th->seed, cluster, step0 + k, (uint32_t)i, z);
+                double sigma = sqrt((1.0 - c1 * c1) * ORC_KB_EV_PER_K * T_target * conv / mass[i]);
+                for (int c = 0; c < 3; ++c) vel[3 * i + c] = c1 * vel[3 * i + c] + sigma * z[c];
+            }
+        }
+        if (th->kind == 2 && N > 0) {"""
+# other orderings of the same sub-steps (each keeps the free-atom Ornstein-Uhlenbeck statistics exact)
+SPLITTING_MUTANTS = [
+    ("full drift, then friction (B A O B)",
+     [(_AOA, """                    pos[3 * i + c] += dt * vel[3 * i + c];
+                    vel[3 * i + c] = c1 * vel[3 * i + c] + sigma * z[c];""")]),
+    ("velocity Verlet, then friction (B A B O)",
+     [(_AOA, "                    pos[3 * i + c] += dt * vel[3 * i + c];"),
+      ("        if (th->kind == 2 && N > 0) {", _O_AT_END)]),
+]
+
+
+@pytest.mark.parametrize("name,subs", SPLITTING_MUTANTS, ids=[m[0] for m in SPLITTING_MUTANTS])
+def test_other_langevin_splittings_fail_the_harmonic_sampling_pin(source, tmp_path, monkeypatch, name, subs):
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle as T
+    text = source
+    for old, new in subs:
+        assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+        text = text.replace(old, new)
+    _use_oracle_library(monkeypatch, text, str(tmp_path), "mutant_split")
+    # with U = 0 the kicks vanish and one friction step per step remains: the free-atom pin cannot tell
+    assert _first_failing_pin([T.test_langevin_ramp_follows_variance_recursion]) is None
+    assert _first_failing_pin([T.test_langevin_baoab_samples_harmonic_configurations_exactly]) is not None
