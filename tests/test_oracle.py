@@ -389,6 +389,24 @@ def test_berendsen_free_atoms_follow_closed_form_relaxation():
     assert b.observables()[0]["T"] == pytest.approx(expect, rel=1e-12)
 
 
+
+def test_berendsen_with_tau_equal_to_dt_lands_on_the_ramp_target_every_step():
+    # with tau = dt the factor is sqrt(T_target / T_inst): rescaling the velocities that end the step sets
+    # T to the step's target exactly, forces or not; with a ramp the target of local step k is
+    # T0 + (T1 - T0) k / n
+    pos = inputs.fcc_sphere(55)
+    m = inputs.masses(55)
+    vel = inputs.maxwell_boltzmann(pos, m, 900.0, seed=6)
+    b = oracle.Batch([55], pos, vel, m)
+    dt, T0, T1, n = 2.0, 700.0, 400.0, 6
+    for k in range(n):  # one call per step: the target of a one-step call is its T0
+        Tk = T0 + (T1 - T0) * k / n
+        b.run(1, dt, oracle.thermostat(oracle.BERENDSEN, Tk, Tk, tau_ps=dt * 1e-3))
+        assert b.observables()[0]["T"] == pytest.approx(Tk, rel=1e-13)
+    b.run(n, dt, oracle.thermostat(oracle.BERENDSEN, T0, T1, tau_ps=dt * 1e-3))
+    assert b.observables()[0]["T"] == pytest.approx(T0 + (T1 - T0) * (n - 1) / n, rel=1e-13)
+
+
 def test_langevin_run_is_reproducible_and_resumable():
     pos = inputs.fcc_sphere(55)
     m = inputs.masses(55)

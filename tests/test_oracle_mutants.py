@@ -388,6 +388,31 @@ SPLITTING_MUTANTS = [
 ]
 
 
+_BER_BLOCK = """        if (th->kind == 2 && N > 0) {
+            double T_inst = 2.0 * kinetic(N, vel, mass) / (3.0 * N * ORC_KB_EV_PER_K);
+            double lambda = T_inst > 0.0
+                                ? sqrt(1.0 + (dt / (th->tau_ps * 1.0e3)) * (T_target / T_inst - 1.0))
+                                : 1.0;
+            for (int i = 0; i < 3 * N; ++i) vel[i] *= lambda;
+        }
+"""
+_SECOND_KICK = """        orc_energy_forces(N, pos, p, forces, NULL, NULL);
+        for (int i = 0; i < N; ++i)
+            for (int c = 0; c < 3; ++c) vel[3 * i + c] += h * forces[3 * i + c] * conv / mass[i];
+"""
+
+
+def test_berendsen_rescale_before_the_second_kick_fails_the_tau_equal_dt_pin(source, tmp_path, monkeypatch):
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle as T
+    old = _SECOND_KICK + _BER_BLOCK
+    assert source.count(old) == 1, "mutation site not unique or missing"
+    _use_oracle_library(monkeypatch, source.replace(old, _BER_BLOCK + _SECOND_KICK), str(tmp_path), "mutant_ber")
+    # free atoms feel no kick, so the closed-form relaxation cannot tell the order apart
+    assert _first_failing_pin([T.test_berendsen_free_atoms_follow_closed_form_relaxation]) is None
+    assert _first_failing_pin([T.test_berendsen_with_tau_equal_to_dt_lands_on_the_ramp_target_every_step]) is not None
+
+
 @pytest.mark.parametrize("name,subs", SPLITTING_MUTANTS, ids=[m[0] for m in SPLITTING_MUTANTS])
 def test_other_langevin_splittings_fail_the_harmonic_sampling_pin(source, tmp_path, monkeypatch, name, subs):
     sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
