@@ -1,25 +1,28 @@
 """Benchmark: Sutton-Chen Ni cluster MD on one GB300 per rank (replicas), one JSON line.
 
-Default workload (Ni~2000 cooling run): fcc_sphere(2000) (a = 3.52 A), Maxwell-Boltzmann
-velocities at 2000 K (seed 2), melted with Langevin at 2000 K for 20 ps (1e4 steps of
-2 fs, gamma = 1/ps; untimed set-up), then the linear Langevin cooling 2000 -> 300 K over
-2e5 steps of 2 fs (gamma = 1/ps), MIXED precision (FP32 pair terms, FP64 rho, energy and
-integration). One timed iteration ("step" of this benchmark) is one md_step call of
---md-steps MD steps (default 500) of that schedule, issued as CUDA-graph replays; the
-default --steps 400 covers the whole 2e5-step cooling schedule. L2 is flushed (a 256 MB
-write) before every timed iteration and that flush is outside the timed events.
+Default workload (the largest single-GPU configuration, the paper's ensemble pattern of
+Sec. III C): 512 independent clusters with N_b uniform in 55..2000 (seed 5; fcc spheres,
+a = 3.52 A), Maxwell-Boltzmann velocities at 2000 K (per-cluster seed 1000 + b), melted with
+Langevin at 2000 K for 20 ps (1e4 steps of 2 fs, gamma = 1/ps; untimed set-up), then quenched
+with Langevin at a fixed 900 K (dt = 2 fs, gamma = 1/ps), MIXED precision (FP32 pair terms,
+FP64 rho, energy and integration), all pairs. One timed iteration ("step" of this benchmark) is
+one md_step call of --md-steps MD steps (default 500), issued as CUDA-graph replays. L2 is
+flushed (a 256 MB write) before every timed iteration and that flush is outside the timed
+events.
 
-Other configs (--config): ni6000, ni20000 (all pairs, MIXED), ni50000 (rcut = 8.8 A on the
-neighbour lists, MIXED: lists of atom quads), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one
-context), batched512 (512 clusters of 55..2000 atoms).
+Other configs (--config): ni2000 (one cluster, Langevin cooling 2000 -> 300 K over 2e5 steps),
+ni6000, ni20000 (all pairs, MIXED), ni50000 (rcut = 8.8 A on the neighbour lists, MIXED: lists of
+atom quads), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one context).
 
 value  : atom-timesteps/s over all ranks (sum of atoms x MD steps / max rank time).
 e2e    : the same metric through the C ABI with host buffers every iteration
          (md_set_state from pinned host arrays, md_step, md_get_state back to the host).
 roofline: the force pass (dominant kernel), FP32-pipe lane operations per launch
-         (16 per ordered pair) over its mean launch time, timed with CUDA events on the
-         library's stream right after the timed region, against 152 SMs x 128 FP32
-         lanes x the maximum SM clock.
+         (16 per ordered pair) over its mean launch time. The launch time is CUDA-event time
+         over back-to-back launches on the library's stream (the same programmatic-dependent
+         launch overlap as inside the step graph) right after the timed region; it must fit the
+         measured MD step. Peak: the device's SM count x 128 FP32 lanes x the maximum SM clock;
+         the FFMA rate measured on this device (md_fp32_peak) is reported beside it.
 cpu_baseline: the FP64 oracle (plain C + OpenMP) on the host cores, on a bounded sample
          of the same workload (rank 0 only).
 --impl reference: times that oracle alone as the reference arm.
@@ -48,11 +51,28 @@ METRIC = "atom-timesteps/s & pair-evals/s vs FP32 peak; mixed vs FP64 at stated 
 UNIT = "atom-timesteps/s"
 FP32_LANES_PER_SM = 128
 FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n,m) = (9,6)
-# DRAM bytes (read + write) of one force-pass launch, from the ncu captures summarised in
-# profiles/k_force_ni2000_mixed.md and profiles/k_q_passes_ni50000_mixed.md (cold caches; the latter on the
-# same 50000-atom sphere with 0.1 A of disorder, whose lists are within 3 % of the timed state's).
-FORCE_DRAM_BYTES_PER_LAUNCH = {"ni2000": 249344, "ni50000": 11197440}
+# DRAM bytes (read + write) of one force-pass launch from an ncu capture (cold caches), with the
+# hash of the kernel sources the capture ran; reported only while those sources are unchanged.
+FORCE_DRAM_BYTES_PER_LAUNCH = {}
+KERNEL_SOURCES = ("paper_1210_3559_gb300/csrc/scmd_kernels.cu", "paper_1210_3559_gb300/csrc/scmd_device.cuh",
+                  "paper_1210_3559_gb300/csrc/scmd_quads.cu")
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def force_traffic(config: str):
+    rec = FORCE_DRAM_BYTES_PER_LAUNCH.get(config)
+    if rec is None or rec[1] != kernel_source_hash():
+        return None
+    return rec[0]
 
 
 # ------------------------------------------------------------------ workloads
@@ -238,11 +258,11 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None, help="timed iterations (default 40; ni2000: 400)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="ni2000", choices=["ni2000", "ni6000", "ni20000", "ni50000", "ni147", "ni147x64",
-                                                       "batched512"])
+    ap.add_argument("--config", default="batched512", choices=["batched512", "ni2000", "ni6000", "ni20000", "ni50000",
+                                                           "ni147", "ni147x64"])
     ap.add_argument("--md-steps", type=int, default=500, help="MD steps per timed iteration")
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
     ap.add_argument("--no-tune", action="store_true")
@@ -255,6 +275,8 @@ def main():
     ap.add_argument("--drift-steps", type=int, default=None, help="NVE steps of the drift runs (default: automatic)")
     ap.add_argument("--skip-analysis", action="store_true", help="no snapshots, drift runs or structure analysis")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 400 if args.config == "ni2000" else 40
     if args.warmup < 3:
         args.warmup = 3
 
@@ -365,7 +387,9 @@ def main():
         pairs_per_eval = pairs
     pair_rate = pairs_per_eval * md_steps_total * world / t_max
     peak_clock = (clocks or {}).get("sm_max_mhz", 2070.0)
-    peak_ops = 152 * FP32_LANES_PER_SM * peak_clock * 1e6
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_ops = n_sm * FP32_LANES_PER_SM * peak_clock * 1e6
+    ffma_measured, _ = scmd.md_fp32_peak(10)
     # algorithmic work of a launch: every ordered pair for all pairs; the pairs closer than rcut with a
     # cutoff (the candidates the cell or neighbour lists test are reported beside)
     useful_pairs = None
@@ -437,8 +461,9 @@ def main():
     # FP64-on-GPU form of the same workload, short sample (mixed vs FP64)
     fp64 = None
     if not args.skip_fp64 and prec == "mixed":
-        cfg64 = scmd.config(precision=scmd.MD_PREC_FP64, graph_chunk=min(M, 512), tune=0 if args.no_tune else 1,
-                            stream=stream.cuda_stream)
+        # built-in launch table: tuning FP64 at the large workloads would time hundreds of launches of
+        # tens of milliseconds each
+        cfg64 = scmd.config(precision=scmd.MD_PREC_FP64, graph_chunk=min(M, 512), tune=0, stream=stream.cuda_stream)
         c64 = scmd.md_create(cfg64, sizes, pos_f, vel_f, w["mass"], scmd.sc_params(rcut=rcut))
         m64 = max(10, M // 10)
         scmd.md_step(c64, m64, dt, therm(0))
@@ -456,7 +481,7 @@ def main():
         fp64 = {"value": natoms * m64 * reps64 / t64, "unit": UNIT,
                 "pair_evals_per_s": (useful_pairs if cells else pairs_per_eval) * m64 * reps64 / t64,
                 "path": {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists"}.get(p64, "all pairs"),
-                "sample": f"{reps64} x {m64} MD steps, same state and thermostat, per GPU"}
+                "sample": f"{reps64} x {m64} MD steps, same state and thermostat, per GPU, built-in launch shapes"}
         scmd.md_destroy(c64)
 
     # NVE energy drift from the melted state, MIXED and FP64 on the GPU (first cluster, or the first 8)
@@ -511,7 +536,7 @@ def main():
             "structure": structure,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
-                         "traffic": FORCE_DRAM_BYTES_PER_LAUNCH.get(args.config) if prec == "mixed" else None,
+                         "traffic": force_traffic(args.config) if prec == "mixed" else None,
                          "kernel": {"cells": "k_cell_force (force pass, cell list)",
                                     "neighbour lists": "k_q_force (force pass, quad lists)" if prec == "mixed"
                                     else "k_v_force (force pass, neighbour lists)"}.get(
@@ -519,7 +544,12 @@ def main():
                          "ms_per_launch": ms_f,
                          "density_pass_ms_per_launch": ms_d, "pairs_per_launch": alg_pairs,
                          "tested_pairs_per_launch": pairs if cells else None,
-                         "peak_basis": f"152 SMs x 128 FP32 lanes x {peak_clock:.0f} MHz (max SM clock)"},
+                         "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {peak_clock:.0f} MHz (max SM clock)",
+                         "peak_measured_ffma": ffma_measured / 1e12,
+                         "frac_of_measured_ffma": achieved / ffma_measured,
+                         "launch_timing": "CUDA events over back-to-back launches (PDL overlap as in the step graph)",
+                         "passes_ms_per_md_step": ms_d + ms_f if not cells else None,
+                         "ms_per_md_step": 1e3 * t_max / md_steps_total},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * natoms * 3 * 8), "d2h_bytes_per_step": int(2 * natoms * 3 * 8),
                     "iterations": e2e_iters},

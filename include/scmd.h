@@ -24,9 +24,12 @@
  * back: cluster b owns atoms off_b .. off_b + sizes[b] - 1, off_b = sum_{c<b} sizes[c].
  *
  * Conventions shared by every entry point:
- *   - Ownership: the caller owns every pointer it passes; the library copies
- *     inputs and never keeps a caller pointer after returning. Device memory is
- *     owned by the context and freed by md_destroy.
+ *   - Ownership: the caller owns every pointer it passes (host arrays, and the
+ *     device arrays of the *_device calls); the library copies inputs and never
+ *     keeps or frees a caller pointer after returning. A context's own device
+ *     memory is allocated in stream order on the context's stream
+ *     (cudaMallocAsync on md_config.stream, or on the stream the library creates)
+ *     and freed by md_destroy.
  *   - Errors: every call returns an md_status and never aborts, prints or traps
  *     the GPU. After an error the context stays valid for md_last_error and
  *     md_destroy; MD_ERR_CUDA means a CUDA call failed (message in
@@ -47,7 +50,7 @@
 extern "C" {
 #endif
 
-#define SCMD_ABI_VERSION 1
+#define SCMD_ABI_VERSION 2
 
 typedef enum {
     MD_OK = 0,
@@ -55,7 +58,9 @@ typedef enum {
     MD_ERR_CUDA = 2,      /* a CUDA runtime call failed or no suitable GPU            */
     MD_ERR_OOM = 3,       /* device or host allocation failed                         */
     MD_ERR_NONFINITE = 4, /* a force, position or velocity became NaN/Inf on the GPU  */
-    MD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up                       */
+    MD_ERR_TIMEOUT = 5,   /* reserved for a bounded device-side wait that gives up; no
+                             kernel of this version waits on another, so no call
+                             returns it                                               */
     MD_ERR_STATE = 6      /* call not valid in the context's current state            */
 } md_status;
 
@@ -169,6 +174,24 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
                     const md_sc_params* params, md_ctx** out);
 
 /*
+ * md_create from device memory the caller owns (for example PyTorch CUDA
+ * tensors): pos_dev[Ntot][3], vel_dev[Ntot][3] (may be NULL: zero velocities)
+ * and mass_dev[Ntot] are contiguous float64 arrays in the same layout as
+ * md_create's, in device memory of the current device; sizes is a host array.
+ * The work is ordered on cfg->stream, which must be the stream that produced
+ * the arrays (or be synchronised with it). The arrays are only read, never kept
+ * or freed. On the all-pairs path they are validated on the GPU (finite
+ * positions and velocities, finite masses > 0; else MD_ERR_INVALID) and copied
+ * into the context's layout by a kernel, with no host round trip. The cell and
+ * neighbour-list paths size each cluster's grid from its positions on the host,
+ * so there the three arrays are read back once first. Results are identical to
+ * md_create with the same values. Errors as md_create.
+ */
+md_status md_create_device(const md_config* cfg, int32_t n_clusters, const int32_t* sizes,
+                           const double* pos_dev, const double* vel_dev, const double* mass_dev,
+                           const md_sc_params* params, md_ctx** out);
+
+/*
  * Evaluate the potential energy and forces at the current positions with the
  * two passes (density, then forces). epot_eV[n_clusters] and
  * forces_eV_per_A[Ntot][3] are host arrays; either may be NULL.
@@ -209,6 +232,16 @@ md_status md_clear_history(md_ctx* ctx);
 md_status md_get_state(md_ctx* ctx, double* pos_A, double* vel_A_per_fs, int64_t* step);
 md_status md_set_state(md_ctx* ctx, const double* pos_A, const double* vel_A_per_fs, int64_t step);
 
+/* The same checkpoint through caller-owned device arrays [Ntot][3] (float64,
+ * current device), converted to and from the context's layout by kernels on
+ * the context's stream; both calls return after that work has completed.
+ * md_get_state_device: either array may be NULL. md_set_state_device: both are
+ * required; the values are validated on the GPU first (non-finite ->
+ * MD_ERR_INVALID and the context is left unchanged), then the forces are
+ * recomputed, as in md_set_state. */
+md_status md_get_state_device(md_ctx* ctx, double* pos_dev, double* vel_dev, int64_t* step);
+md_status md_set_state_device(md_ctx* ctx, const double* pos_dev, const double* vel_dev, int64_t step);
+
 /* MIXED precision keeps pair coordinates in FP32 relative to one origin per
  * cluster, set to the cluster's centre of mass when the context is created and
  * kept fixed afterwards (so that forces depend on the positions alone and a
@@ -242,9 +275,10 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
 
 /*
  * Mean device time (ms) of one launch of the density pass and of the force
- * pass, timed alone with CUDA events on the context's stream over reps
- * launches after warm-up (with the neighbour lists in FP64, each pass includes
- * its gather kernel). Pair-evaluation counts per launch are returned in *pairs
+ * pass: CUDA events on the context's stream around reps back-to-back launches
+ * of one pass after warm-up (consecutive launches overlap through programmatic
+ * dependent launch as inside a step; with the neighbour lists in FP64, each
+ * pass includes its gather kernel). Pair-evaluation counts per launch are returned in *pairs
  * (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for the cell
  * path, every atom times the atoms of the 5 x 5 x 5 cell octants around its own,
  * self included, as binned at the current positions; for the MIXED lists, 16
@@ -253,6 +287,16 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
  */
 md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* ms_force,
                          double* pairs);
+
+/*
+ * The FP32 lane-operation rate of the current device, measured: every SM runs
+ * independent FFMA chains (one FFMA = one lane operation) for reps timed
+ * launches, *measured_ops_per_s = lane operations / CUDA-event time. Also
+ * *derived_ops_per_s = SMs x 128 FP32 lanes x the maximum SM clock. This is
+ * the denominator of the pair passes' roofline (they are FP32-pipe bound).
+ * reps >= 1; MD_ERR_CUDA without a GPU.
+ */
+md_status md_fp32_peak(int32_t reps, double* measured_ops_per_s, double* derived_ops_per_s);
 
 /* Number of GPU kernels issued per md_step step (all pairs: 2, cells: 5,
  * neighbour lists: 8 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
@@ -293,7 +337,7 @@ md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int
  * time-critical loop that must never enter the CUDA allocator.
  *   pos_dev[n_atoms][3]     positions (Angstrom), device memory, read only
  *   forces_dev[n_atoms][3]  forces (eV/A), device memory, written
- *   epot_dev[1]             potential energy of Eq. 1 (eV), device memory, written
+ *   epot_dev[1]             total Sutton-Chen potential energy (eV), device memory, written
  *   stream                  cudaStream_t on which the work is queued (0 = default stream)
  * The caller owns all three buffers. The arithmetic is that of md_energy_forces
  * in MIXED precision (FP32 pair terms, FP64 rho and energy), all pairs, or the
@@ -307,7 +351,12 @@ md_status md_langevin_normals(uint64_t seed, uint32_t cluster, int64_t step, int
  * calls whose work overlaps on the GPU (other streams, other host threads) race and
  * must be serialised by the caller. The first call on each device looks up the
  * array's device address (with that device current); make that first call before
- * starting any stream capture.
+ * starting any stream capture. That address belongs to the CUDA context current at
+ * the first call: after cudaDeviceReset (or any teardown of the device's primary
+ * context) the next call looks it up again, so that call too must come before any
+ * capture. The outputs are not checked: coincident atoms or non-finite positions
+ * give non-finite forces and energy while the call still returns MD_OK, so a
+ * caller that may pass such input tests the outputs for finiteness itself.
  */
 md_status md_energy_forces_noalloc(const double* pos_dev, int32_t n_atoms, const md_sc_params* params,
                                    double* forces_dev, double* epot_dev, uint64_t stream);

@@ -71,6 +71,7 @@ struct md_ctx {
     bool own_stream = false;
     // device buffers
     int32_t *d_poff = nullptr, *d_nreal = nullptr, *d_clg = nullptr, *d_status = nullptr;
+    int32_t* d_off = nullptr;  // [B+1] unpadded cluster offsets (caller layout of the state arrays)
     double *d_x = nullptr, *d_v = nullptr, *d_mass = nullptr, *d_rho = nullptr, *d_origin = nullptr;
     double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr, *d_hs = nullptr;
     float* d_sig0 = nullptr;
@@ -147,6 +148,19 @@ md_status fail(md_ctx* c, md_status st, const char* fmt, ...) {
                         __LINE__);                                                                \
         }                                                                                         \
     } while (0)
+
+// Device memory of a context is allocated and freed in stream order on the context's stream
+// (the caller's stream when md_config.stream is set).
+template <class T> cudaError_t dmalloc(md_ctx* c, T** p, size_t bytes) {
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, c->stream);
+}
+void dfree(md_ctx* c, void* p) {
+    if (!p) return;
+    if (c->stream)
+        cudaFreeAsync(p, c->stream);
+    else
+        cudaFree(p);
+}
 
 bool finite_all(const double* p, size_t n) {
     for (size_t k = 0; k < n; ++k)
@@ -463,7 +477,7 @@ void drop_graphs(md_ctx* c) {
 
 void free_all(md_ctx* c) {
     drop_graphs(c);
-    void* ptrs[] = {c->d_poff, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
+    void* ptrs[] = {c->d_poff, c->d_off, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
@@ -475,8 +489,8 @@ void free_all(md_ctx* c) {
                     c->d_vposg, c->d_vxref, c->d_vdmax,
                     c->sb.com, c->sb.core, c->sb.ncore, c->sb.hist, c->sb.ref, c->sb.ref_com, c->sb.sel, c->sb.msd,
                     c->sb.nsel, c->sb.nb, c->sb.nnb, c->sb.cls, c->sb.counts, c->sb.capped};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dfree(c, p);
+    if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->h_run) cudaFreeHost(c->h_run);
     if (c->h_step) cudaFreeHost(c->h_step);
@@ -596,8 +610,26 @@ int32_t md_abi_version(void) { return SCMD_ABI_VERSION; }
 
 const char* md_last_error(const md_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
-md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* sizes, const double* pos,
-                    const double* vel, const double* mass, const md_sc_params* prm, md_ctx** out) {
+}  // extern "C"
+
+namespace {
+
+// Pair path that md_create resolves from the configuration: 0 all pairs, 1 cells, 2 neighbour lists.
+int resolve_path(const md_config* cfg, const md_sc_params* prm, int32_t n_clusters, const int32_t* sizes) {
+    int maxn = 0;
+    for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
+    // automatic: with a cutoff and a large cluster (or a shifted cutoff), the neighbour lists (quad
+    // lists in MIXED, per-atom lists in FP64)
+    const bool big = cfg->path == MD_PATH_AUTO && prm->rcut_A > 0 && (maxn >= kAutoCellsMinAtoms || prm->cutoff_shift);
+    const bool verlet = cfg->path == MD_PATH_VERLET || big;
+    const bool cells = verlet || cfg->path == MD_PATH_CELLS;
+    return verlet ? 2 : (cells ? 1 : 0);
+}
+
+// md_create (host arrays) and md_create_device on the all-pairs path (device arrays: on_device;
+// the values are then validated on the GPU before they are used).
+md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* sizes, const double* pos,
+                      const double* vel, const double* mass, bool on_device, const md_sc_params* prm, md_ctx** out) {
     g_create_error.clear();
     if (!out) return fail(nullptr, MD_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -626,10 +658,13 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         ntot += sizes[b];
     }
     if (ntot > 200000000) return fail(nullptr, MD_ERR_INVALID, "too many atoms");
-    if (!finite_all(pos, 3 * ntot)) return fail(nullptr, MD_ERR_INVALID, "non-finite position");
-    if (vel && !finite_all(vel, 3 * ntot)) return fail(nullptr, MD_ERR_INVALID, "non-finite velocity");
-    for (int64_t k = 0; k < ntot; ++k)
-        if (!(std::isfinite(mass[k]) && mass[k] > 0)) return fail(nullptr, MD_ERR_INVALID, "mass %lld invalid", (long long)k);
+    if (!on_device) {
+        if (!finite_all(pos, 3 * ntot)) return fail(nullptr, MD_ERR_INVALID, "non-finite position");
+        if (vel && !finite_all(vel, 3 * ntot)) return fail(nullptr, MD_ERR_INVALID, "non-finite velocity");
+        for (int64_t k = 0; k < ntot; ++k)
+            if (!(std::isfinite(mass[k]) && mass[k] > 0))
+                return fail(nullptr, MD_ERR_INVALID, "mass %lld invalid", (long long)k);
+    }
 
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -697,14 +732,12 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     P.shm = P.shift ? std::pow(P.rcut, -(double)P.m) : 0.0;
     P.shn = P.shift ? std::pow(P.rcut, -(double)P.n) : 0.0;
     {
-        int maxn = 0;
-        for (int b = 0; b < n_clusters; ++b) maxn = std::max(maxn, sizes[b]);
-        // automatic: with a cutoff and a large cluster (or a shifted cutoff), the neighbour lists (quad
-        // lists in MIXED, per-atom lists in FP64)
-        const bool big = cfg->path == MD_PATH_AUTO && P.rcut > 0 && (maxn >= kAutoCellsMinAtoms || P.shift);
-        const bool verlet = cfg->path == MD_PATH_VERLET || big;
-        const bool cells = verlet || cfg->path == MD_PATH_CELLS || big;
-        c->path = verlet ? 2 : (cells ? 1 : 0);
+        c->path = resolve_path(cfg, prm, n_clusters, sizes);
+        const bool cells = c->path >= 1;
+        if (cells && on_device) {  // md_create_device reads the positions back for the cell grids first
+            delete c;
+            return fail(nullptr, MD_ERR_INVALID, "internal: device positions on a cell path");
+        }
         // FP64 lists address a pair's place in 32 bits: nslot * kVMax < 2^32
         const int64_t vmax_atoms = cfg->precision == MD_PREC_FP64 ? (1 << 23) : (1 << 26);
         if (c->path == 2 && c->ntot >= vmax_atoms) {
@@ -745,32 +778,33 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
     }
     CKC(configure_kernels());
     const size_t np = c->npad;
-    CKC(cudaMalloc(&c->d_poff, sizeof(int32_t) * (n_clusters + 1)));
-    CKC(cudaMalloc(&c->d_nreal, sizeof(int32_t) * n_clusters));
-    CKC(cudaMalloc(&c->d_clg, sizeof(int32_t) * c->ngroups));
-    CKC(cudaMalloc(&c->d_status, sizeof(int32_t)));
-    CKC(cudaMalloc(&c->d_x, sizeof(double) * 3 * np));
-    CKC(cudaMalloc(&c->d_v, sizeof(double) * 3 * np));
-    CKC(cudaMalloc(&c->d_mass, sizeof(double) * np));
-    CKC(cudaMalloc(&c->d_rho, sizeof(double) * np));
-    CKC(cudaMalloc(&c->d_origin, sizeof(double) * 3 * n_clusters));
-    CKC(cudaMalloc(&c->d_hs, sizeof(double) * np));
-    CKC(cudaMalloc(&c->d_sig0, sizeof(float) * np));
+    CKC(dmalloc(c, &c->d_poff, sizeof(int32_t) * (n_clusters + 1)));
+    CKC(dmalloc(c, &c->d_off, sizeof(int32_t) * (n_clusters + 1)));
+    CKC(dmalloc(c, &c->d_nreal, sizeof(int32_t) * n_clusters));
+    CKC(dmalloc(c, &c->d_clg, sizeof(int32_t) * c->ngroups));
+    CKC(dmalloc(c, &c->d_status, sizeof(int32_t)));
+    CKC(dmalloc(c, &c->d_x, sizeof(double) * 3 * np));
+    CKC(dmalloc(c, &c->d_v, sizeof(double) * 3 * np));
+    CKC(dmalloc(c, &c->d_mass, sizeof(double) * np));
+    CKC(dmalloc(c, &c->d_rho, sizeof(double) * np));
+    CKC(dmalloc(c, &c->d_origin, sizeof(double) * 3 * n_clusters));
+    CKC(dmalloc(c, &c->d_hs, sizeof(double) * np));
+    CKC(dmalloc(c, &c->d_sig0, sizeof(float) * np));
     if (cfg->precision == MD_PREC_MIXED) {
         // Langevin normals of a whole chunk are drawn ahead of it; the buffer holds at most
         // 256 MB, which bounds the chunk length for very large batches.
         const size_t per_step = sizeof(float4) * np;
         c->noise_steps = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->cfg.graph_chunk, (256u << 20) / per_step));
-        CKC(cudaMalloc(&c->d_noise, per_step * c->noise_steps));
+        CKC(dmalloc(c, &c->d_noise, per_step * c->noise_steps));
     }
-    CKC(cudaMalloc(&c->d_part, sizeof(double) * kObsFields * c->ngroups));
-    CKC(cudaMalloc(&c->d_ke, sizeof(double) * c->ngroups));
-    CKC(cudaMalloc(&c->d_hist, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
-    CKC(cudaMalloc(&c->d_f, (size_t)elem_size(c) * 3 * np));
-    CKC(cudaMalloc(&c->d_mirror, (size_t)vec4_size(c) * np));
-    CKC(cudaMalloc(&c->d_posg, (size_t)vec4_size(c) * np));
-    CKC(cudaMalloc(&c->d_step, sizeof(int64_t)));
-    CKC(cudaMalloc(&c->d_run, sizeof(Run)));
+    CKC(dmalloc(c, &c->d_part, sizeof(double) * kObsFields * c->ngroups));
+    CKC(dmalloc(c, &c->d_ke, sizeof(double) * c->ngroups));
+    CKC(dmalloc(c, &c->d_hist, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
+    CKC(dmalloc(c, &c->d_f, (size_t)elem_size(c) * 3 * np));
+    CKC(dmalloc(c, &c->d_mirror, (size_t)vec4_size(c) * np));
+    CKC(dmalloc(c, &c->d_posg, (size_t)vec4_size(c) * np));
+    CKC(dmalloc(c, &c->d_step, sizeof(int64_t)));
+    CKC(dmalloc(c, &c->d_run, sizeof(Run)));
     if (c->path >= 1) {
         std::vector<int32_t> cell_cl(c->n_cells), order(c->n_cells);
         std::vector<double> depth(c->n_cells);
@@ -788,26 +822,26 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         // ones fill the tail of the pass instead of extending it
         for (int k = 0; k < c->n_cells; ++k) order[k] = k;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return depth[a] < depth[b]; });
-        CKC(cudaMalloc(&c->d_grid, sizeof(CellGrid) * n_clusters));
-        CKC(cudaMalloc(&c->d_cell_cl, sizeof(int32_t) * c->n_cells));
-        CKC(cudaMalloc(&c->d_cell_order, sizeof(int32_t) * c->n_cells));
-        CKC(cudaMemcpy(c->d_cell_order, order.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice));
-        CKC(cudaMalloc(&c->d_cell_count, sizeof(int32_t) * c->n_cells));
-        CKC(cudaMalloc(&c->d_cell_atoms, sizeof(int32_t) * kCellCap * (size_t)c->n_cells));
-        CKC(cudaMalloc(&c->d_cell_oct, sizeof(int32_t) * 9 * (size_t)c->n_cells));
-        CKC(cudaMalloc(&c->d_cell_obyte, (size_t)kCellCap * c->n_cells));
-        CKC(cudaMemset(c->d_cell_oct, 0, sizeof(int32_t) * 9 * (size_t)c->n_cells));
-        CKC(cudaMalloc(&c->d_cpos, (size_t)vec4_size(c) * kCellCap * c->n_cells));
-        CKC(cudaMalloc(&c->d_cposg, (size_t)vec4_size(c) * kCellCap * c->n_cells));
-        CKC(cudaMalloc(&c->d_eatom, sizeof(double) * 2 * np));
-        CKC(cudaMalloc(&c->d_obs_x, sizeof(double) * 3 * np));
-        CKC(cudaMalloc(&c->d_obs_v, sizeof(double) * 3 * np));
-        CKC(cudaMemcpy(c->d_grid, c->grids.data(), sizeof(CellGrid) * n_clusters, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_cell_cl, cell_cl.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice));
-        CKC(cudaMemset(c->d_cell_count, 0, sizeof(int32_t) * c->n_cells));
-        CKC(cudaMemset(c->d_eatom, 0, sizeof(double) * 2 * np));
-        CKC(cudaMemset(c->d_obs_x, 0, sizeof(double) * 3 * np));
-        CKC(cudaMemset(c->d_obs_v, 0, sizeof(double) * 3 * np));
+        CKC(dmalloc(c, &c->d_grid, sizeof(CellGrid) * n_clusters));
+        CKC(dmalloc(c, &c->d_cell_cl, sizeof(int32_t) * c->n_cells));
+        CKC(dmalloc(c, &c->d_cell_order, sizeof(int32_t) * c->n_cells));
+        CKC(cudaMemcpyAsync(c->d_cell_order, order.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice, c->stream));
+        CKC(dmalloc(c, &c->d_cell_count, sizeof(int32_t) * c->n_cells));
+        CKC(dmalloc(c, &c->d_cell_atoms, sizeof(int32_t) * kCellCap * (size_t)c->n_cells));
+        CKC(dmalloc(c, &c->d_cell_oct, sizeof(int32_t) * 9 * (size_t)c->n_cells));
+        CKC(dmalloc(c, &c->d_cell_obyte, (size_t)kCellCap * c->n_cells));
+        CKC(cudaMemsetAsync(c->d_cell_oct, 0, sizeof(int32_t) * 9 * (size_t)c->n_cells, c->stream));
+        CKC(dmalloc(c, &c->d_cpos, (size_t)vec4_size(c) * kCellCap * c->n_cells));
+        CKC(dmalloc(c, &c->d_cposg, (size_t)vec4_size(c) * kCellCap * c->n_cells));
+        CKC(dmalloc(c, &c->d_eatom, sizeof(double) * 2 * np));
+        CKC(dmalloc(c, &c->d_obs_x, sizeof(double) * 3 * np));
+        CKC(dmalloc(c, &c->d_obs_v, sizeof(double) * 3 * np));
+        CKC(cudaMemcpyAsync(c->d_grid, c->grids.data(), sizeof(CellGrid) * n_clusters, cudaMemcpyHostToDevice, c->stream));
+        CKC(cudaMemcpyAsync(c->d_cell_cl, cell_cl.data(), sizeof(int32_t) * c->n_cells, cudaMemcpyHostToDevice, c->stream));
+        CKC(cudaMemsetAsync(c->d_cell_count, 0, sizeof(int32_t) * c->n_cells, c->stream));
+        CKC(cudaMemsetAsync(c->d_eatom, 0, sizeof(double) * 2 * np, c->stream));
+        CKC(cudaMemsetAsync(c->d_obs_x, 0, sizeof(double) * 3 * np, c->stream));
+        CKC(cudaMemsetAsync(c->d_obs_v, 0, sizeof(double) * 3 * np, c->stream));
     }
     if (c->path == 2) {
         const bool quads = cfg->precision == MD_PREC_MIXED;
@@ -815,77 +849,78 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
         c->nqmax = quads ? (int)((c->ntot + 3 * (int64_t)c->n_cells + 3) / 4) : 0;
         const size_t ns = quads ? 4 * (size_t)c->nqmax : (size_t)c->ntot;
         c->nslot = (int32_t)ns;
-        CKC(cudaMalloc(&c->d_vorder, sizeof(int32_t) * ns));
-        CKC(cudaMalloc(&c->d_vslotof, sizeof(int32_t) * np));
-        CKC(cudaMalloc(&c->d_vhi, (size_t)vec4_size(c) * ns));
-        CKC(cudaMalloc(&c->d_vposg, (size_t)vec4_size(c) * ns));
-        CKC(cudaMalloc(&c->d_vxref, sizeof(double) * 3 * ns));
-        CKC(cudaMalloc(&c->d_vdmax, sizeof(uint32_t) * 2));
-        CKC(cudaMemset(c->d_vdmax, 0, sizeof(uint32_t) * 2));
+        CKC(dmalloc(c, &c->d_vorder, sizeof(int32_t) * ns));
+        CKC(dmalloc(c, &c->d_vslotof, sizeof(int32_t) * np));
+        CKC(dmalloc(c, &c->d_vhi, (size_t)vec4_size(c) * ns));
+        CKC(dmalloc(c, &c->d_vposg, (size_t)vec4_size(c) * ns));
+        CKC(dmalloc(c, &c->d_vxref, sizeof(double) * 3 * ns));
+        CKC(dmalloc(c, &c->d_vdmax, sizeof(uint32_t) * 2));
+        CKC(cudaMemsetAsync(c->d_vdmax, 0, sizeof(uint32_t) * 2, c->stream));
         // every slot and entry starts as a valid index (atom 0, empty list)
-        CKC(cudaMemset(c->d_vorder, 0, sizeof(int32_t) * ns));
-        CKC(cudaMemset(c->d_vslotof, 0, sizeof(int32_t) * np));
-        CKC(cudaMemset(c->d_vxref, 0, sizeof(double) * 3 * ns));
+        CKC(cudaMemsetAsync(c->d_vorder, 0, sizeof(int32_t) * ns, c->stream));
+        CKC(cudaMemsetAsync(c->d_vslotof, 0, sizeof(int32_t) * np, c->stream));
+        CKC(cudaMemsetAsync(c->d_vxref, 0, sizeof(double) * 3 * ns, c->stream));
         if (quads) {
             const size_t nq = (size_t)c->nqmax;
-            CKC(cudaMalloc(&c->d_q_n, sizeof(int32_t)));
-            CKC(cudaMalloc(&c->d_cell_base, sizeof(int32_t) * c->n_cells));
-            CKC(cudaMalloc(&c->d_q_ref, sizeof(float4) * nq));
-            CKC(cudaMalloc(&c->d_q_box, sizeof(float4) * 2 * nq));
-            CKC(cudaMalloc(&c->d_q_cell, sizeof(int32_t) * nq));
-            CKC(cudaMalloc(&c->d_q_list, sizeof(int32_t) * kQMax * nq));
-            CKC(cudaMalloc(&c->d_q_count, sizeof(int32_t) * nq));
-            CKC(cudaMemset(c->d_q_n, 0, sizeof(int32_t)));
-            CKC(cudaMemset(c->d_cell_base, 0, sizeof(int32_t) * c->n_cells));
-            CKC(cudaMemset(c->d_q_count, 0, sizeof(int32_t) * nq));
+            CKC(dmalloc(c, &c->d_q_n, sizeof(int32_t)));
+            CKC(dmalloc(c, &c->d_cell_base, sizeof(int32_t) * c->n_cells));
+            CKC(dmalloc(c, &c->d_q_ref, sizeof(float4) * nq));
+            CKC(dmalloc(c, &c->d_q_box, sizeof(float4) * 2 * nq));
+            CKC(dmalloc(c, &c->d_q_cell, sizeof(int32_t) * nq));
+            CKC(dmalloc(c, &c->d_q_list, sizeof(int32_t) * kQMax * nq));
+            CKC(dmalloc(c, &c->d_q_count, sizeof(int32_t) * nq));
+            CKC(cudaMemsetAsync(c->d_q_n, 0, sizeof(int32_t), c->stream));
+            CKC(cudaMemsetAsync(c->d_cell_base, 0, sizeof(int32_t) * c->n_cells, c->stream));
+            CKC(cudaMemsetAsync(c->d_q_count, 0, sizeof(int32_t) * nq, c->stream));
         } else {
-            CKC(cudaMalloc(&c->d_vlist, sizeof(int32_t) * kVMax * ns));
-            CKC(cudaMalloc(&c->d_vcount, sizeof(int32_t) * ns));
-            CKC(cudaMalloc(&c->d_vsub, sizeof(int32_t) * kVLanes * ns));
-            CKC(cudaMalloc(&c->d_vslot, sizeof(int32_t)));
-            CKC(cudaMalloc(&c->d_vrcount, sizeof(int32_t) * ns));
-            CKC(cudaMalloc(&c->d_vrev, sizeof(uint64_t) * kVMax * ns));
-            CKC(cudaMalloc(&c->d_vrsub, sizeof(int32_t) * kVLanes * ns));
-            CKC(cudaMalloc(&c->d_vcl, sizeof(int2) * kVMax * ns));
-            CKC(cudaMalloc(&c->d_vcn, sizeof(int32_t) * ns));
-            CKC(cudaMalloc(&c->d_vflag, (size_t)kVMax * ns));
-            CKC(cudaMemset(c->d_vflag, 0, (size_t)kVMax * ns));
-            CKC(cudaMemset(c->d_vrsub, 0, sizeof(int32_t) * kVLanes * ns));
-            CKC(cudaMalloc(&c->d_hbuf, sizeof(double) * kVMax * ns));
-            CKC(cudaMalloc(&c->d_fbuf, sizeof(double4) * kVMax * ns));
-            CKC(cudaMalloc(&c->d_rho_half, sizeof(double) * ns));
-            CKC(cudaMalloc(&c->d_fhalf, sizeof(double4) * ns));
-            CKC(cudaMemset(c->d_vrcount, 0, sizeof(int32_t) * ns));
-            CKC(cudaMemset(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns));
-            CKC(cudaMemset(c->d_vcount, 0, sizeof(int32_t) * ns));
-            CKC(cudaMemset(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns));
+            CKC(dmalloc(c, &c->d_vlist, sizeof(int32_t) * kVMax * ns));
+            CKC(dmalloc(c, &c->d_vcount, sizeof(int32_t) * ns));
+            CKC(dmalloc(c, &c->d_vsub, sizeof(int32_t) * kVLanes * ns));
+            CKC(dmalloc(c, &c->d_vslot, sizeof(int32_t)));
+            CKC(dmalloc(c, &c->d_vrcount, sizeof(int32_t) * ns));
+            CKC(dmalloc(c, &c->d_vrev, sizeof(uint64_t) * kVMax * ns));
+            CKC(dmalloc(c, &c->d_vrsub, sizeof(int32_t) * kVLanes * ns));
+            CKC(dmalloc(c, &c->d_vcl, sizeof(int2) * kVMax * ns));
+            CKC(dmalloc(c, &c->d_vcn, sizeof(int32_t) * ns));
+            CKC(dmalloc(c, &c->d_vflag, (size_t)kVMax * ns));
+            CKC(cudaMemsetAsync(c->d_vflag, 0, (size_t)kVMax * ns, c->stream));
+            CKC(cudaMemsetAsync(c->d_vrsub, 0, sizeof(int32_t) * kVLanes * ns, c->stream));
+            CKC(dmalloc(c, &c->d_hbuf, sizeof(double) * kVMax * ns));
+            CKC(dmalloc(c, &c->d_fbuf, sizeof(double4) * kVMax * ns));
+            CKC(dmalloc(c, &c->d_rho_half, sizeof(double) * ns));
+            CKC(dmalloc(c, &c->d_fhalf, sizeof(double4) * ns));
+            CKC(cudaMemsetAsync(c->d_vrcount, 0, sizeof(int32_t) * ns, c->stream));
+            CKC(cudaMemsetAsync(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns, c->stream));
+            CKC(cudaMemsetAsync(c->d_vcount, 0, sizeof(int32_t) * ns, c->stream));
+            CKC(cudaMemsetAsync(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns, c->stream));
         }
     }
     for (int k = 0; k < 2; ++k) {
-        CKC(cudaMalloc(&c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
-        CKC(cudaMemcpy(c->items_d[k], c->items_h[k].data(), sizeof(Item) * c->items_h[k].size(), cudaMemcpyHostToDevice));
+        CKC(dmalloc(c, &c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
+        CKC(cudaMemcpyAsync(c->items_d[k], c->items_h[k].data(), sizeof(Item) * c->items_h[k].size(), cudaMemcpyHostToDevice, c->stream));
     }
     c->h_stage_n = std::max<size_t>(6 * np, 16);
     CKC(cudaMallocHost(&c->h_stage, sizeof(double) * c->h_stage_n));
     CKC(cudaMallocHost(&c->h_run, sizeof(Run)));
     CKC(cudaMallocHost(&c->h_step, sizeof(int64_t)));
     std::vector<int32_t> nreal(sizes, sizes + n_clusters);
-    CKC(cudaMemcpy(c->d_poff, c->poff.data(), sizeof(int32_t) * (n_clusters + 1), cudaMemcpyHostToDevice));
-    CKC(cudaMemcpy(c->d_nreal, nreal.data(), sizeof(int32_t) * n_clusters, cudaMemcpyHostToDevice));
-    CKC(cudaMemcpy(c->d_clg, c->cl_of_group.data(), sizeof(int32_t) * c->ngroups, cudaMemcpyHostToDevice));
-    CKC(cudaMemset(c->d_status, 0, sizeof(int32_t)));
-    CKC(cudaMemset(c->d_part, 0, sizeof(double) * kObsFields * c->ngroups));
-    CKC(cudaMemset(c->d_ke, 0, sizeof(double) * c->ngroups));
-    CKC(cudaMemset(c->d_hist, 0, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1)));
-    CKC(cudaMemset(c->d_f, 0, (size_t)elem_size(c) * 3 * np));
-    CKC(cudaMemset(c->d_rho, 0, sizeof(double) * np));
-    CKC(cudaMemset(c->d_step, 0, sizeof(int64_t)));
-    // masses (padding atoms get mass 1 so that no division by zero can occur)
-    {
+    CKC(cudaMemcpyAsync(c->d_poff, c->poff.data(), sizeof(int32_t) * (n_clusters + 1), cudaMemcpyHostToDevice, c->stream));
+    CKC(cudaMemcpyAsync(c->d_off, c->off.data(), sizeof(int32_t) * (n_clusters + 1), cudaMemcpyHostToDevice, c->stream));
+    CKC(cudaMemcpyAsync(c->d_nreal, nreal.data(), sizeof(int32_t) * n_clusters, cudaMemcpyHostToDevice, c->stream));
+    CKC(cudaMemcpyAsync(c->d_clg, c->cl_of_group.data(), sizeof(int32_t) * c->ngroups, cudaMemcpyHostToDevice, c->stream));
+    CKC(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
+    CKC(cudaMemsetAsync(c->d_part, 0, sizeof(double) * kObsFields * c->ngroups, c->stream));
+    CKC(cudaMemsetAsync(c->d_ke, 0, sizeof(double) * c->ngroups, c->stream));
+    CKC(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * kHistFields * (size_t)n_clusters * (c->hist_cap + 1), c->stream));
+    CKC(cudaMemsetAsync(c->d_f, 0, (size_t)elem_size(c) * 3 * np, c->stream));
+    CKC(cudaMemsetAsync(c->d_rho, 0, sizeof(double) * np, c->stream));
+    CKC(cudaMemsetAsync(c->d_step, 0, sizeof(int64_t), c->stream));
+    // masses (padding atoms get mass 1 so that no division by zero can occur; device input: k_import)
+    if (!on_device) {
         std::vector<double> m(np, 1.0);
         for (int b = 0; b < n_clusters; ++b)
             for (int a = 0; a < sizes[b]; ++a) m[c->poff[b] + a] = mass[c->off[b] + a];
-        CKC(cudaMemcpy(c->d_mass, m.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpyAsync(c->d_mass, m.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
     }
     // padding atoms of the mirror and posg buffers: far apart and far from everything, g = 0
     {
@@ -903,8 +938,8 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
                     memcpy(pad.data() + 32 * p, v, 32);
                 }
             }
-        CKC(cudaMemcpy(c->d_mirror, pad.data(), pad.size(), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_posg, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpyAsync(c->d_mirror, pad.data(), pad.size(), cudaMemcpyHostToDevice, c->stream));
+        CKC(cudaMemcpyAsync(c->d_posg, pad.data(), pad.size(), cudaMemcpyHostToDevice, c->stream));
     }
     fill_dev(c);
     c->shape[0] = default_shape(c, 0);
@@ -916,7 +951,20 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
             c->shape[1] = cached[1];
         }
     }
-    md_status st = upload_state(c, pos, vel);
+    md_status st = MD_OK;
+    if (on_device) {
+        CKC(launch_check_input(pos, vel, mass, ntot, c->d_status, c->stream));
+        int32_t flag = 0;
+        CKC(cudaMemcpyAsync(&flag, c->d_status, sizeof flag, cudaMemcpyDeviceToHost, c->stream));
+        CKC(cudaStreamSynchronize(c->stream));
+        if (flag & invalid_input_bit()) {
+            fail(c, MD_ERR_INVALID, "non-finite position or velocity, or a mass that is not finite and > 0");
+            return bail(MD_ERR_INVALID);
+        }
+        CKC(launch_import(c->dev, c->d_off, pos, vel, mass, c->stream));
+    } else {
+        st = upload_state(c, pos, vel);
+    }
     if (st != MD_OK) return bail(st);
     // Run parameters used by the observable reduction before the first md_step
     memset(c->h_run, 0, sizeof(Run));
@@ -935,6 +983,44 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
 #undef CKC
     *out = c;
     return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* sizes, const double* pos,
+                    const double* vel, const double* mass, const md_sc_params* prm, md_ctx** out) {
+    return create_impl(cfg, n_clusters, sizes, pos, vel, mass, false, prm, out);
+}
+
+md_status md_create_device(const md_config* cfg, int32_t n_clusters, const int32_t* sizes, const double* pos_dev,
+                           const double* vel_dev, const double* mass_dev, const md_sc_params* prm, md_ctx** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, MD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!cfg || !sizes || !pos_dev || !mass_dev || !prm) return fail(nullptr, MD_ERR_INVALID, "NULL argument");
+    if (n_clusters < 1) return fail(nullptr, MD_ERR_INVALID, "n_clusters must be >= 1");
+    int64_t ntot = 0;
+    for (int b = 0; b < n_clusters; ++b) {
+        if (sizes[b] < 1) return fail(nullptr, MD_ERR_INVALID, "cluster %d has size %d", b, sizes[b]);
+        ntot += sizes[b];
+    }
+    if (ntot > 200000000) return fail(nullptr, MD_ERR_INVALID, "too many atoms");
+    if (resolve_path(cfg, prm, n_clusters, sizes) == 0)
+        return create_impl(cfg, n_clusters, sizes, pos_dev, vel_dev, mass_dev, true, prm, out);
+    // The cell and neighbour-list paths size each cluster's grid from its positions on the host:
+    // the three arrays are read back once, on the given stream, and the context is made from them.
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cfg->stream);
+    std::vector<double> p(3 * (size_t)ntot), v(vel_dev ? 3 * (size_t)ntot : 0), m((size_t)ntot);
+    cudaError_t e = cudaMemcpyAsync(p.data(), pos_dev, sizeof(double) * p.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && vel_dev)
+        e = cudaMemcpyAsync(v.data(), vel_dev, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.data(), mass_dev, sizeof(double) * m.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return fail(nullptr, MD_ERR_CUDA, "reading the device arrays failed: %s", cudaGetErrorString(e));
+    return create_impl(cfg, n_clusters, sizes, p.data(), vel_dev ? v.data() : nullptr, m.data(), false, prm, out);
 }
 
 void md_destroy(md_ctx* ctx) {
@@ -1120,6 +1206,36 @@ md_status md_set_state(md_ctx* c, const double* pos, const double* vel, int64_t 
     return check_status(c);
 }
 
+md_status md_get_state_device(md_ctx* c, double* pos_dev, double* vel_dev, int64_t* step) {
+    if (!c) return MD_ERR_INVALID;
+    if (pos_dev || vel_dev) {
+        CK(c, launch_export(c->dev, c->d_off, pos_dev, vel_dev, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (step) *step = c->step;
+    return MD_OK;
+}
+
+md_status md_set_state_device(md_ctx* c, const double* pos_dev, const double* vel_dev, int64_t step) {
+    if (!c || !pos_dev || !vel_dev) return MD_ERR_INVALID;
+    if (step < 0) return fail(c, MD_ERR_INVALID, "step < 0");
+    // validate first, so that a rejected state leaves the context as it was
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
+    CK(c, launch_check_input(pos_dev, vel_dev, nullptr, c->ntot, c->d_status, c->stream));
+    int32_t flag = 0;
+    CK(c, cudaMemcpyAsync(&flag, c->d_status, sizeof flag, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (flag & invalid_input_bit()) {
+        CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
+        return fail(c, MD_ERR_INVALID, "non-finite position or velocity");
+    }
+    CK(c, launch_import(c->dev, c->d_off, pos_dev, vel_dev, nullptr, c->stream));
+    c->step = step;
+    md_status st = recompute_forces(c, false);
+    if (st != MD_OK) return st;
+    return check_status(c);
+}
+
 md_status md_recenter(md_ctx* c) {
     if (!c) return MD_ERR_INVALID;
     md_status st = recompute_forces(c, true);
@@ -1167,33 +1283,26 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
         CK(c, density());
         CK(c, force());
     }
-    std::vector<cudaEvent_t> ev(2 * reps + 2);
-    for (auto& e : ev) CK(c, cudaEventCreate(&e));
+    // reps launches back to back between one pair of events: consecutive launches overlap through
+    // programmatic dependent launch exactly as they do inside the step graph, so the mean is the
+    // pass's cost within a step (one event pair per launch would add a serialising gap to each)
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
     double td = 0, tf = 0;
     md_status st = MD_OK;
-    for (int k = 0; k < reps && st == MD_OK; ++k) {
-        cudaEventRecord(ev[2 * k], c->stream);
-        if (density() != cudaSuccess) st = MD_ERR_CUDA;
-        cudaEventRecord(ev[2 * k + 1], c->stream);
-    }
-    cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < reps && st == MD_OK; ++k) {
+    for (int which = 0; which < 2 && st == MD_OK; ++which) {
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < reps && st == MD_OK; ++k)
+            if ((which == 0 ? density() : force()) != cudaSuccess) st = MD_ERR_CUDA;
+        cudaEventRecord(e1, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = MD_ERR_CUDA;
         float ms = 0;
-        cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
-        td += ms;
+        if (st == MD_OK) cudaEventElapsedTime(&ms, e0, e1);
+        (which == 0 ? td : tf) = ms;
     }
-    for (int k = 0; k < reps && st == MD_OK; ++k) {
-        cudaEventRecord(ev[2 * k], c->stream);
-        if (force() != cudaSuccess) st = MD_ERR_CUDA;
-        cudaEventRecord(ev[2 * k + 1], c->stream);
-    }
-    cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < reps && st == MD_OK; ++k) {
-        float ms = 0;
-        cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
-        tf += ms;
-    }
-    for (auto& e : ev) cudaEventDestroy(e);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
     if (ms_d) *ms_d = td / reps;
     if (ms_f) *ms_f = tf / reps;
@@ -1296,9 +1405,9 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     const size_t nb = sizeof(double) * 3 * c->npad;
     const size_t fb = (size_t)elem_size(c) * 3 * c->npad;
     void *sx = nullptr, *sv = nullptr, *sf = nullptr;
-    CK(c, cudaMalloc(&sx, nb));
-    CK(c, cudaMalloc(&sv, nb));
-    CK(c, cudaMalloc(&sf, fb));
+    CK(c, dmalloc(c, &sx, nb));
+    CK(c, dmalloc(c, &sv, nb));
+    CK(c, dmalloc(c, &sf, fb));
     CK(c, cudaMemcpyAsync(sx, c->d_x, nb, cudaMemcpyDeviceToDevice, c->stream));
     CK(c, cudaMemcpyAsync(sv, c->d_v, nb, cudaMemcpyDeviceToDevice, c->stream));
     CK(c, cudaMemcpyAsync(sf, c->d_f, fb, cudaMemcpyDeviceToDevice, c->stream));
@@ -1341,9 +1450,9 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     CK(c, cudaMemcpyAsync(c->d_f, sf, fb, cudaMemcpyDeviceToDevice, c->stream));
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    cudaFree(sx);
-    cudaFree(sv);
-    cudaFree(sf);
+    dfree(c, sx);
+    dfree(c, sv);
+    dfree(c, sf);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != MD_OK) return st;
@@ -1412,19 +1521,19 @@ md_status struct_alloc(md_ctx* c) {
     if (c->sb.com) return MD_OK;
     const size_t np = (size_t)c->npad, B = (size_t)c->B;
     StructBufs& b = c->sb;
-    CK(c, cudaMalloc(&b.com, sizeof(double) * 3 * B));
-    CK(c, cudaMalloc(&b.core, sizeof(int32_t) * np));
-    CK(c, cudaMalloc(&b.ncore, sizeof(int32_t) * B));
-    CK(c, cudaMalloc(&b.ref, sizeof(double) * 3 * np));
-    CK(c, cudaMalloc(&b.ref_com, sizeof(double) * 3 * B));
-    CK(c, cudaMalloc(&b.sel, np));
-    CK(c, cudaMalloc(&b.msd, sizeof(double) * B));
-    CK(c, cudaMalloc(&b.nsel, sizeof(int32_t) * B));
-    CK(c, cudaMalloc(&b.nb, sizeof(int32_t) * kNbCap * np));
-    CK(c, cudaMalloc(&b.nnb, sizeof(int32_t) * np));
-    CK(c, cudaMalloc(&b.cls, np));
-    CK(c, cudaMalloc(&b.counts, sizeof(int32_t) * 4 * B));
-    CK(c, cudaMalloc(&b.capped, sizeof(int32_t) * B));
+    CK(c, dmalloc(c, &b.com, sizeof(double) * 3 * B));
+    CK(c, dmalloc(c, &b.core, sizeof(int32_t) * np));
+    CK(c, dmalloc(c, &b.ncore, sizeof(int32_t) * B));
+    CK(c, dmalloc(c, &b.ref, sizeof(double) * 3 * np));
+    CK(c, dmalloc(c, &b.ref_com, sizeof(double) * 3 * B));
+    CK(c, dmalloc(c, &b.sel, np));
+    CK(c, dmalloc(c, &b.msd, sizeof(double) * B));
+    CK(c, dmalloc(c, &b.nsel, sizeof(int32_t) * B));
+    CK(c, dmalloc(c, &b.nb, sizeof(int32_t) * kNbCap * np));
+    CK(c, dmalloc(c, &b.nnb, sizeof(int32_t) * np));
+    CK(c, dmalloc(c, &b.cls, np));
+    CK(c, dmalloc(c, &b.counts, sizeof(int32_t) * 4 * B));
+    CK(c, dmalloc(c, &b.capped, sizeof(int32_t) * B));
     CK(c, cudaMemsetAsync(b.nnb, 0, sizeof(int32_t) * np, c->stream));
     CK(c, cudaMemsetAsync(b.cls, 0, np, c->stream));
     return MD_OK;
@@ -1441,10 +1550,10 @@ md_status md_rdf(md_ctx* c, double r_core_A, double bin_A, int32_t nbins, int64_
     md_status st = struct_alloc(c);
     if (st != MD_OK) return st;
     if (nbins > c->sb_nbins) {
-        if (c->sb.hist) cudaFree(c->sb.hist);
+        dfree(c, c->sb.hist);
         c->sb.hist = nullptr;
         c->sb_nbins = 0;
-        CK(c, cudaMalloc(&c->sb.hist, sizeof(unsigned long long) * (size_t)c->B * nbins));
+        CK(c, dmalloc(c, &c->sb.hist, sizeof(unsigned long long) * (size_t)c->B * nbins));
         c->sb_nbins = nbins;
     }
     CK(c, cudaMemsetAsync(c->sb.hist, 0, sizeof(unsigned long long) * (size_t)c->B * nbins, c->stream));

@@ -248,6 +248,14 @@ cudaError_t launch_rdf(const Dev& d, const StructBufs& sb, double r_core, double
 cudaError_t launch_msd_ref(const Dev& d, const StructBufs& sb, double r_core, cudaStream_t s);
 cudaError_t launch_msd(const Dev& d, const StructBufs& sb, cudaStream_t s);
 cudaError_t launch_cna(const Dev& d, const StructBufs& sb, double r_nb, cudaStream_t s);
+// State exchange with caller-owned device arrays (defined in scmd_import.cu). off[B+1] are the
+// unpadded cluster offsets of the caller's [Ntot][3] / [Ntot] arrays.
+int invalid_input_bit();  // status bit launch_check_input sets
+cudaError_t launch_check_input(const double* pos, const double* vel, const double* mass, int64_t ntot,
+                               int32_t* status, cudaStream_t s);
+cudaError_t launch_import(const Dev& d, const int32_t* off, const double* pos, const double* vel,
+                          const double* mass, cudaStream_t s);
+cudaError_t launch_export(const Dev& d, const int32_t* off, double* pos, double* vel, cudaStream_t s);
 // The calling thread's error message returned by md_last_error(NULL) (defined in scmd_api.cu).
 void set_thread_error(const char* msg);
 cudaError_t configure_kernels();

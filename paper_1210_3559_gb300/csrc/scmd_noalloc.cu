@@ -12,6 +12,7 @@
 // The arithmetic is that of md_energy_forces in MIXED precision (FP32 pair terms on
 // FP32 offsets from the centre of mass, FP64 accumulation of rho and of the energy), with
 // a plain tiled layout: one i-atom per thread, j-tiles staged in shared memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,8 +40,42 @@ struct NoAllocScratch {
 // Shared by every call on a device; each call overwrites what it reads before reading it.
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
+// Device address of the scratch array per device ordinal, with the id of the CUDA context it was
+// looked up in: a device reset makes a new primary context, reloads the module, and may move the
+// array, so a changed context id means the address is looked up again.
+struct ScratchAddr {
+    NoAllocScratch* ptr;
+    unsigned long long ctx_id;
+    bool have_id;
+};
 std::mutex g_noalloc_mutex;
-NoAllocScratch* g_noalloc_ptr[256] = {nullptr};
+ScratchAddr g_noalloc_addr[256] = {};
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current CUDA context (through the driver entry points the runtime
+// exposes, so the library needs no link to the driver library); false when unavailable.
+bool current_ctx_id(unsigned long long* id) {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PfnCtxGetId>(f);
+    }
+    CUcontext cur = nullptr;
+    if (!get_current || !get_id || get_current(&cur) != CUDA_SUCCESS || !cur) return false;
+    return get_id(cur, id) == CUDA_SUCCESS;
+}
 
 struct Consts {
     double eps, c, a, am, B, A, ecoef, rcut2;
@@ -190,16 +225,23 @@ md_status md_energy_forces_noalloc(const double* pos_dev, int32_t n_atoms, const
     if (e != cudaSuccess || dev < 0 || dev >= 256) return na_fail(MD_ERR_CUDA, "no usable CUDA device");
     NoAllocScratch* S = nullptr;
     {
-        // first call on this device: look up the device address of the scratch array
+        // first call on this device (or in a new context of it): look up the device address of the
+        // scratch array, with this device current
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
-            e = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_noalloc_ptr[dev]), g_noalloc_scratch);
+        ScratchAddr& A = g_noalloc_addr[dev];
+        unsigned long long id = 0;
+        const bool have_id = current_ctx_id(&id);
+        if (!A.ptr || !have_id || !A.have_id || A.ctx_id != id) {
+            NoAllocScratch* p = nullptr;
+            e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
             if (e != cudaSuccess) {
-                g_noalloc_ptr[dev] = nullptr;
+                A = ScratchAddr{};
                 return na_fail(MD_ERR_CUDA, cudaGetErrorString(e));
             }
+            A.ptr = p;
+            A.have_id = current_ctx_id(&A.ctx_id);  // the lookup has made the context current
         }
-        S = g_noalloc_ptr[dev];
+        S = A.ptr;
     }
     Consts K;
     K.eps = params->eps_eV;

@@ -80,7 +80,11 @@ def lib() -> ctypes.CDLL:
                 "md_observables": ([_VP, P(md_obs)], i32),
                 "md_obs_history": ([_VP, P(md_obs), i32, P(i32)], i32),
                 "md_clear_history": ([_VP], i32),
+                "md_create_device": ([P(md_config), i32, P(i32), _VP, _VP, _VP, P(md_sc_params), P(_VP)], i32),
                 "md_get_state": ([_VP, _DP, _DP, P(i64)], i32),
+                "md_get_state_device": ([_VP, _VP, _VP, P(i64)], i32),
+                "md_set_state_device": ([_VP, _VP, _VP, i64], i32),
+                "md_fp32_peak": ([i32, _DP, _DP], i32),
                 "md_set_state": ([_VP, _DP, _DP, i64], i32),
                 "md_get_forces": ([_VP, _DP], i32),
                 "md_recenter": ([_VP], i32),
@@ -113,7 +117,8 @@ def exported_symbols():
             "md_obs_history", "md_clear_history", "md_get_state", "md_set_state", "md_get_forces", "md_recenter",
             "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts", "md_get_path",
             "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals",
-            "md_energy_forces_noalloc", "md_rdf", "md_msd_reference", "md_msd", "md_cna"]
+            "md_energy_forces_noalloc", "md_rdf", "md_msd_reference", "md_msd", "md_cna", "md_create_device",
+            "md_get_state_device", "md_set_state_device", "md_fp32_peak"]
 
 
 def md_abi_version() -> int:
@@ -191,6 +196,49 @@ def md_create(cfg: md_config, sizes, pos, vel, mass, params: md_sc_params | None
                          mass.ctypes.data_as(_DP), ctypes.byref(params), ctypes.byref(out))
     _check(st)
     return Context(out.value, sizes)
+
+
+def _dptr(x) -> int:
+    """Device address of a CUDA tensor (anything with data_ptr()) or a raw integer address; None -> 0."""
+    if x is None:
+        return 0
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+def md_create_device(cfg: md_config, sizes, pos_dev, vel_dev, mass_dev, params: md_sc_params | None = None) -> Context:
+    """md_create from caller-owned device arrays: pos_dev/vel_dev [Ntot][3] float64, mass_dev [Ntot]
+    float64 (CUDA tensors or raw device addresses; vel_dev may be None). The caller keeps ownership."""
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    params = params or sc_params()
+    out = _VP()
+    st = lib().md_create_device(ctypes.byref(cfg), len(sizes), sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                _dptr(pos_dev) or None, _dptr(vel_dev) or None, _dptr(mass_dev) or None,
+                                ctypes.byref(params), ctypes.byref(out))
+    _check(st)
+    return Context(out.value, sizes)
+
+
+def md_get_state_device(ctx: Context, pos_dev, vel_dev) -> int:
+    """Copy positions and/or velocities into caller-owned device arrays [Ntot][3] float64 (either may
+    be None); returns the step counter."""
+    step = ctypes.c_int64(0)
+    _check(lib().md_get_state_device(ctx.handle, _dptr(pos_dev) or None, _dptr(vel_dev) or None, ctypes.byref(step)),
+           ctx.handle)
+    return step.value
+
+
+def md_set_state_device(ctx: Context, pos_dev, vel_dev, step: int):
+    _check(lib().md_set_state_device(ctx.handle, _dptr(pos_dev) or None, _dptr(vel_dev) or None, int(step)),
+           ctx.handle)
+
+
+def md_fp32_peak(reps: int = 20):
+    """Measured FP32 lane-operation rate of the device (FFMA chains on every SM) and its clock-derived
+    ceiling: returns (measured, derived) in lane-ops/s."""
+    meas = ctypes.c_double(0.0)
+    derived = ctypes.c_double(0.0)
+    _check(lib().md_fp32_peak(int(reps), ctypes.byref(meas), ctypes.byref(derived)))
+    return meas.value, derived.value
 
 
 def md_destroy(ctx: Context):

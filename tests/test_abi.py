@@ -42,7 +42,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_abi_version_and_argument_errors_without_gpu(lib):
     from paper_1210_3559_gb300 import scmd
-    assert lib.md_abi_version() == 1
+    assert lib.md_abi_version() == 2
     # invalid arguments are rejected before any device call
     with pytest.raises(scmd.ScmdError) as e:
         scmd.md_create(scmd.config(), [0], [[0.0, 0.0, 0.0]] * 0, None, [])
