@@ -265,6 +265,8 @@ def main():
                                                            "ni147", "ni147x64"])
     ap.add_argument("--md-steps", type=int, default=500, help="MD steps per timed iteration")
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--path", default="auto", choices=["auto", "allpairs", "half"],
+                    help="pair path of the all-pairs workloads: automatic, ordered pairs, or FP64 each pair once")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--skip-cpu", action="store_true")
@@ -303,7 +305,9 @@ def main():
     prec = args.precision or w["prec"]
     P = scmd.MD_PREC_MIXED if prec == "mixed" else scmd.MD_PREC_FP64
     stream = torch.cuda.Stream()
-    cfg = scmd.config(precision=P, graph_chunk=min(args.md_steps, 512), tune=0 if args.no_tune else 1,
+    path_arg = {"auto": scmd.MD_PATH_AUTO, "allpairs": scmd.MD_PATH_ALLPAIRS,
+                "half": scmd.MD_PATH_ALLPAIRS_HALF}[args.path]
+    cfg = scmd.config(precision=P, path=path_arg, graph_chunk=min(args.md_steps, 512), tune=0 if args.no_tune else 1,
                       stream=stream.cuda_stream)
     sizes = np.asarray(w["sizes"], dtype=np.int32)
     natoms = int(sizes.sum())
@@ -314,7 +318,8 @@ def main():
     ctx = scmd.md_create(cfg, sizes, w["pos"], w["vel"], w["mass"], scmd.sc_params(rcut=rcut))
     path = scmd.md_get_path(ctx)
     cells = path in (scmd.MD_PATH_CELLS, scmd.MD_PATH_VERLET)  # a cutoff path
-    path_name = {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists"}.get(path, "all pairs")
+    path_name = {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists",
+                 scmd.MD_PATH_ALLPAIRS_HALF: "all pairs, each pair once"}.get(path, "all pairs")
     if args.shapes:
         v = [int(x) for x in args.shapes.split(",")]
         scmd.md_set_launch(ctx, 0, *v[0:3])
@@ -480,7 +485,8 @@ def main():
         p64 = scmd.md_get_path(c64)
         fp64 = {"value": natoms * m64 * reps64 / t64, "unit": UNIT,
                 "pair_evals_per_s": (useful_pairs if cells else pairs_per_eval) * m64 * reps64 / t64,
-                "path": {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists"}.get(p64, "all pairs"),
+                "path": {scmd.MD_PATH_CELLS: "cells", scmd.MD_PATH_VERLET: "neighbour lists",
+                         scmd.MD_PATH_ALLPAIRS_HALF: "all pairs, each pair once"}.get(p64, "all pairs"),
                 "sample": f"{reps64} x {m64} MD steps, same state and thermostat, per GPU, built-in launch shapes"}
         scmd.md_destroy(c64)
 

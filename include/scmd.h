@@ -71,14 +71,20 @@ typedef enum {
 
 typedef enum {
     MD_PATH_AUTO = 0,     /* neighbour lists when rcut_A > 0 and the largest cluster has
-                             >= 8192 atoms (or the cutoff is shifted); else all pairs    */
+                             >= 8192 atoms (or the cutoff is shifted); else all pairs, in
+                             FP64 as MD_PATH_ALLPAIRS_HALF once the batch has >= 1216 of
+                             its work units (about one 1100-atom cluster)                */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
     MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
-    MD_PATH_VERLET = 3    /* neighbour lists of rcut_A + 1 A built on the cell grid, rebuilt
+    MD_PATH_VERLET = 3,   /* neighbour lists of rcut_A + 1 A built on the cell grid, rebuilt
                              when an atom has moved 0.5 A; requires rcut_A > 0. FP64: per
                              atom, forces independent of the rebuild times. MIXED: per quad
                              of 4 nearby atoms, summed in list order, so a resumed run
                              (md_set_state) agrees to rounding rather than bit for bit      */
+    MD_PATH_ALLPAIRS_HALF = 4 /* FP64 only: all pairs, each unordered pair evaluated once and
+                             added to both atoms (Newton's third law), in work units of 32 x 16
+                             atoms whose partial sums are added per atom in a fixed order
+                             (deterministic; bitwise resume). MIXED: MD_ERR_INVALID         */
 } md_path;
 
 /* The cell path (not in the paper, which sums every pair and leaves cutoffs to
@@ -298,7 +304,8 @@ md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* 
  */
 md_status md_fp32_peak(int32_t reps, double* measured_ops_per_s, double* derived_ops_per_s);
 
-/* Number of GPU kernels issued per md_step step (all pairs: 2, cells: 5,
+/* Number of GPU kernels issued per md_step step (all pairs: 2, or 4 with
+ * MD_PATH_ALLPAIRS_HALF, cells: 5,
  * neighbour lists: 8 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
  * cells or lists, and the observable kernels of recorded steps) and per graph
  * replay overhead (launches per chunk), for launch accounting. */

@@ -42,6 +42,11 @@ constexpr int kAutoCellsMinAtoms = 8192;
 constexpr double kSkin = 1.0;
 constexpr double kSkinMargin = 1e-3;  // the rebuild triggers at kSkin / 2 - kSkinMargin (covers rounding)
 constexpr double kPi = 3.14159265358979323846;
+// MD_PATH_AUTO in FP64 evaluates each pair once when the batch has at least this many work units
+// (32 x 16 atoms each): two per FP64 sub-partition of the 152 SMs, i.e. about one 1100-atom
+// cluster. Below it the ordered-pair kernels, which spread a small cluster's pairs over more warps,
+// finish sooner.
+constexpr int kHalfMinUnits = 2 * 4 * 152;
 
 struct GraphKey {
     int M, phase, kind, obs_every;
@@ -72,6 +77,12 @@ struct md_ctx {
     // device buffers
     int32_t *d_poff = nullptr, *d_nreal = nullptr, *d_clg = nullptr, *d_status = nullptr;
     int32_t* d_off = nullptr;  // [B+1] unpadded cluster offsets (caller layout of the state arrays)
+    // FP64 all pairs with each pair once (scmd_half64.cu)
+    bool half = false;
+    int32_t h_nunits = 0;
+    int4* d_h_unit = nullptr;
+    int32_t* d_h_ubase = nullptr;
+    void *d_h_pi = nullptr, *d_h_pj = nullptr;
     double *d_x = nullptr, *d_v = nullptr, *d_mass = nullptr, *d_rho = nullptr, *d_origin = nullptr;
     double *d_part = nullptr, *d_ke = nullptr, *d_hist = nullptr, *d_hs = nullptr;
     float* d_sig0 = nullptr;
@@ -245,6 +256,11 @@ void fill_dev(md_ctx* c) {
     d.eatom = c->d_eatom;
     d.obs_x = c->d_obs_x;
     d.obs_v = c->d_obs_v;
+    d.h_nunits = c->half ? c->h_nunits : 0;
+    d.h_unit = c->d_h_unit;
+    d.h_ubase = c->d_h_ubase;
+    d.h_pi = c->d_h_pi;
+    d.h_pj = c->d_h_pj;
 }
 
 // Cell grid of every cluster (cell-list and neighbour-list paths; "rcut" below is the reach:
@@ -477,7 +493,7 @@ void drop_graphs(md_ctx* c) {
 
 void free_all(md_ctx* c) {
     drop_graphs(c);
-    void* ptrs[] = {c->d_poff, c->d_off, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
+    void* ptrs[] = {c->d_poff, c->d_off, c->d_h_unit, c->d_h_ubase, c->d_h_pi, c->d_h_pj, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
                     c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
@@ -638,8 +654,10 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
     if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED)
         return fail(nullptr, MD_ERR_INVALID, "unknown precision %d", cfg->precision);
     if (cfg->path != MD_PATH_AUTO && cfg->path != MD_PATH_ALLPAIRS && cfg->path != MD_PATH_CELLS &&
-        cfg->path != MD_PATH_VERLET)
+        cfg->path != MD_PATH_VERLET && cfg->path != MD_PATH_ALLPAIRS_HALF)
         return fail(nullptr, MD_ERR_INVALID, "unknown path %d", cfg->path);
+    if (cfg->path == MD_PATH_ALLPAIRS_HALF && cfg->precision != MD_PREC_FP64)
+        return fail(nullptr, MD_ERR_INVALID, "MD_PATH_ALLPAIRS_HALF runs in FP64 only");
     if ((cfg->path == MD_PATH_CELLS || cfg->path == MD_PATH_VERLET) && !(prm->rcut_A > 0))
         return fail(nullptr, MD_ERR_INVALID, "the cell and neighbour-list paths need a cutoff (rcut_A > 0)");
     if (cfg->obs_every < 0 || cfg->graph_chunk < 0 || cfg->obs_capacity < 0)
@@ -650,7 +668,7 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
         return fail(nullptr, MD_ERR_INVALID, "invalid Sutton-Chen parameters");
     if (prm->cutoff_shift && !(prm->rcut_A > 0))
         return fail(nullptr, MD_ERR_INVALID, "a shifted cutoff needs rcut_A > 0");
-    if (prm->cutoff_shift && cfg->path == MD_PATH_ALLPAIRS)
+    if (prm->cutoff_shift && (cfg->path == MD_PATH_ALLPAIRS || cfg->path == MD_PATH_ALLPAIRS_HALF))
         return fail(nullptr, MD_ERR_INVALID, "the shifted cutoff runs on the cell and neighbour-list paths");
     int64_t ntot = 0;
     for (int b = 0; b < n_clusters; ++b) {
@@ -893,6 +911,32 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
             CKC(cudaMemsetAsync(c->d_vlist, 0, sizeof(int32_t) * kVMax * ns, c->stream));
             CKC(cudaMemsetAsync(c->d_vcount, 0, sizeof(int32_t) * ns, c->stream));
             CKC(cudaMemsetAsync(c->d_vsub, 0, sizeof(int32_t) * kVLanes * ns, c->stream));
+        }
+    }
+    {
+        // FP64 all pairs: the work units of the each-pair-once kernels, when that form is chosen
+        std::vector<int4> units;
+        std::vector<int32_t> ubase(n_clusters);
+        if (c->path == 0 && cfg->precision == MD_PREC_FP64 &&
+            (cfg->path == MD_PATH_AUTO || cfg->path == MD_PATH_ALLPAIRS_HALF)) {
+            for (int b = 0; b < n_clusters; ++b) {
+                ubase[b] = (int32_t)units.size();
+                const int n = sizes[b], T = (n + 31) / 32, H = (n + 15) / 16;
+                for (int I = 0; I < T; ++I)
+                    for (int h = 2 * I; h < H; ++h)
+                        units.push_back(make_int4(c->poff[b] + 32 * I, c->poff[b] + 16 * h, h < 2 * I + 2 ? 1 : 0, b));
+            }
+            c->half = cfg->path == MD_PATH_ALLPAIRS_HALF || units.size() >= (size_t)kHalfMinUnits;
+        }
+        if (c->half) {
+            c->h_nunits = (int32_t)units.size();
+            CKC(dmalloc(c, &c->d_h_unit, sizeof(int4) * units.size()));
+            CKC(dmalloc(c, &c->d_h_ubase, sizeof(int32_t) * n_clusters));
+            CKC(dmalloc(c, &c->d_h_pi, (size_t)32 * 32 * units.size()));
+            CKC(dmalloc(c, &c->d_h_pj, (size_t)16 * 32 * units.size()));
+            CKC(cudaMemcpyAsync(c->d_h_unit, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, c->stream));
+            CKC(cudaMemcpyAsync(c->d_h_ubase, ubase.data(), sizeof(int32_t) * n_clusters, cudaMemcpyHostToDevice,
+                                c->stream));
         }
     }
     for (int k = 0; k < 2; ++k) {
@@ -1359,7 +1403,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
 
 md_status md_autotune(md_ctx* c, int32_t reps) {
     if (!c || reps < 1) return MD_ERR_INVALID;
-    if (c->path >= 1) return MD_OK;  // the cell and neighbour-list kernels have one launch shape
+    if (c->path >= 1 || c->half) return MD_OK;  // the cell, list and each-pair-once kernels have one launch shape
     const Dev& d = c->dev;
     const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[4] = {1, 2, 4, 8};
     // Phase 1: every shape of each pass timed alone (CUDA events over reps launches).
@@ -1469,7 +1513,8 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
 
 md_status md_get_path(const md_ctx* c, int32_t* path) {
     if (!c || !path) return MD_ERR_INVALID;
-    *path = c->path == 2 ? MD_PATH_VERLET : (c->path == 1 ? MD_PATH_CELLS : MD_PATH_ALLPAIRS);
+    *path = c->path == 2 ? MD_PATH_VERLET
+                         : (c->path == 1 ? MD_PATH_CELLS : (c->half ? MD_PATH_ALLPAIRS_HALF : MD_PATH_ALLPAIRS));
     return MD_OK;
 }
 
@@ -1478,7 +1523,7 @@ md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chun
     // lists: positions, cell build (3), list build (MIXED scan, order, list; FP64 build, sort, reverse sort,
     // commit), passes (MIXED 2; FP64 compaction, 2 passes, 2 gathers)
     // (MIXED: the position kernel runs once per chunk, and every step with Berendsen)
-    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 8 : 13) : (c->path == 1 ? 5 : 2);
+    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 8 : 13) : (c->path == 1 ? 5 : (c->half ? 4 : 2));
     if (per_chunk) *per_chunk = c->path == 2 && c->nqmax > 0 ? 4 : 3;
     return MD_OK;
 }

@@ -1,0 +1,330 @@
+// scmd_half64.cu -- FP64 all-pairs passes that evaluate each pair once (Newton's third law).
+//
+// Both sweeps of the method (Sec. II, "Computational approach") are sums over pairs of terms
+// symmetric in (i, j): the density term (a/r_ij)^m of Eq. 2 enters rho_i and rho_j, and the force
+// term of the derivative of Eq. 1 enters F_i and, with the opposite sign, F_j. In FP64 the pair
+// arithmetic runs on the FP64 pipe, which on this part has 1/64 of the FP32 rate, so evaluating
+// each unordered pair once instead of twice nearly halves the passes' cost. (In MIXED precision
+// the FP32 pipe is so fast that the extra shared-memory traffic of the second target would cost
+// more than it saves; those passes stay on the ordered-pair kernels.)
+//
+// Work decomposition. A cluster of n atoms has T = ceil(n/32) i-tiles of 32 atoms and
+// H = ceil(n/16) j half-tiles of 16 atoms. A work unit is (i-tile I, half-tile h) with h >= 2I:
+//   * h in {2I, 2I+1} (the half-tiles inside tile I, "diagonal"): every ordered pair (i, j),
+//     i in tile I, j in the half-tile, j != i, added to i only;
+//   * h >= 2I+2: every unordered pair (i in tile I, j in half-tile h), added to i and to j.
+// Each unordered pair of the cluster is thus visited exactly once. One warp takes a unit: lane l
+// holds i = 32I + l; the 16 j atoms sit in shared memory; at step k = 0..15 lane l pairs with
+// j = 16h + ((l + k) mod 16), so within each half of the warp the 16 lanes address 16 distinct
+// j and add to their j-side sums (two copies per j, one per half-warp) without atomics.
+// Each unit writes its i-side sums (32 atoms) and j-side sums (16 atoms) to its own slots; a
+// second kernel adds an atom's slots in a fixed order (its row's units by h, then the earlier
+// rows' units by I) and finishes the pass (rho and g; or F and the integrator step). Results are
+// deterministic run to run, so checkpoint/resume stays bitwise.
+#include "scmd_device.cuh"
+
+namespace scmd {
+namespace {
+
+constexpr int kHW = 4;  // warps (units) per CTA
+
+// Unit of row X (i-tile X of the cluster) and half-tile h: (X, h) -> index within the cluster.
+__device__ __forceinline__ int unit_index(int X, int h, int H) { return X * H - X * (X - 1) + (h - 2 * X); }
+
+// ------------------------------------------------------------------ density
+template <int SPECIAL, int CUT>
+__global__ void __launch_bounds__(32 * kHW) k_h_density(const Dev d) {
+    __shared__ dbl4 tj[kHW][16];
+    __shared__ double acc[kHW][32];  // [half-warp copy][16 j]
+    pdl_launch_dependents();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * kHW + warp;
+    pdl_wait();  // positions come from the previous kernel
+    if (u >= d.h_nunits) return;
+    const int4 U = d.h_unit[u];  // (first i atom, first j atom, diagonal, cluster)
+    const dbl4* mir = reinterpret_cast<const dbl4*>(d.mirror);
+    const dbl4 pi = mir[U.x + lane];
+    if (lane < 16) tj[warp][lane] = mir[U.y + lane];
+    acc[warp][lane] = 0.0;
+    __syncwarp();
+    const double rc2 = d.pot.rcut2;
+    const int mexp = d.pot.m, l16 = lane & 15, cbase = lane & 16;
+    const bool diag = U.z != 0;
+    double si = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int jj = (l16 + k) & 15;
+        const dbl4 p = tj[warp][jj];
+        const double dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        if (CUT) r2 = (r2 < rc2) ? r2 : big<double>();
+        if (diag && U.y + jj == U.x + lane) r2 = big<double>();
+        double t;
+        if (SPECIAL) {
+            const double inv = inv_r2(r2);
+            t = inv * inv * inv;
+        } else {
+            const double ir = inv_r(r2);
+            t = rpow(ir * ir, ir, mexp);
+        }
+        si += t;
+        if (!diag) acc[warp][cbase + jj] += t;
+        __syncwarp();
+    }
+    reinterpret_cast<dbl4*>(d.h_pi)[(size_t)u * 32 + lane].x = si;
+    if (!diag && lane < 16) reinterpret_cast<dbl4*>(d.h_pj)[(size_t)u * 16 + lane].x = acc[warp][lane] + acc[warp][16 + lane];
+}
+
+// rho_i from the unit sums, then what the ordered-pair density pass's epilogue does: rho (FP64),
+// g = B6 rho^-1/2 into posg, and the embedding-energy partials when observables are due.
+__global__ void __launch_bounds__(32 * kHW) k_h_density_sum(const Dev d, int obs) {
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, g = blockIdx.x * kHW + (threadIdx.x >> 5);
+    pdl_wait();
+    if (g >= d.ngroups) return;
+    const int i = g * 32 + lane, cl = d.cl_of_group[g];
+    const int base = d.poff[cl], la = i - base, n = d.nreal[cl];
+    const bool real = la < n;
+    double tot = 0.0;
+    if (real) {
+        const int H = (n + 15) >> 4, X = la >> 5, hA = la >> 4;
+        const dbl4* pi = reinterpret_cast<const dbl4*>(d.h_pi);
+        const dbl4* pj = reinterpret_cast<const dbl4*>(d.h_pj);
+        const size_t ub = (size_t)d.h_ubase[cl];
+        const size_t r0 = ub + unit_index(X, 2 * X, H);
+        for (int h = 2 * X; h < H; ++h) tot += pi[(r0 + (h - 2 * X)) * 32 + (la & 31)].x;
+        for (int J = 0; J < X; ++J) tot += pj[(ub + unit_index(J, hA, H)) * 16 + (la & 15)].x;
+    }
+    const double rho = tot * d.pot.am;
+    if (real) {
+        dbl4 p = reinterpret_cast<const dbl4*>(d.mirror)[i];
+        p.w = rho > 0.0 ? d.pot.B6 / sqrt(rho) : 0.0;
+        d.rho[i] = rho;
+        reinterpret_cast<dbl4*>(d.posg)[i] = p;
+    }
+    if (obs) {
+        double e = real ? -d.pot.eps * d.pot.c * sqrt(rho) : 0.0;
+        e = warp_sum(e);
+        if (lane == 0) d.part[(size_t)g * kObsFields + OF_EEMB] = e;
+    }
+}
+
+// -------------------------------------------------------------------- force
+template <int SPECIAL, int CUT, int ENERGY>
+__global__ void __launch_bounds__(32 * kHW) k_h_force(const Dev d) {
+    __shared__ dbl4 tj[kHW][16];
+    __shared__ dbl4 acc[kHW][32];  // [half-warp copy][16 j]: (fx, fy, fz, sum r^-n)
+    pdl_launch_dependents();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * kHW + warp;
+    pdl_wait();  // posg comes from the density pass
+    if (u >= d.h_nunits) return;
+    const int4 U = d.h_unit[u];
+    const dbl4* pg = reinterpret_cast<const dbl4*>(d.posg);
+    const dbl4 pi = pg[U.x + lane];
+    if (lane < 16) tj[warp][lane] = pg[U.y + lane];
+    acc[warp][lane] = dbl4{0.0, 0.0, 0.0, 0.0};
+    __syncwarp();
+    const double A = d.pot.A9, rc2 = d.pot.rcut2;
+    const int nexp = d.pot.n, mexp = d.pot.m, l16 = lane & 15, cbase = lane & 16;
+    const bool diag = U.z != 0;
+    double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
+#pragma unroll 2
+    for (int k = 0; k < 16; ++k) {
+        const int jj = (l16 + k) & 15;
+        const dbl4 p = tj[warp][jj];
+        const double dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        if (CUT) r2 = (r2 < rc2) ? r2 : big<double>();
+        if (diag && U.y + jj == U.x + lane) r2 = big<double>();
+        const double ir = inv_r(r2);
+        const double inv = ir * ir;
+        double coef, rn;
+        if (SPECIAL) {
+            const double inv2 = inv * inv, inv4 = inv2 * inv2;
+            coef = inv4 * fma(A, inv * ir, -(pi.w + p.w));
+            rn = inv4 * ir;
+        } else {
+            rn = rpow(inv, ir, nexp);
+            const double rm = rpow(inv, ir, mexp);
+            coef = inv * (A * rn - (pi.w + p.w) * rm);
+        }
+        fx = fma(coef, dx, fx);
+        fy = fma(coef, dy, fy);
+        fz = fma(coef, dz, fz);
+        if (ENERGY) e += rn;
+        if (!diag) {
+            dbl4& a = acc[warp][cbase + jj];
+            a.x = fma(-coef, dx, a.x);
+            a.y = fma(-coef, dy, a.y);
+            a.z = fma(-coef, dz, a.z);
+            if (ENERGY) a.w += rn;
+        }
+        __syncwarp();
+    }
+    reinterpret_cast<dbl4*>(d.h_pi)[(size_t)u * 32 + lane] = dbl4{fx, fy, fz, e};
+    if (!diag && lane < 16) {
+        const dbl4 a = acc[warp][lane], b = acc[warp][16 + lane];
+        reinterpret_cast<dbl4*>(d.h_pj)[(size_t)u * 16 + lane] = dbl4{a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+    }
+}
+
+// F_i and the pair-energy sum from the unit sums, then the force pass's epilogue (FP64): store F;
+// mode 1: every observable partial at the current (x, v); mode 2: finish this MD step's half kick,
+// record observables if due (flags bit 1), and start the next step unless it is the chunk's last
+// (flags bit 0). The same arithmetic, in the same order, as the ordered-pair force pass.
+__global__ void __launch_bounds__(32 * kHW) k_h_force_sum(const Dev d, int mode, int k_local, int flags) {
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, group = blockIdx.x * kHW + (threadIdx.x >> 5);
+    pdl_wait();
+    if (group >= d.ngroups) return;
+    const int i = group * 32 + lane, cl = d.cl_of_group[group];
+    const int base = d.poff[cl], la = i - base, n = d.nreal[cl];
+    const bool real = la < n;
+    const bool energy = mode == 1 || (mode == 2 && (flags & 2));
+    const bool last = flags & 1;
+    double Fx = 0.0, Fy = 0.0, Fz = 0.0, Ep = 0.0;
+    if (real) {
+        const int H = (n + 15) >> 4, X = la >> 5, hA = la >> 4;
+        const dbl4* pi = reinterpret_cast<const dbl4*>(d.h_pi);
+        const dbl4* pj = reinterpret_cast<const dbl4*>(d.h_pj);
+        const size_t ub = (size_t)d.h_ubase[cl];
+        const size_t r0 = ub + unit_index(X, 2 * X, H);
+        for (int h = 2 * X; h < H; ++h) {
+            const dbl4 s = pi[(r0 + (h - 2 * X)) * 32 + (la & 31)];
+            Fx += s.x;
+            Fy += s.y;
+            Fz += s.z;
+            Ep += s.w;
+        }
+        for (int J = 0; J < X; ++J) {
+            const dbl4 s = pj[(ub + unit_index(J, hA, H)) * 16 + (la & 15)];
+            Fx += s.x;
+            Fy += s.y;
+            Fz += s.z;
+            Ep += s.w;
+        }
+    }
+    const int np = d.npad;
+    double* fo = reinterpret_cast<double*>(d.f);
+    if (real) {
+        fo[i] = Fx;
+        fo[np + i] = Fy;
+        fo[2 * np + i] = Fz;
+        if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(d.status, 1);
+    }
+    if (mode == 1) {
+        const double mm = real ? d.mass[i] : 0.0;
+        if (energy) {
+            const double e = warp_sum(real ? Ep : 0.0);
+            if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
+        }
+        const double x = real ? d.x[i] : 0.0, y = real ? d.x[np + i] : 0.0, z = real ? d.x[2 * np + i] : 0.0;
+        const double vx = real ? d.v[i] : 0.0, vy = real ? d.v[np + i] : 0.0, vz = real ? d.v[2 * np + i] : 0.0;
+        obs_velocity_partials(d, group, real, mm, x, y, z, vx, vy, vz, lane);
+        obs_position_partials(d, group, real, mm, x, y, z, lane);
+        return;
+    }
+    if (mode != 2) return;
+    const Run* rr = d.run;
+    const int r_kind = rr->kind;
+    const double vx0 = real ? d.v[i] : 0.0, vy0 = real ? d.v[np + i] : 0.0, vz0 = real ? d.v[2 * np + i] : 0.0;
+    const double xx0 = real ? d.x[i] : 0.0, yy0 = real ? d.x[np + i] : 0.0, zz0 = real ? d.x[2 * np + i] : 0.0;
+    const double hs = real ? d.hs[i] : 0.0, m = real ? d.mass[i] : 0.0;
+    // velocities at the end of this step (second half kick)
+    const double vx = fma(hs, Fx, vx0), vy = fma(hs, Fy, vy0), vz = fma(hs, Fz, vz0);
+    if (energy) {  // observables are due at step + 1
+        const double e = warp_sum(real ? Ep : 0.0);
+        if (lane == 0) d.part[(size_t)group * kObsFields + OF_EPAIR] = e;
+        obs_position_partials(d, group, real, m, xx0, yy0, zz0, lane);
+        if (r_kind != 2) obs_velocity_partials(d, group, real, m, xx0, yy0, zz0, vx, vy, vz, lane);
+    }
+    if (r_kind == 2) {  // Berendsen: the rescale kernel finishes the step
+        if (real) {
+            d.v[i] = vx;
+            d.v[np + i] = vy;
+            d.v[2 * np + i] = vz;
+        }
+        const double ke2 = warp_sum(real ? m * (vx * vx + vy * vy + vz * vz) : 0.0);
+        if (lane == 0) d.ke_grp[group] = ke2;
+        return;
+    }
+    if (!real) return;
+    if (last) {
+        d.v[i] = vx;
+        d.v[np + i] = vy;
+        d.v[2 * np + i] = vz;
+        return;
+    }
+    // next step (same arithmetic as begin_step): first half kick, then A O A or A A
+    double ux = fma(hs, Fx, vx), uy = fma(hs, Fy, vy), uz = fma(hs, Fz, vz);
+    double x, y, z;
+    if (r_kind == 1) {
+        const Run r = *rr;
+        const int64_t s1 = *d.step_base + k_local + 1;
+        double w[3];
+        normals_f64(r.seed, (uint32_t)cl, s1, (uint32_t)la, w);
+        const double sig = sqrt(r.noise_k * fmax(ramp_T(r, s1), 0.0) / m);
+        const double nx = sig * w[0], ny = sig * w[1], nz = sig * w[2];
+        x = fma(r.hk, ux, fma(r.h, nx, xx0));
+        y = fma(r.hk, uy, fma(r.h, ny, yy0));
+        z = fma(r.hk, uz, fma(r.h, nz, zz0));
+        ux = fma(r.c1, ux, nx);
+        uy = fma(r.c1, uy, ny);
+        uz = fma(r.c1, uz, nz);
+    } else {
+        const double dt = rr->dt;
+        x = fma(dt, ux, xx0);
+        y = fma(dt, uy, yy0);
+        z = fma(dt, uz, zz0);
+    }
+    store_mirror<0>(d, i, cl, x, y, z);
+    d.v[i] = ux;
+    d.v[np + i] = uy;
+    d.v[2 * np + i] = uz;
+    d.x[i] = x;
+    d.x[np + i] = y;
+    d.x[2 * np + i] = z;
+    if (!(finite_bits(x) && finite_bits(y) && finite_bits(z) && finite_bits(ux) && finite_bits(uy) && finite_bits(uz)))
+        atomicOr(d.status, 1);
+}
+
+template <int SP, int CUT>
+cudaError_t density_h(const Dev& d, int obs, cudaStream_t s) {
+    cudaError_t e = launch_ex(k_h_density<SP, CUT>, (d.h_nunits + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_h_density_sum, (d.ngroups + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d, obs);
+}
+template <int SP, int CUT, int EN>
+cudaError_t force_h(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
+    cudaError_t e = launch_ex(k_h_force<SP, CUT, EN>, (d.h_nunits + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_h_force_sum, (d.ngroups + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d, mode, k_local, flags);
+}
+
+}  // namespace
+
+cudaError_t launch_h_density(const Dev& d, int obs, cudaStream_t s) {
+    const bool sp = d.pot.special != 0, cut = d.pot.rcut > 0.0;
+    if (sp && !cut) return density_h<1, 0>(d, obs, s);
+    if (sp && cut) return density_h<1, 1>(d, obs, s);
+    if (!sp && !cut) return density_h<0, 0>(d, obs, s);
+    return density_h<0, 1>(d, obs, s);
+}
+
+cudaError_t launch_h_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
+    const bool sp = d.pot.special != 0, cut = d.pot.rcut > 0.0;
+    const bool en = (mode == 1) || (mode == 2 && (flags & 2));
+    if (en) {
+        if (sp && !cut) return force_h<1, 0, 1>(d, mode, k_local, flags, s);
+        if (sp && cut) return force_h<1, 1, 1>(d, mode, k_local, flags, s);
+        if (!sp && !cut) return force_h<0, 0, 1>(d, mode, k_local, flags, s);
+        return force_h<0, 1, 1>(d, mode, k_local, flags, s);
+    }
+    if (sp && !cut) return force_h<1, 0, 0>(d, mode, k_local, flags, s);
+    if (sp && cut) return force_h<1, 1, 0>(d, mode, k_local, flags, s);
+    if (!sp && !cut) return force_h<0, 0, 0>(d, mode, k_local, flags, s);
+    return force_h<0, 1, 0>(d, mode, k_local, flags, s);
+}
+
+}  // namespace scmd

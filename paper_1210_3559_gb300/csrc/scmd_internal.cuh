@@ -179,6 +179,12 @@ struct Dev {
     int32_t* q_cell;     // [nqmax] cell of each quad
     int32_t* q_list;     // [nqmax][kQMax] quads with an atom within rcut + skin of one of this one's
     int32_t* q_count;    // [nqmax]
+    // FP64 all pairs with each pair evaluated once (scmd_half64.cu); h_nunits == 0: ordered pairs
+    int32_t h_nunits;    // work units: (i-tile of 32 atoms, j half-tile of 16) with the half-tile at or after the i-tile
+    const int4* h_unit;  // [h_nunits] (first i atom, first j atom, 1 if the half-tile is inside the i-tile, cluster)
+    const int32_t* h_ubase;  // [B] first unit of each cluster (units ordered by cluster, i-tile, half-tile)
+    void* h_pi;          // [h_nunits][32] dbl4 i-side sums of each unit (density: .x; force: F, sum r^-n)
+    void* h_pj;          // [h_nunits][16] dbl4 j-side sums of each unit
 };
 
 constexpr int kHistFields = 20;  // doubles per history record (see md_obs packing in the API)
@@ -248,6 +254,9 @@ cudaError_t launch_rdf(const Dev& d, const StructBufs& sb, double r_core, double
 cudaError_t launch_msd_ref(const Dev& d, const StructBufs& sb, double r_core, cudaStream_t s);
 cudaError_t launch_msd(const Dev& d, const StructBufs& sb, cudaStream_t s);
 cudaError_t launch_cna(const Dev& d, const StructBufs& sb, double r_nb, cudaStream_t s);
+// FP64 all pairs, each pair once (defined in scmd_half64.cu): pair kernel + per-atom sum kernel per pass.
+cudaError_t launch_h_density(const Dev& d, int obs, cudaStream_t s);
+cudaError_t launch_h_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // State exchange with caller-owned device arrays (defined in scmd_import.cu). off[B+1] are the
 // unpadded cluster offsets of the caller's [Ntot][3] / [Ntot] arrays.
 int invalid_input_bit();  // status bit launch_check_input sets

@@ -818,6 +818,7 @@ static cudaError_t force_p(const Dev& d, const Item* it, int n, Shape sh, int mo
 }
 
 cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s) {
+    if (d.h_nunits > 0) return launch_h_density(d, obs, s);  // FP64, each pair once
     if (nitems <= 0) return cudaSuccess;
     if (d.prec == 1)
         return sh.ipt == 2 ? density_p<1, 2>(d, items, nitems, sh, obs, s) : density_p<1, 1>(d, items, nitems, sh, obs, s);
@@ -826,6 +827,7 @@ cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh
 
 cudaError_t launch_force(const Dev& d, const Item* items, int nitems, Shape sh, int mode, int k_local, int flags,
                          cudaStream_t s) {
+    if (d.h_nunits > 0) return launch_h_force(d, mode, k_local, flags, s);  // FP64, each pair once
     if (nitems <= 0) return cudaSuccess;
     // ENERGY (pair-energy accumulation in the inner loop) is compiled in for fresh
     // evaluations (mode 1) and for MD steps whose end is an observation (flag bit 1).

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libscmd.so")
 
 MD_OK, MD_ERR_INVALID, MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_NONFINITE, MD_ERR_TIMEOUT, MD_ERR_STATE = range(7)
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
-MD_PATH_AUTO, MD_PATH_ALLPAIRS, MD_PATH_CELLS, MD_PATH_VERLET = 0, 1, 2, 3
+MD_PATH_AUTO, MD_PATH_ALLPAIRS, MD_PATH_CELLS, MD_PATH_VERLET, MD_PATH_ALLPAIRS_HALF = 0, 1, 2, 3, 4
 MD_NVE, MD_LANGEVIN, MD_BERENDSEN = 0, 1, 2
 _STATUS = {0: "MD_OK", 1: "MD_ERR_INVALID", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD_ERR_NONFINITE",
            5: "MD_ERR_TIMEOUT", 6: "MD_ERR_STATE"}

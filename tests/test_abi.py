@@ -81,6 +81,8 @@ def test_degenerate_and_invalid_configurations_without_gpu(lib):
         (scmd.config(path=9), [1], one, [58.6934], scmd.sc_params()),
         (scmd.config(path=scmd.MD_PATH_CELLS), [1], one, [58.6934], scmd.sc_params(rcut=0.0)),
         (scmd.config(), [1], one, [58.6934], scmd.sc_params(rcut=-1.0)),
+        (scmd.config(precision=scmd.MD_PREC_MIXED, path=scmd.MD_PATH_ALLPAIRS_HALF), [1], one, [58.6934],
+         scmd.sc_params()),
     ]
     for cfg, sizes, pos, mass, prm in cases:
         with pytest.raises(scmd.ScmdError) as e:
