@@ -19,8 +19,11 @@ Host analysis of the output of ``quench.py`` (no GPU work). It covers:
   and for the MIXED-against-FP64 ensembles (two-sample Kolmogorov-Smirnov, Fisher's exact test on the
   solidified counts, Mann-Whitney on per-cluster quantities).
 
+- ``fit_rate3``: Eq. rate3 fitted to escape rates measured at several temperatures, free or with T0 fixed.
+
 Usage: python -m paper_1210_3559_gb300.kinetics --table1 780 run_780.json
        python -m paper_1210_3559_gb300.kinetics --compare run_mixed.json run_fp64.json
+       python -m paper_1210_3559_gb300.kinetics --fit run_780.json run_800.json run_820.json ...
 """
 from __future__ import annotations
 
@@ -113,6 +116,39 @@ def compare_with_table1(T: int, lifetimes_ps, n_censored: int = 0, horizon_ps: f
     }
 
 
+def fit_rate3(T, kappa, events=None, T0: float | None = None) -> dict:
+    """Least-squares fit of Eq. rate3, ln(kappa ps) = a - b / (k_B T (T - T0)^2), to escape rates kappa (ps^-1)
+    measured at temperatures T (K). With `events` (solidified runs per temperature), each ln(kappa) is
+    weighted by its standard error 1/sqrt(events) (exponential lifetimes). T0=None fits (a, b, T0); a given
+    T0 (e.g. the paper's 1029 K) fits (a, b) alone, which stays well conditioned with few temperatures.
+    Returns the parameters, their standard errors, and the residuals of ln(kappa)."""
+    from scipy.optimize import curve_fit
+    T = np.asarray(T, dtype=np.float64)
+    y = np.log(np.asarray(kappa, dtype=np.float64))
+    sig = None if events is None else 1.0 / np.sqrt(np.asarray(events, dtype=np.float64))
+    if T0 is None:
+        def f(t, a, b, t0):
+            return a - b / (KB_EV_PER_K * t * (t - t0) ** 2)
+        p, c = curve_fit(f, T, y, p0=[FIT_A, FIT_B_EV_K2, FIT_T0_K], sigma=sig, absolute_sigma=sig is not None,
+                         maxfev=20000)
+        res = y - f(T, *p)
+        names = ["a", "b_eV_K2", "T0_K"]
+    else:
+        def f(t, a, b):
+            return a - b / (KB_EV_PER_K * t * (t - T0) ** 2)
+        p, c = curve_fit(f, T, y, p0=[FIT_A, FIT_B_EV_K2], sigma=sig, absolute_sigma=sig is not None, maxfev=20000)
+        res = y - f(T, *p)
+        names = ["a", "b_eV_K2"]
+    err = np.sqrt(np.diag(c))
+    out = {k: float(v) for k, v in zip(names, p)}
+    out.update({k + "_se": float(v) for k, v in zip(names, err)})
+    if T0 is not None:
+        out["T0_K"] = float(T0)
+        out["T0_fixed"] = True
+    out["residuals_ln_kappa"] = [float(r) for r in res]
+    return out
+
+
 def compare_ensembles(a: dict, b: dict) -> dict:
     """Two quench ensembles (outputs of quench.run with the same clusters and schedule), e.g. MIXED against
     FP64: solidified counts, lifetimes, censored rates, final crystalline fractions, and (when both carry
@@ -157,6 +193,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--table1", type=int, default=None, choices=sorted(TABLE_I), help="temperature (K)")
     ap.add_argument("--compare", action="store_true", help="compare two quench outputs")
+    ap.add_argument("--fit", action="store_true",
+                    help="fit Eq. rate3 to the censored escape rates of quench outputs at several temperatures")
     ap.add_argument("files", nargs="+", help="quench.py --out JSON files")
     a = ap.parse_args()
     runs = [json.load(open(p)) for p in a.files]
@@ -164,13 +202,36 @@ def main():
         if len(runs) != 2:
             raise SystemExit("--compare takes two files")
         print(json.dumps(compare_ensembles(runs[0], runs[1])))
+    elif a.fit:
+        by_T = {}
+        for r in runs:
+            by_T.setdefault(float(r["T_K"]), []).append(r)
+        T, kap, ev, rows = [], [], [], []
+        for t in sorted(by_T):
+            lt = [c["t_nuc_ps"] for r in by_T[t] for c in r["per_cluster"] if c["t_nuc_ps"] is not None]
+            nc = sum(_censored(r) for r in by_T[t])
+            k, d, risk = rate_mle(lt, nc, max(r["horizon_ps"] for r in by_T[t]))
+            T.append(t)
+            kap.append(k)
+            ev.append(d)
+            row = {"T_K": t, "runs": len(lt) + nc, "solidified": d, "kappa_per_ps": k,
+                   "paper_fit_kappa_per_ps": float(kappa_fit(t)), "fit_offset_K": temperature_for_kappa(k) - t}
+            if int(t) in TABLE_I and float(int(t)) == t:
+                row["table1"] = compare_with_table1(int(t), lt, nc, max(r["horizon_ps"] for r in by_T[t]))
+            rows.append(row)
+        out = {"temperatures": rows}
+        if len(T) >= 2:
+            out["fit_T0_paper"] = fit_rate3(T, kap, ev, T0=FIT_T0_K)
+        if len(T) >= 4:
+            out["fit_free"] = fit_rate3(T, kap, ev)
+        print(json.dumps(out))
     elif a.table1 is not None:
         t = [c["t_nuc_ps"] for r in runs for c in r["per_cluster"] if c["t_nuc_ps"] is not None]
         nc = sum(_censored(r) for r in runs)
         horizon = max(r["horizon_ps"] for r in runs)
         print(json.dumps(compare_with_table1(a.table1, t, nc, horizon)))
     else:
-        raise SystemExit("give --table1 T or --compare")
+        raise SystemExit("give --table1 T, --compare or --fit")
 
 
 if __name__ == "__main__":

@@ -94,3 +94,26 @@ def test_compare_ensembles_on_synthetic_quench_outputs():
     assert 0.0 <= c["fisher_p"] <= 1.0 and c["rate_ratio_ci95"][0] < c["rate_ratio"] < c["rate_ratio_ci95"][1]
     fast = K.compare_ensembles(run(5e-2), run(2e-3))
     assert fast["rate_ratio_ci95"][0] > 1.0 and fast["fisher_p"] < 1e-3
+
+
+def test_rate3_fit_recovers_the_papers_constants_from_its_printed_rates():
+    """Fitting Eq. rate3 (read in ps) to Table I's printed kappa row gives the paper's own a = 1.24,
+    b = 31053 eV K^2, T0 = 1029 K to within the rounding of that row."""
+    T = [780, 800, 820, 830, 835]
+    kap = [K.TABLE_I_KAPPA_1E5[t] * 1e-5 for t in T]
+    f = K.fit_rate3(T, kap)
+    assert abs(f["a"] - 1.24) < 0.1
+    assert abs(f["b_eV_K2"] - 31053) / 31053 < 0.03
+    assert abs(f["T0_K"] - 1029) < 3
+    # with T0 fixed at the paper's value the two-parameter fit lands on (a, b) too
+    g = K.fit_rate3(T, kap, T0=1029.0)
+    assert abs(g["a"] - 1.24) < 0.1 and abs(g["b_eV_K2"] - 31053) / 31053 < 0.03
+
+
+def test_rate3_fit_is_exact_on_its_own_curve():
+    T = np.array([770.0, 790.0, 810.0, 825.0, 840.0])
+    kap = K.kappa_fit(T, a=2.0, b=40000.0, T0=1050.0)
+    f = K.fit_rate3(T, kap)
+    assert f["a"] == pytest.approx(2.0, rel=1e-6) and f["T0_K"] == pytest.approx(1050.0, rel=1e-7)
+    assert f["b_eV_K2"] == pytest.approx(40000.0, rel=1e-6)
+    assert max(abs(r) for r in f["residuals_ln_kappa"]) < 1e-8
