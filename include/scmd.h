@@ -73,7 +73,8 @@ typedef enum {
     MD_PATH_AUTO = 0,     /* neighbour lists when rcut_A > 0 and the largest cluster has
                              >= 8192 atoms (or the cutoff is shifted); else all pairs, in
                              FP64 as MD_PATH_ALLPAIRS_HALF once the batch has >= 1216 of
-                             its work units (about one 1100-atom cluster)                */
+                             its work units (about one 1100-atom cluster) and its clusters
+                             are large (sum n^3 / sum n^2 >= 512 atoms)                  */
     MD_PATH_ALLPAIRS = 1, /* every ordered pair (with the cutoff test if rcut_A > 0)    */
     MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
     MD_PATH_VERLET = 3,   /* neighbour lists of rcut_A + 1 A built on the cell grid, rebuilt
@@ -288,7 +289,8 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
  * (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for the cell
  * path, every atom times the atoms of the 5 x 5 x 5 cell octants around its own,
  * self included, as binned at the current positions; for the MIXED lists, 16
- * per listed quad; for the FP64 lists, twice the half-list entries). Any output
+ * per listed quad plus the 12 within each quad; for the FP64 lists, twice the
+ * half-list entries). Any output
  * may be NULL.
  */
 md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* ms_force,

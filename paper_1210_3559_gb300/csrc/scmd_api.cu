@@ -45,8 +45,12 @@ constexpr double kPi = 3.14159265358979323846;
 // MD_PATH_AUTO in FP64 evaluates each pair once when the batch has at least this many work units
 // (32 x 16 atoms each): two per FP64 sub-partition of the 152 SMs, i.e. about one 1100-atom
 // cluster. Below it the ordered-pair kernels, which spread a small cluster's pairs over more warps,
-// finish sooner.
+// finish sooner...
 constexpr int kHalfMinUnits = 2 * 4 * 152;
+// ... and when its clusters are large: a unit covers 32 x 16 atoms, so for small clusters the ragged
+// tiles, and the diagonal units that visit their pairs twice, take much of the work (64 Ni147 clusters:
+// the ordered-pair kernels measured 1.65x faster). Pair-weighted mean cluster size, atoms.
+constexpr double kHalfMinMeanSize = 512.0;
 
 struct GraphKey {
     int M, phase, kind, obs_every;
@@ -869,8 +873,10 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
         c->nslot = (int32_t)ns;
         CKC(dmalloc(c, &c->d_vorder, sizeof(int32_t) * ns));
         CKC(dmalloc(c, &c->d_vslotof, sizeof(int32_t) * np));
-        CKC(dmalloc(c, &c->d_vhi, (size_t)vec4_size(c) * ns));
-        CKC(dmalloc(c, &c->d_vposg, (size_t)vec4_size(c) * ns));
+        // MIXED: 4 more slots for the padding quad of the lists (index nqmax), far from every atom
+        const size_t ns_alloc = quads ? ns + 4 : ns;
+        CKC(dmalloc(c, &c->d_vhi, (size_t)vec4_size(c) * ns_alloc));
+        CKC(dmalloc(c, &c->d_vposg, (size_t)vec4_size(c) * ns_alloc));
         CKC(dmalloc(c, &c->d_vxref, sizeof(double) * 3 * ns));
         CKC(dmalloc(c, &c->d_vdmax, sizeof(uint32_t) * 2));
         CKC(cudaMemsetAsync(c->d_vdmax, 0, sizeof(uint32_t) * 2, c->stream));
@@ -882,7 +888,7 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
             const size_t nq = (size_t)c->nqmax;
             CKC(dmalloc(c, &c->d_q_n, sizeof(int32_t)));
             CKC(dmalloc(c, &c->d_cell_base, sizeof(int32_t) * c->n_cells));
-            CKC(dmalloc(c, &c->d_q_ref, sizeof(float4) * nq));
+            CKC(dmalloc(c, &c->d_q_ref, sizeof(float4) * (nq + 1)));
             CKC(dmalloc(c, &c->d_q_box, sizeof(float4) * 2 * nq));
             CKC(dmalloc(c, &c->d_q_cell, sizeof(int32_t) * nq));
             CKC(dmalloc(c, &c->d_q_list, sizeof(int32_t) * kQMax * nq));
@@ -890,6 +896,16 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
             CKC(cudaMemsetAsync(c->d_q_n, 0, sizeof(int32_t), c->stream));
             CKC(cudaMemsetAsync(c->d_cell_base, 0, sizeof(int32_t) * c->n_cells, c->stream));
             CKC(cudaMemsetAsync(c->d_q_count, 0, sizeof(int32_t) * nq, c->stream));
+            {  // the padding quad of the lists: reference point 0, its 4 slots far from every atom and every
+               // empty slot (g = 0)
+                constexpr float F = -kQuadFar;
+                static const float far4[4][4] = {{F, F, F, 0.f}, {F, F, F, 0.f}, {F, F, F, 0.f}, {F, F, F, 0.f}};
+                CKC(cudaMemcpyAsync(static_cast<float4*>(c->d_vhi) + ns, far4, sizeof far4, cudaMemcpyHostToDevice,
+                                    c->stream));
+                CKC(cudaMemcpyAsync(static_cast<float4*>(c->d_vposg) + ns, far4, sizeof far4, cudaMemcpyHostToDevice,
+                                    c->stream));
+                CKC(cudaMemsetAsync(c->d_q_ref + nq, 0, sizeof(float4), c->stream));
+            }
         } else {
             CKC(dmalloc(c, &c->d_vlist, sizeof(int32_t) * kVMax * ns));
             CKC(dmalloc(c, &c->d_vcount, sizeof(int32_t) * ns));
@@ -926,7 +942,14 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
                     for (int h = 2 * I; h < H; ++h)
                         units.push_back(make_int4(c->poff[b] + 32 * I, c->poff[b] + 16 * h, h < 2 * I + 2 ? 1 : 0, b));
             }
-            c->half = cfg->path == MD_PATH_ALLPAIRS_HALF || units.size() >= (size_t)kHalfMinUnits;
+            // pair-weighted mean cluster size sum n^3 / sum n^2: small clusters waste much of a unit
+            double s2 = 0.0, s3 = 0.0;
+            for (int b = 0; b < n_clusters; ++b) {
+                s2 += (double)sizes[b] * sizes[b];
+                s3 += (double)sizes[b] * sizes[b] * sizes[b];
+            }
+            c->half = cfg->path == MD_PATH_ALLPAIRS_HALF ||
+                      (units.size() >= (size_t)kHalfMinUnits && s3 >= kHalfMinMeanSize * s2);
         }
         if (c->half) {
             c->h_nunits = (int32_t)units.size();
@@ -1350,7 +1373,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
     if (ms_d) *ms_d = td / reps;
     if (ms_f) *ms_f = tf / reps;
-    if (pairs && vl && c->nqmax > 0) {  // quad lists: 16 pairs tested per listed quad
+    if (pairs && vl && c->nqmax > 0) {  // quad lists: 16 pairs per listed quad, 12 within each quad
         int32_t nq = 0;
         std::vector<int32_t> cnt(c->nqmax);
         CK(c, cudaMemcpyAsync(&nq, c->d_q_n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -1358,7 +1381,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
                               c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
         double p = 0;
-        for (int q = 0; q < nq && q < c->nqmax; ++q) p += 16.0 * cnt[q];
+        for (int q = 0; q < nq && q < c->nqmax; ++q) p += 16.0 * cnt[q] + 12.0;
         *pairs = p;
     } else if (pairs && vl) {  // half-list entries: each an unordered pair, i.e. two ordered pairs
         std::vector<int32_t> cnt(c->ntot);

@@ -18,9 +18,10 @@
 // j = 16h + ((l + k) mod 16), so within each half of the warp the 16 lanes address 16 distinct
 // j and add to their j-side sums (two copies per j, one per half-warp) without atomics.
 // Each unit writes its i-side sums (32 atoms) and j-side sums (16 atoms) to its own slots; a
-// second kernel adds an atom's slots in a fixed order (its row's units by h, then the earlier
-// rows' units by I) and finishes the pass (rho and g; or F and the integrator step). Results are
-// deterministic run to run, so checkpoint/resume stays bitwise.
+// second kernel adds an atom's slots in a fixed order (a fixed split over 8 warps, each taking
+// every 8th of the atom's slots, then a fixed tree over the 8 partials) and finishes the pass
+// (rho and g; or F and the integrator step). Results are deterministic run to run, so
+// checkpoint/resume stays bitwise.
 #include "scmd_device.cuh"
 
 namespace scmd {
@@ -30,6 +31,50 @@ constexpr int kHW = 4;  // warps (units) per CTA
 
 // Unit of row X (i-tile X of the cluster) and half-tile h: (X, h) -> index within the cluster.
 __device__ __forceinline__ int unit_index(int X, int h, int H) { return X * H - X * (X - 1) + (h - 2 * X); }
+
+// The per-atom sum kernels: one CTA of kSW warps per 32-atom group. An atom of tile X has K = (H - 2X) + X
+// unit sums: term k < H - 2X is the i-side sum of unit (X, 2X + k), term k = H - 2X + J the j-side sum of
+// unit (J, its half-tile), J < X. Warp w adds the terms k = w, w + kSW, ... of its lane's atom (every lane
+// of a group has the same X, so the warps' loops are uniform); the kSW partials are then added in a fixed
+// tree. Each dependent FP64 chain is thus ~K / kSW long instead of K (the FP64 add latency is 64 cycles).
+constexpr int kSW = 8;
+
+template <int NV>  // NV = 1: the .x component (density); 4: every component (force, pair energy)
+__device__ __forceinline__ dbl4 unit_sums(const Dev& d, int la, int n, size_t ub, int warp) {
+    const int H = (n + 15) >> 4, X = la >> 5, hA = la >> 4, ni = H - 2 * X, K = ni + X;
+    const dbl4* pi = reinterpret_cast<const dbl4*>(d.h_pi);
+    const dbl4* pj = reinterpret_cast<const dbl4*>(d.h_pj);
+    const size_t r0 = ub + unit_index(X, 2 * X, H);
+    dbl4 s = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int k = warp; k < K; k += kSW) {
+        const dbl4* src = k < ni ? pi + (r0 + k) * 32 + (la & 31)
+                                 : pj + (ub + unit_index(k - ni, hA, H)) * 16 + (la & 15);
+        if (NV == 1) {
+            s.x += src->x;
+        } else {
+            const dbl4 t = *src;
+            s.x += t.x;
+            s.y += t.y;
+            s.z += t.z;
+            s.w += t.w;
+        }
+    }
+    return s;
+}
+
+// Fixed-order tree over the kSW warp partials of lane t (red[w * 32 + t]).
+__device__ __forceinline__ dbl4 tree8(const dbl4* red, int t) {
+    dbl4 q[kSW];
+#pragma unroll
+    for (int w = 0; w < kSW; ++w) q[w] = red[w * 32 + t];
+#pragma unroll
+    for (int h = kSW / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int w = 0; w < h; ++w) q[w] = dbl4{q[w].x + q[w + h].x, q[w].y + q[w + h].y, q[w].z + q[w + h].z,
+                                                 q[w].w + q[w + h].w};
+    return q[0];
+}
 
 // ------------------------------------------------------------------ density
 template <int SPECIAL, int CUT>
@@ -77,24 +122,18 @@ __global__ void __launch_bounds__(32 * kHW) k_h_density(const Dev d) {
 
 // rho_i from the unit sums, then what the ordered-pair density pass's epilogue does: rho (FP64),
 // g = B6 rho^-1/2 into posg, and the embedding-energy partials when observables are due.
-__global__ void __launch_bounds__(32 * kHW) k_h_density_sum(const Dev d, int obs) {
+__global__ void __launch_bounds__(32 * kSW) k_h_density_sum(const Dev d, int obs) {
+    __shared__ dbl4 red[kSW * 32];
     pdl_launch_dependents();
-    const int lane = threadIdx.x & 31, g = blockIdx.x * kHW + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = blockIdx.x;
     pdl_wait();
-    if (g >= d.ngroups) return;
     const int i = g * 32 + lane, cl = d.cl_of_group[g];
     const int base = d.poff[cl], la = i - base, n = d.nreal[cl];
     const bool real = la < n;
-    double tot = 0.0;
-    if (real) {
-        const int H = (n + 15) >> 4, X = la >> 5, hA = la >> 4;
-        const dbl4* pi = reinterpret_cast<const dbl4*>(d.h_pi);
-        const dbl4* pj = reinterpret_cast<const dbl4*>(d.h_pj);
-        const size_t ub = (size_t)d.h_ubase[cl];
-        const size_t r0 = ub + unit_index(X, 2 * X, H);
-        for (int h = 2 * X; h < H; ++h) tot += pi[(r0 + (h - 2 * X)) * 32 + (la & 31)].x;
-        for (int J = 0; J < X; ++J) tot += pj[(ub + unit_index(J, hA, H)) * 16 + (la & 15)].x;
-    }
+    red[warp * 32 + lane] = real ? unit_sums<1>(d, la, n, (size_t)d.h_ubase[cl], warp) : dbl4{0.0, 0.0, 0.0, 0.0};
+    __syncthreads();
+    if (warp != 0) return;
+    const double tot = tree8(red, lane).x;
     const double rho = tot * d.pot.am;
     if (real) {
         dbl4 p = reinterpret_cast<const dbl4*>(d.mirror)[i];
@@ -173,38 +212,21 @@ __global__ void __launch_bounds__(32 * kHW) k_h_force(const Dev d) {
 // mode 1: every observable partial at the current (x, v); mode 2: finish this MD step's half kick,
 // record observables if due (flags bit 1), and start the next step unless it is the chunk's last
 // (flags bit 0). The same arithmetic, in the same order, as the ordered-pair force pass.
-__global__ void __launch_bounds__(32 * kHW) k_h_force_sum(const Dev d, int mode, int k_local, int flags) {
+__global__ void __launch_bounds__(32 * kSW) k_h_force_sum(const Dev d, int mode, int k_local, int flags) {
+    __shared__ dbl4 red[kSW * 32];
     pdl_launch_dependents();
-    const int lane = threadIdx.x & 31, group = blockIdx.x * kHW + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, group = blockIdx.x;
     pdl_wait();
-    if (group >= d.ngroups) return;
     const int i = group * 32 + lane, cl = d.cl_of_group[group];
     const int base = d.poff[cl], la = i - base, n = d.nreal[cl];
     const bool real = la < n;
+    red[warp * 32 + lane] = real ? unit_sums<4>(d, la, n, (size_t)d.h_ubase[cl], warp) : dbl4{0.0, 0.0, 0.0, 0.0};
+    __syncthreads();
+    if (warp != 0) return;
     const bool energy = mode == 1 || (mode == 2 && (flags & 2));
     const bool last = flags & 1;
-    double Fx = 0.0, Fy = 0.0, Fz = 0.0, Ep = 0.0;
-    if (real) {
-        const int H = (n + 15) >> 4, X = la >> 5, hA = la >> 4;
-        const dbl4* pi = reinterpret_cast<const dbl4*>(d.h_pi);
-        const dbl4* pj = reinterpret_cast<const dbl4*>(d.h_pj);
-        const size_t ub = (size_t)d.h_ubase[cl];
-        const size_t r0 = ub + unit_index(X, 2 * X, H);
-        for (int h = 2 * X; h < H; ++h) {
-            const dbl4 s = pi[(r0 + (h - 2 * X)) * 32 + (la & 31)];
-            Fx += s.x;
-            Fy += s.y;
-            Fz += s.z;
-            Ep += s.w;
-        }
-        for (int J = 0; J < X; ++J) {
-            const dbl4 s = pj[(ub + unit_index(J, hA, H)) * 16 + (la & 15)];
-            Fx += s.x;
-            Fy += s.y;
-            Fz += s.z;
-            Ep += s.w;
-        }
-    }
+    const dbl4 S = tree8(red, lane);
+    const double Fx = S.x, Fy = S.y, Fz = S.z, Ep = S.w;
     const int np = d.npad;
     double* fo = reinterpret_cast<double*>(d.f);
     if (real) {
@@ -293,13 +315,13 @@ template <int SP, int CUT>
 cudaError_t density_h(const Dev& d, int obs, cudaStream_t s) {
     cudaError_t e = launch_ex(k_h_density<SP, CUT>, (d.h_nunits + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d);
     if (e != cudaSuccess) return e;
-    return launch_ex(k_h_density_sum, (d.ngroups + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d, obs);
+    return launch_ex(k_h_density_sum, d.ngroups, 32 * kSW, 0, 0, s, d, obs);
 }
 template <int SP, int CUT, int EN>
 cudaError_t force_h(const Dev& d, int mode, int k_local, int flags, cudaStream_t s) {
     cudaError_t e = launch_ex(k_h_force<SP, CUT, EN>, (d.h_nunits + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d);
     if (e != cudaSuccess) return e;
-    return launch_ex(k_h_force_sum, (d.ngroups + kHW - 1) / kHW, 32 * kHW, 0, 0, s, d, mode, k_local, flags);
+    return launch_ex(k_h_force_sum, d.ngroups, 32 * kSW, 0, 0, s, d, mode, k_local, flags);
 }
 
 }  // namespace

@@ -35,7 +35,7 @@ namespace scmd {
 namespace {
 
 constexpr int kQThreads = 256;  // 8 warps, one quad each
-constexpr float kFar = 1.0e5f;  // coordinate of an empty slot: outside every cutoff of every atom
+constexpr float kFar = kQuadFar;  // coordinate of an empty slot: outside every cutoff of every atom
 
 // Sub-cell (side h/8) of an offset from the cell centre along one axis, clamped to the cell.
 __device__ __forceinline__ uint32_t sub8(float o, float h) {
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
             for (int t0 = 0; t0 < nq; t0 += 32) {
                 bool in = false;
                 const int J = q0 + t0 + lane;
-                if (t0 + lane < nq) {
+                if (t0 + lane < nq && J != Q) {  // the quad's own pairs are summed apart from its list
                     const float4 l2 = d.q_box[2 * J], h2 = d.q_box[2 * J + 1];
                     const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
                     const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
@@ -258,21 +258,32 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
                 n += __popc(b);
             }
         }
+        // pad to a whole number of 16-entry iterations of the passes with the padding quad
+        for (int k = min(n, kQMax) + lane; k < min((n + 15) & ~15, kQMax); k += 32) out[k] = d.nqmax;
         if (lane == 0) d.q_count[Q] = min(n, kQMax);
         if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(d.status, 4);
     }
 }
 
 // ---------------------------------------------------------------- passes
-// Atom q of listed quad J (J < 0: past the end of the list) as an offset from the warp's quad
-// reference point, or far away.
+// Atom q of listed quad J as an offset from the warp's quad reference point (the padding quad's atoms
+// land far from every atom and every empty slot).
 __device__ __forceinline__ float4 q_neighbour(const Dev& d, const float4* vp, int J, int q, const float4& CI) {
-    if (J < 0) return make_float4(kFar, kFar, kFar, 0.f);
     const float4 pj = vp[4 * J + q];
     const float4 CJ = d.q_ref[J];
     return make_float4(pj.x - (CI.x - CJ.x), pj.y - (CI.y - CJ.y), pj.z - (CI.z - CJ.z), pj.w);
 }
-__device__ __forceinline__ int q_entry(const int* L, int k, int n) { return k < n ? L[k] : -1; }
+// List entry k of a list padded to n16 entries (the padding quad past the end).
+__device__ __forceinline__ int q_entry(const Dev& d, const int* L, int k, int n16) { return k < n16 ? L[k] : d.nqmax; }
+// Lanes 0..3: atom (lane) of the warp's own quad, to be paired with its other three atoms before the
+// list loop; the other lanes: far away.
+__device__ __forceinline__ float4 q_self(const float4 oi[4], int lane) {
+    float4 p = make_float4(-kFar, -kFar, -kFar, 0.f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        if (lane == a) p = oi[a];
+    return p;
+}
 
 // The 4 atoms of this warp's quad (far away for a warp past the last quad).
 __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int nq, float4 oi[4], float4& CI) {
@@ -291,7 +302,7 @@ __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int 
 // Each CTA takes 8 quads (32 slots). The warps sum their quads' pairs; then warp 0 finishes all 32
 // atoms with one lane each, so the FP64 per-atom work runs on full warps.
 template <int SPECIAL, int SHIFT>
-__global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs, int k_local) {
+__global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const Dev d, int obs, int k_local) {
     __shared__ double s_sum[32];
     __shared__ float4 s_own[32];
     pdl_launch_dependents();
@@ -309,33 +320,42 @@ __global__ void __launch_bounds__(kQThreads) k_q_density(const Dev d, int obs, i
     const int mexp = d.pot.m;
     float tacc[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
+#define SCMD_Q_DENSITY_PAIR(P, A, EXTRA)                                        \
+    {                                                                           \
+        const float dx = oi[A].x - P.x, dy = oi[A].y - P.y, dz = oi[A].z - P.z; \
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));                         \
+        const bool in = r2 < rc2 EXTRA;                                         \
+        r2 = in ? r2 : big<float>();                                            \
+        if (SHIFT) nin[A] += in;                                                \
+        if (SPECIAL) {                                                          \
+            const float inv = inv_r2(r2);                                       \
+            tacc[A] = fmaf(inv * inv, inv, tacc[A]);                            \
+        } else {                                                                \
+            const float ir = inv_r(r2);                                         \
+            tacc[A] += rpow(ir * ir, ir, mexp);                                 \
+        }                                                                       \
+    }
+    if (n > 0) {  // the quad's own pairs (lanes 0..3); r2 > 0 also drops two empty slots of one quad
+        const float4 p = q_self(oi, lane);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) SCMD_Q_DENSITY_PAIR(p, a, && r2 > 0.f && a != lane)
+    }
     // two listed quads per lane and iteration; the list entries of the next iteration are loaded
-    // one iteration ahead
-    int J0 = q_entry(L, lane >> 2, n), J1 = q_entry(L, 8 + (lane >> 2), n);
-    for (int k0 = 0; k0 < n; k0 += 16) {
+    // one iteration ahead; only the cutoff decides (no listed atom coincides with an own one)
+    const int n16 = (n + 15) & ~15;
+    int J0 = q_entry(d, L, lane >> 2, n16), J1 = q_entry(d, L, 8 + (lane >> 2), n16);
+    for (int k0 = 0; k0 < n16; k0 += 16) {
         const float4 pp[2] = {q_neighbour(d, vp, J0, q, CI), q_neighbour(d, vp, J1, q, CI)};
-        J0 = q_entry(L, k0 + 16 + (lane >> 2), n);
-        J1 = q_entry(L, k0 + 24 + (lane >> 2), n);
+        J0 = q_entry(d, L, k0 + 16 + (lane >> 2), n16);
+        J1 = q_entry(d, L, k0 + 24 + (lane >> 2), n16);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 p = pp[h];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const bool in = r2 < rc2 && r2 > 0.f;
-                r2 = in ? r2 : big<float>();
-                if (SHIFT) nin[a] += in;
-                if (SPECIAL) {
-                    const float inv = inv_r2(r2);
-                    tacc[a] = fmaf(inv * inv, inv, tacc[a]);
-                } else {
-                    const float ir = inv_r(r2);
-                    tacc[a] += rpow(ir * ir, ir, mexp);
-                }
-            }
+            for (int a = 0; a < 4; ++a) SCMD_Q_DENSITY_PAIR(p, a, )
         }
     }
+#undef SCMD_Q_DENSITY_PAIR
 #pragma unroll
     for (int a = 0; a < 4; ++a) {  // a fixed butterfly over the warp: every lane gets the sums
         double v = (double)tacc[a];
@@ -382,50 +402,59 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
     float4 oi[4], CI;
     const int n = q_own(d, vp, Q, nq, oi, CI);
     const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
-    const float A = (float)d.pot.A9;
+    const float A9 = (float)d.pot.A9;
     const float rc2 = (float)d.pot.rcut2;
     const int nexp = d.pot.n, mexp = d.pot.m;
     float fx[4] = {0.f, 0.f, 0.f, 0.f}, fy[4] = {0.f, 0.f, 0.f, 0.f}, fz[4] = {0.f, 0.f, 0.f, 0.f};
     float se[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
+#define SCMD_Q_FORCE_PAIR(P, A, EXTRA)                                          \
+    {                                                                           \
+        const float dx = oi[A].x - P.x, dy = oi[A].y - P.y, dz = oi[A].z - P.z; \
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));                         \
+        const bool in = r2 < rc2 EXTRA;                                         \
+        r2 = in ? r2 : big<float>();                                            \
+        const float ir = inv_r(r2);                                             \
+        const float inv = ir * ir;                                              \
+        float coef, rn;                                                         \
+        if (SPECIAL) {                                                          \
+            const float inv2 = inv * inv, inv4 = inv2 * inv2;                   \
+            coef = inv4 * fmaf(A9, inv * ir, -(oi[A].w + P.w));                 \
+            rn = inv4 * ir;                                                     \
+        } else {                                                                \
+            rn = rpow(inv, ir, nexp);                                           \
+            const float rm = rpow(inv, ir, mexp);                               \
+            coef = inv * (A9 * rn - (oi[A].w + P.w) * rm);                      \
+        }                                                                       \
+        fx[A] = fmaf(coef, dx, fx[A]);                                          \
+        fy[A] = fmaf(coef, dy, fy[A]);                                          \
+        fz[A] = fmaf(coef, dz, fz[A]);                                          \
+        if (ENERGY) {                                                           \
+            se[A] += rn;                                                        \
+            nin[A] += in;                                                       \
+        }                                                                       \
+    }
+    if (n > 0) {  // the quad's own pairs (lanes 0..3); r2 > 0 also drops two empty slots of one quad
+        const float4 p = q_self(oi, lane);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) SCMD_Q_FORCE_PAIR(p, a, && r2 > 0.f && a != lane)
+    }
     // two listed quads per lane and iteration; the list entries of the next iteration are loaded
-    // one iteration ahead
-    int J0 = q_entry(L, lane >> 2, n), J1 = q_entry(L, 8 + (lane >> 2), n);
-    for (int k0 = 0; k0 < n; k0 += 16) {
+    // one iteration ahead; only the cutoff decides (no listed atom coincides with an own one)
+    const int n16 = (n + 15) & ~15;
+    int J0 = q_entry(d, L, lane >> 2, n16), J1 = q_entry(d, L, 8 + (lane >> 2), n16);
+    for (int k0 = 0; k0 < n16; k0 += 16) {
         const float4 pp[2] = {q_neighbour(d, vp, J0, q, CI), q_neighbour(d, vp, J1, q, CI)};
-        J0 = q_entry(L, k0 + 16 + (lane >> 2), n);
-        J1 = q_entry(L, k0 + 24 + (lane >> 2), n);
+        J0 = q_entry(d, L, k0 + 16 + (lane >> 2), n16);
+        J1 = q_entry(d, L, k0 + 24 + (lane >> 2), n16);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 p = pp[h];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float dx = oi[a].x - p.x, dy = oi[a].y - p.y, dz = oi[a].z - p.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const bool in = r2 < rc2 && r2 > 0.f;
-                r2 = in ? r2 : big<float>();
-                const float ir = inv_r(r2);
-                const float inv = ir * ir;
-                float coef, rn;
-                if (SPECIAL) {
-                    const float inv2 = inv * inv, inv4 = inv2 * inv2;
-                    coef = inv4 * fmaf(A, inv * ir, -(oi[a].w + p.w));
-                    rn = inv4 * ir;
-                } else {
-                    rn = rpow(inv, ir, nexp);
-                    const float rm = rpow(inv, ir, mexp);
-                    coef = inv * (A * rn - (oi[a].w + p.w) * rm);
-                }
-                fx[a] = fmaf(coef, dx, fx[a]);
-                fy[a] = fmaf(coef, dy, fy[a]);
-                fz[a] = fmaf(coef, dz, fz[a]);
-                if (ENERGY) {
-                    se[a] += rn;
-                    nin[a] += in;
-                }
-            }
+            for (int a = 0; a < 4; ++a) SCMD_Q_FORCE_PAIR(p, a, )
         }
     }
+#undef SCMD_Q_FORCE_PAIR
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         float x = fx[a], y = fy[a], z = fz[a];

@@ -154,6 +154,10 @@ def test_automatic_choice(scmd):
     assert path(FP64, 1000) == scmd.MD_PATH_ALLPAIRS
     assert path(FP64, 2000, scmd.MD_PATH_ALLPAIRS) == scmd.MD_PATH_ALLPAIRS
     assert path(MIXED, 2000) == scmd.MD_PATH_ALLPAIRS
+    # many small clusters: enough work units, but the ordered-pair kernels suit them better
+    pos = np.concatenate([inputs.mackay_icosahedron(3, 2.49)] * 64)
+    ctx = scmd.md_create(scmd.config(precision=FP64), [147] * 64, pos, None, inputs.masses(len(pos)))
+    assert scmd.md_get_path(ctx) == scmd.MD_PATH_ALLPAIRS
     with pytest.raises(scmd.ScmdError) as e:
         path(MIXED, 100, scmd.MD_PATH_ALLPAIRS_HALF)
     assert e.value.status == scmd.MD_ERR_INVALID
