@@ -58,9 +58,9 @@ typedef enum {
     MD_ERR_CUDA = 2,      /* a CUDA runtime call failed or no suitable GPU            */
     MD_ERR_OOM = 3,       /* device or host allocation failed                         */
     MD_ERR_NONFINITE = 4, /* a force, position or velocity became NaN/Inf on the GPU  */
-    MD_ERR_TIMEOUT = 5,   /* reserved for a bounded device-side wait that gives up; no
-                             kernel of this version waits on another, so no call
-                             returns it                                               */
+    MD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up (the all-pairs passes wait,
+                             within a thread-block cluster, for the partial sums the other
+                             CTAs push; a correct run never comes near the bound)       */
     MD_ERR_STATE = 6      /* call not valid in the context's current state            */
 } md_status;
 

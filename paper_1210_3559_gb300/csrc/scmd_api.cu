@@ -22,7 +22,7 @@
 #include <vector>
 
 #include "../../include/scmd.h"
-#include "scmd_internal.cuh"
+#include "scmd_device.cuh"
 
 using namespace scmd;
 
@@ -544,6 +544,8 @@ md_status check_status(md_ctx* c) {
                     kCellCap);
     if (s & 4)
         return fail(c, MD_ERR_STATE, "a neighbour list overflowed (more than %d entries); forces are invalid", kVMax);
+    if (s & kStatusTimeout)
+        return fail(c, MD_ERR_TIMEOUT, "a pair pass gave up waiting for its partial sums; forces are invalid");
     return MD_OK;
 }
 

@@ -330,6 +330,57 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+// Pushing partial sums to the cluster's rank-0 CTA without a second cluster barrier. Rank 0 sets up an
+// mbarrier that completes when the expected number of bytes has arrived (and its own single arrival,
+// made at set-up); the other CTAs write their partials into rank 0's shared memory with st.async, whose
+// completion counts those bytes on that mbarrier, and exit. Rank 0 waits on the mbarrier with a bounded
+// number of polls.
+__device__ __forceinline__ void mbar_setup(uint64_t* bar, uint32_t tx_bytes) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(tx_bytes) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Shared-memory address of p in the cluster's rank-0 CTA (a shared::cluster address).
+__device__ __forceinline__ unsigned rank0_addr(const void* p) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return r;
+}
+__device__ __forceinline__ void st_async(unsigned raddr, float v, unsigned rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(raddr), "f"(v),
+                 "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(unsigned raddr, double v, unsigned rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(raddr), "d"(v),
+                 "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(unsigned raddr, f2sum v, unsigned rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "f"(v.hi), "f"(v.lo), "r"(rbar)
+                 : "memory");
+}
+// Wait for phase 0 of the mbarrier; false after kMbarPolls polls (each try_wait may also suspend the
+// thread for a while), which no correct run comes near: the pushes of a pass land within microseconds.
+constexpr int kMbarPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait0(uint64_t* bar) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    for (int k = 0; k < kMbarPolls; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// Status bit set when a bounded wait gave up (reported as MD_ERR_TIMEOUT).
+constexpr int kStatusTimeout = 16;
+
 // CTA barrier 1 over the first n threads (n a multiple of 32); barrier 0 is __syncthreads.
 __device__ __forceinline__ void bar_sync_first(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
 

@@ -47,11 +47,14 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     using V4 = typename Tr<PREC>::V4;
     constexpr int BI = 32 * IPT;
     extern __shared__ __align__(32) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_bar;  // rank 0: completes when the other ranks' partials have landed
+    __shared__ int s_late;
     cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    if (rank == 0 && threadIdx.x == 0) mbar_setup(&s_bar, (unsigned)((C - 1) * BI * 8));
     cluster_arrive_relaxed();  // "this CTA has started": waited for before any remote store
     pdl_launch_dependents();
     const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = (int)cluster.block_rank();
     const Item it = load_item<BI>(d, items, C);
     V4* tiles = reinterpret_cast<V4*>(smem);
     // MIXED: partials are double-float (2 floats); FP64: one double (same 8 bytes)
@@ -150,20 +153,33 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
             red[warp * BI + q * 32 + lane] = racc[q] + (double)sacc[q];
     }
     __syncthreads();
-    cluster_wait();  // every CTA of the cluster has started: its shared memory may be written
+    cluster_wait();  // every CTA of the cluster has started: rank 0's shared memory and mbarrier are set up
     if (threadIdx.x < BI) {
+        // this CTA's sum over its warps, into rank 0's inbox: rank 0 stores its own, the others push it
+        // with st.async, which counts the bytes on rank 0's mbarrier
         if (PREC == 1) {
             const f2sum s2 = f2_tree_sum(red2 + threadIdx.x, W, BI);
-            *cluster.map_shared_rank(inbox2 + rank * BI + threadIdx.x, 0) = s2;
+            if (rank == 0)
+                inbox2[threadIdx.x] = s2;
+            else
+                st_async(rank0_addr(inbox2 + rank * BI + threadIdx.x), s2, rank0_addr(&s_bar));
         } else {
             double s = 0.0;
             for (int w = 0; w < W; ++w) s += red[w * BI + threadIdx.x];
-            *cluster.map_shared_rank(inbox + rank * BI + threadIdx.x, 0) = s;
+            if (rank == 0)
+                inbox[threadIdx.x] = s;
+            else
+                st_async(rank0_addr(inbox + rank * BI + threadIdx.x), s, rank0_addr(&s_bar));
         }
     }
-    cluster_arrive_release();
-    cluster_wait();
-    if (rank != 0 || threadIdx.x >= BI) return;
+    if (rank != 0) return;
+    if (threadIdx.x == 0) s_late = mbar_wait0(&s_bar) ? 0 : 1;
+    __syncthreads();
+    if (s_late) {
+        if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
+        return;
+    }
+    if (threadIdx.x >= BI) return;
     double tot;
     float sf = 0.f;  // MIXED: the density sum in FP32 (the high word of its double-float form)
     if (PREC == 1) {
@@ -212,11 +228,15 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     using V4 = typename Tr<PREC>::V4;
     constexpr int BI = 32 * IPT;
     extern __shared__ __align__(32) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_bar;  // rank 0: completes when the other ranks' partials have landed
+    __shared__ int s_late;
     cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    if (rank == 0 && threadIdx.x == 0)
+        mbar_setup(&s_bar, (unsigned)((C - 1) * BI * (3 * sizeof(typename Tr<PREC>::R) + (ENERGY ? 8 : 0))));
     cluster_arrive_relaxed();
     pdl_launch_dependents();
     const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = (int)cluster.block_rank();
     const Item it = load_item<BI>(d, items, C);
     V4* tiles = reinterpret_cast<V4*>(smem);
     double* rede = reinterpret_cast<double*>(smem + (size_t)W * 32 * sizeof(V4));
@@ -389,14 +409,27 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
             az += redf[3 * sidx + 2];
             if (ENERGY) ae += rede[sidx];
         }
-        R* dst = cluster.map_shared_rank(inboxf + 3 * (rank * BI + threadIdx.x), 0);
-        dst[0] = ax;
-        dst[1] = ay;
-        dst[2] = az;
-        if (ENERGY) *cluster.map_shared_rank(inboxe + rank * BI + threadIdx.x, 0) = ae;
+        R* dst = inboxf + 3 * (rank * BI + threadIdx.x);
+        if (rank == 0) {
+            dst[0] = ax;
+            dst[1] = ay;
+            dst[2] = az;
+            if (ENERGY) inboxe[threadIdx.x] = ae;
+        } else {  // pushed into rank 0's inbox; the bytes count on rank 0's mbarrier
+            const unsigned bar = rank0_addr(&s_bar);
+            st_async(rank0_addr(dst), ax, bar);
+            st_async(rank0_addr(dst + 1), ay, bar);
+            st_async(rank0_addr(dst + 2), az, bar);
+            if (ENERGY) st_async(rank0_addr(inboxe + rank * BI + threadIdx.x), ae, bar);
+        }
     }
-    cluster_arrive_release();
-    cluster_wait();
+    if (rank != 0) return;
+    if (threadIdx.x == 0) s_late = mbar_wait0(&s_bar) ? 0 : 1;
+    __syncthreads();
+    if (s_late) {
+        if (threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
+        return;
+    }
     // Split epilogue (MIXED, NVE or Langevin, not the chunk's last step). FP64 runs at 1/64 of
     // the FP32 rate here and a warp instruction holds its sub-partition's FP64 unit for ~68
     // cycles, so one warp integrating all three components of its 32 atoms is ~27 FP64
