@@ -329,7 +329,7 @@ Shape default_shape(const md_ctx* c, int which) {
 
 bool shape_ok(Shape s) {
     return (s.ipt == 1 || s.ipt == 2) && (s.warps == 2 || s.warps == 4 || s.warps == 8 || s.warps == 16) &&
-           (s.cluster == 1 || s.cluster == 2 || s.cluster == 4 || s.cluster == 8);
+           s.cluster >= 1 && s.cluster <= 8;
 }
 
 const Item* items_for(const md_ctx* c, Shape s, int* n) {
@@ -1430,7 +1430,8 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     if (!c || reps < 1) return MD_ERR_INVALID;
     if (c->path >= 1 || c->half) return MD_OK;  // the cell, list and each-pair-once kernels have one launch shape
     const Dev& d = c->dev;
-    const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[4] = {1, 2, 4, 8};
+    // cluster sizes that are not powers of two let a small work list fill the 152 SMs more evenly
+    const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[7] = {1, 2, 3, 4, 5, 6, 8};
     // Phase 1: every shape of each pass timed alone (CUDA events over reps launches).
     std::vector<std::pair<float, Shape>> timed[2];
     cudaEvent_t e0, e1;

@@ -286,13 +286,19 @@ template <int K> __device__ __forceinline__ f2sum f2_tree(const f2sum* p, int s)
     else
         return f2_add(f2_tree<K / 2>(p, s), f2_tree<K / 2>(p + (K / 2) * s, s));
 }
-__device__ __forceinline__ f2sum f2_tree_sum(const f2sum* p, int k, int s) {  // k in {1, 2, 4, 8, 16}
+// k in {1, 2, 4, 8, 16} as the balanced tree; any other k (1..16) as a left fold, also in a fixed order.
+__device__ __forceinline__ f2sum f2_tree_sum(const f2sum* p, int k, int s) {
     switch (k) {
         case 16: return f2_tree<16>(p, s);
         case 8: return f2_tree<8>(p, s);
         case 4: return f2_tree<4>(p, s);
         case 2: return f2_tree<2>(p, s);
-        default: return p[0];
+        case 1: return p[0];
+        default: {
+            f2sum a = p[0];
+            for (int r = 1; r < k; ++r) a = f2_add(a, p[r * s]);
+            return a;
+        }
     }
 }
 // Pin a loaded value in a register at this point: the load must complete here, so the

@@ -122,7 +122,7 @@ def test_every_launch_shape_agrees_with_oracle(scmd, prec):
     ctx = make(scmd, [333], pos, prec=prec)
     for ipt in (1, 2):
         for warps in (2, 4, 8, 16):
-            for cl in (1, 2, 4, 8):
+            for cl in (1, 2, 3, 4, 5, 6, 7, 8):
                 for which in (0, 1):
                     scmd.md_set_launch(ctx, which, ipt, warps, cl)
                 E, F = scmd.md_energy_forces(ctx)
