@@ -222,6 +222,14 @@ def cpu_baseline(w, budget_s: float):
     return out
 
 
+def arm_config(w, world: int) -> dict:
+    """The workload both arms report (the same dict for the GPU arm and the oracle arm)."""
+    return {"workload": w["desc"], "atoms_per_gpu": int(np.sum(w["sizes"])), "clusters_per_gpu": int(len(w["sizes"])),
+            "dt_fs": w["dt"], "rcut_A": w.get("rcut") or None,
+            "l2": "GPU arm: flushed (256 MB write) before every timed iteration, outside the timed events",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
 def cut_note(w):
     return f", cutoff {w['rcut']} A tested on every pair" if w.get("rcut") else ""
 
@@ -247,7 +255,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w["desc"], "sample_atoms": n, "md_steps_per_step": 1},
+            "data": "synthetic", "config": arm_config(w, world),
+            "run": {"sample_atoms": n, "sample_clusters": len(sizes), "md_steps_per_step": 1, "precision": "fp64"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step = 1 MD step of {n} atoms (FP64 oracle, all pairs{cut_note(w)})"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -526,13 +535,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": w["desc"], "atoms_per_gpu": natoms, "clusters_per_gpu": int(len(sizes)),
-                       "md_steps_per_step": M, "dt_fs": dt, "precision": prec,
-                       "l2": "flushed (256 MB write) before every timed iteration, outside the timed events",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "launch_shapes": {k: list(v) for k, v in shapes.items()} if not cells else path_name,
-                       "rcut_A": rcut or None, "path": path_name,
-                       "wall_s_timed_region": t_wall},
+            "config": arm_config(w, world),
+            "run": {"md_steps_per_step": M, "precision": prec, "path": path_name,
+                    "launch_shapes": {k: list(v) for k, v in shapes.items()} if not cells else path_name,
+                    "wall_s_timed_region": t_wall},
             "pair_evals_per_s": pair_rate if not cells else useful_pairs * md_steps_total * world / t_max,
             "candidate_pairs_per_s": pair_rate if cells else None,
             "fp32_pipe_frac_force_pass": achieved / peak_ops,
