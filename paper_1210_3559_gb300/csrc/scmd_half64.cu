@@ -29,6 +29,31 @@ namespace {
 
 constexpr int kHW = 4;  // warps (units) per CTA
 
+// r^2 of a masked pair (self pair of a diagonal unit, or beyond the cutoff): finite, so that the
+// Newton steps below stay finite, and far enough that every term underflows to 0.
+constexpr double kMaskR2 = 1.0e300;
+
+// FP64 reciprocal and reciprocal square root: the hardware's approximate values (MUFU) refined by two
+// Newton-Raphson steps, each of which roughly doubles the number of correct bits, so the result is
+// accurate to a few ulp. On the FP64 pipe this costs 4 (reciprocal) and 7 (reciprocal square root)
+// multiply-adds, fewer than the IEEE-rounded division and square root, and the pair passes' tolerances
+// (1e-12 relative) need no correctly rounded result. Inputs must be finite and positive.
+__device__ __forceinline__ double rcp_nr(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double h = 0.5 * x;
+    y = y * fma(-h, y * y, 1.5);
+    return y * fma(-h, y * y, 1.5);
+}
+
 // Unit of row X (i-tile X of the cluster) and half-tile h: (X, h) -> index within the cluster.
 __device__ __forceinline__ int unit_index(int X, int h, int H) { return X * H - X * (X - 1) + (h - 2 * X); }
 
@@ -102,14 +127,14 @@ __global__ void __launch_bounds__(32 * kHW) k_h_density(const Dev d) {
         const dbl4 p = tj[warp][jj];
         const double dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
         double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        if (CUT) r2 = (r2 < rc2) ? r2 : big<double>();
-        if (diag && U.y + jj == U.x + lane) r2 = big<double>();
+        if (CUT) r2 = (r2 < rc2) ? r2 : kMaskR2;
+        if (diag && U.y + jj == U.x + lane) r2 = kMaskR2;
         double t;
         if (SPECIAL) {
-            const double inv = inv_r2(r2);
+            const double inv = rcp_nr(r2);
             t = inv * inv * inv;
         } else {
-            const double ir = inv_r(r2);
+            const double ir = rsqrt_nr(r2);
             t = rpow(ir * ir, ir, mexp);
         }
         si += t;
@@ -174,9 +199,9 @@ __global__ void __launch_bounds__(32 * kHW) k_h_force(const Dev d) {
         const dbl4 p = tj[warp][jj];
         const double dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
         double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        if (CUT) r2 = (r2 < rc2) ? r2 : big<double>();
-        if (diag && U.y + jj == U.x + lane) r2 = big<double>();
-        const double ir = inv_r(r2);
+        if (CUT) r2 = (r2 < rc2) ? r2 : kMaskR2;
+        if (diag && U.y + jj == U.x + lane) r2 = kMaskR2;
+        const double ir = rsqrt_nr(r2);
         const double inv = ir * ir;
         double coef, rn;
         if (SPECIAL) {
