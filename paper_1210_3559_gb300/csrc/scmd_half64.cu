@@ -36,8 +36,9 @@ constexpr double kMaskR2 = 1.0e300;
 // FP64 reciprocal and reciprocal square root: the hardware's approximate values (MUFU) refined by two
 // Newton-Raphson steps, each of which roughly doubles the number of correct bits, so the result is
 // accurate to a few ulp. On the FP64 pipe this costs 4 (reciprocal) and 7 (reciprocal square root)
-// multiply-adds, fewer than the IEEE-rounded division and square root, and the pair passes' tolerances
-// (1e-12 relative) need no correctly rounded result. Inputs must be finite and positive.
+// multiply-adds; the pair passes' tolerances (1e-12 relative) need no correctly rounded result. The
+// density pass uses the reciprocal (faster than the IEEE division); the force pass keeps the library's
+// reciprocal square root, which measured faster than this one. Inputs must be finite and positive.
 __device__ __forceinline__ double rcp_nr(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(32 * kHW) k_h_force(const Dev d) {
         double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         if (CUT) r2 = (r2 < rc2) ? r2 : kMaskR2;
         if (diag && U.y + jj == U.x + lane) r2 = kMaskR2;
-        const double ir = rsqrt_nr(r2);
+        const double ir = inv_r(r2);  // (the Newton form measured slower than the library's here)
         const double inv = ir * ir;
         double coef, rn;
         if (SPECIAL) {

@@ -358,15 +358,19 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
 #undef SCMD_Q_DENSITY_PAIR
 #pragma unroll
     for (int a = 0; a < 4; ++a) {  // a fixed butterfly over the warp: every lane gets the sums
-        double v = (double)tacc[a];
+        // double-float (TwoSum) on the FP32 pipe: an FP64 butterfly here held the 1/64-rate FP64 pipe for
+        // ~1/3 of the pass. TwoSum is exact, so both lanes of a pair compute the same sum.
+        f2sum v = {tacc[a], 0.f};
         int m = nin[a];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            v += __shfl_xor_sync(0xffffffffu, v, o);
+            const f2sum u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+            v = f2_add(v, u);
             if (SHIFT) m += __shfl_xor_sync(0xffffffffu, m, o);
         }
         if (lane == a) {
-            s_sum[4 * w + a] = SHIFT ? v - (double)m * d.pot.shm : v;
+            const double t = (double)v.hi + (double)v.lo;
+            s_sum[4 * w + a] = SHIFT ? t - (double)m * d.pot.shm : t;
             s_own[4 * w + a] = oi[a];
         }
     }
