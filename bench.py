@@ -51,26 +51,30 @@ METRIC = "atom-timesteps/s & pair-evals/s vs FP32 peak; mixed vs FP64 at stated 
 UNIT = "atom-timesteps/s"
 FP32_LANES_PER_SM = 128
 FORCE_OPS_PER_PAIR = 16    # FP32 pipe lane-ops per ordered pair, force pass, (n,m) = (9,6)
-# DRAM bytes (read + write) of one force-pass launch from an ncu capture (cold caches), with the
-# hash of the kernel sources the capture ran; reported only while those sources are unchanged.
-FORCE_DRAM_BYTES_PER_LAUNCH = {"batched512": (51965952 + 833792, "d65cec2899f25359")}
-KERNEL_SOURCES = ("paper_1210_3559_gb300/csrc/scmd_kernels.cu", "paper_1210_3559_gb300/csrc/scmd_device.cuh",
-                  "paper_1210_3559_gb300/csrc/scmd_quads.cu")
+# DRAM bytes (read + write) of one force-pass launch from an ncu capture (cold caches), with the hash
+# of the sources of that kernel when it was captured; reported only while those sources are unchanged.
+FORCE_SOURCES = {
+    "all pairs": ("paper_1210_3559_gb300/csrc/scmd_kernels.cu", "paper_1210_3559_gb300/csrc/scmd_device.cuh",
+                  "paper_1210_3559_gb300/csrc/scmd_internal.cuh"),
+    "neighbour lists": ("paper_1210_3559_gb300/csrc/scmd_quads.cu", "paper_1210_3559_gb300/csrc/scmd_device.cuh",
+                        "paper_1210_3559_gb300/csrc/scmd_internal.cuh", "paper_1210_3559_gb300/csrc/scmd_cells.cuh"),
+}
+FORCE_DRAM_BYTES_PER_LAUNCH = {"batched512": (51966976 + 837888, "f933930675d29b85")}
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(path_name: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in FORCE_SOURCES.get(path_name, ()):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def force_traffic(config: str):
+def force_traffic(config: str, path_name: str):
     rec = FORCE_DRAM_BYTES_PER_LAUNCH.get(config)
-    if rec is None or rec[1] != kernel_source_hash():
+    if rec is None or rec[1] != kernel_source_hash(path_name):
         return None
     return rec[0]
 
@@ -548,7 +552,7 @@ def main():
             "structure": structure,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
-                         "traffic": force_traffic(args.config) if prec == "mixed" else None,
+                         "traffic": force_traffic(args.config, path_name) if prec == "mixed" else None,
                          "kernel": {"cells": "k_cell_force (force pass, cell list)",
                                     "neighbour lists": "k_q_force (force pass, quad lists)" if prec == "mixed"
                                     else "k_v_force (force pass, neighbour lists)"}.get(
