@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2) k_cell_densit
     const CellGrid g = d.grid[cl];
     const V4* cp = reinterpret_cast<const V4*>(d.cpos);
     const int M = octant_box(d, c, g, s_src, s_cnt, s_pref);
-    const R rc2 = (R)d.pot.rcut2, h = (R)g.h;
+    const R rc2 = PREC == 1 ? (R)d.pot.rcut2f : (R)d.pot.rcut2, h = (R)g.h;
     const int mexp = d.pot.m;
     const int nblk = oct_blocks(d, c), lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int blk = 0; blk < nblk; ++blk) {
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kCellThreads, PREC == 1 ? 5 : 2)
     const CellGrid g = d.grid[cl];
     const V4* pg = reinterpret_cast<const V4*>(d.cposg);
     const int M = octant_box(d, c, g, s_src, s_cnt, s_pref);
-    const R A = (R)d.pot.A9;
-    const R rc2 = (R)d.pot.rcut2, h = (R)g.h;
+    const R A = PREC == 1 ? (R)d.pot.A9f : (R)d.pot.A9;
+    const R rc2 = PREC == 1 ? (R)d.pot.rcut2f : (R)d.pot.rcut2, h = (R)g.h;
     const int nexp = d.pot.n, mexp = d.pot.m;
     const int nblk = oct_blocks(d, c), lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int blk = 0; blk < nblk; ++blk) {

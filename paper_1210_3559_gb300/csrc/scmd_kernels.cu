@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     f2sum* red2 = reinterpret_cast<f2sum*>(red);
     f2sum* inbox2 = reinterpret_cast<f2sum*>(inbox);
     const V4* mir = reinterpret_cast<const V4*>(d.mirror);
-    const R rc2 = (R)d.pot.rcut2;
+    const R rc2 = PREC == 1 ? (R)d.pot.rcut2f : (R)d.pot.rcut2;  // no FP64 conversion in MIXED
     const int mexp = d.pot.m;
     constexpr int S = SplitOf<PREC>::S, L = 32 / S;
     const int ntile = (it.nj + 31) >> 5, nunit = ntile * S;
@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(512, 1) k_force(const Dev d, const Item* __res
     R* redf = reinterpret_cast<R*>(inboxe + C * BI);
     R* inboxf = redf + W * BI * 3;
     const V4* pg = reinterpret_cast<const V4*>(d.posg);
-    const R A = (R)d.pot.A9;
-    const R rc2 = (R)d.pot.rcut2;
+    const R A = PREC == 1 ? (R)d.pot.A9f : (R)d.pot.A9;  // no FP64 conversion in MIXED
+    const R rc2 = PREC == 1 ? (R)d.pot.rcut2f : (R)d.pot.rcut2;
     const int nexp = d.pot.n, mexp = d.pot.m;
     constexpr int S = SplitOf<PREC>::S, L = 32 / S;
     const int ntile = (it.nj + 31) >> 5, nunit = ntile * S;

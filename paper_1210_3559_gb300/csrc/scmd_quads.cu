@@ -303,7 +303,8 @@ __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int 
 // atoms with one lane each, so the FP64 per-atom work runs on full warps.
 template <int SPECIAL, int SHIFT>
 __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const Dev d, int obs, int k_local) {
-    __shared__ double s_sum[32];
+    __shared__ f2sum s_sum[32];  // per slot: the density sum as double-float (FP64 only in warp 0's finish)
+    __shared__ int s_nin[32];
     __shared__ float4 s_own[32];
     pdl_launch_dependents();
     pdl_wait();
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
     float4 oi[4], CI;
     const int n = q_own(d, vp, Q, nq, oi, CI);
     const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
-    const float rc2 = (float)d.pot.rcut2;
+    const float rc2 = d.pot.rcut2f;  // (FP32 constants from the host: a conversion would run on the FP64 pipe)
     const int mexp = d.pot.m;
     float tacc[4] = {0.f, 0.f, 0.f, 0.f};
     int nin[4] = {0, 0, 0, 0};
@@ -369,8 +370,8 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
             if (SHIFT) m += __shfl_xor_sync(0xffffffffu, m, o);
         }
         if (lane == a) {
-            const double t = (double)v.hi + (double)v.lo;
-            s_sum[4 * w + a] = SHIFT ? t - (double)m * d.pot.shm : t;
+            s_sum[4 * w + a] = v;
+            if (SHIFT) s_nin[4 * w + a] = m;
             s_own[4 * w + a] = oi[a];
         }
     }
@@ -379,7 +380,8 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
     const int s = blockIdx.x * kQThreads / 8 + lane, i = d.vorder[s];
     float4 pg = make_float4(kFar, kFar, kFar, 0.f);
     if (i >= 0) {
-        const double rho = s_sum[lane] * d.pot.am;
+        const double t = (double)s_sum[lane].hi + (double)s_sum[lane].lo;
+        const double rho = (SHIFT ? t - (double)s_nin[lane] * d.pot.shm : t) * d.pot.am;
         d.rho[i] = rho;
         const float rf = (float)rho;
         float y = rsqrt_approx(rf);
@@ -406,8 +408,7 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
     float4 oi[4], CI;
     const int n = q_own(d, vp, Q, nq, oi, CI);
     const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
-    const float A9 = (float)d.pot.A9;
-    const float rc2 = (float)d.pot.rcut2;
+    const float A9 = d.pot.A9f, rc2 = d.pot.rcut2f;
     const int nexp = d.pot.n, mexp = d.pot.m;
     float fx[4] = {0.f, 0.f, 0.f, 0.f}, fy[4] = {0.f, 0.f, 0.f, 0.f}, fz[4] = {0.f, 0.f, 0.f, 0.f};
     float se[4] = {0.f, 0.f, 0.f, 0.f};
