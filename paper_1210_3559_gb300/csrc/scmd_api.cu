@@ -1492,6 +1492,9 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     md_status st = MD_OK;
     md_thermostat nve{};
     nve.kind = MD_NVE;
+    // two rounds over the combinations, each keeping its best time: a combination must be slow twice to
+    // lose, which keeps one noisy measurement from deciding the shapes
+    for (int round = 0; round < 2 && st == MD_OK; ++round)
     for (int a = 0; a < std::min<int>(K, (int)timed[0].size()) && st == MD_OK; ++a)
         for (int b = 0; b < std::min<int>(K, (int)timed[1].size()) && st == MD_OK; ++b) {
             c->shape[0] = timed[0][a].second;
