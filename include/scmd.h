@@ -182,7 +182,8 @@ md_status md_create(const md_config* cfg, int32_t n_clusters, const int32_t* siz
 
 /*
  * md_create from device memory the caller owns (for example PyTorch CUDA
- * tensors): pos_dev[Ntot][3], vel_dev[Ntot][3] (may be NULL: zero velocities)
+ * tensors); the state is that of the MD runs of Sec. II ("Computational
+ * approach") and Sec. III: positions, velocities and masses of every atom: pos_dev[Ntot][3], vel_dev[Ntot][3] (may be NULL: zero velocities)
  * and mass_dev[Ntot] are contiguous float64 arrays in the same layout as
  * md_create's, in device memory of the current device; sizes is a host array.
  * The work is ordered on cfg->stream, which must be the stream that produced
@@ -239,7 +240,8 @@ md_status md_clear_history(md_ctx* ctx);
 md_status md_get_state(md_ctx* ctx, double* pos_A, double* vel_A_per_fs, int64_t* step);
 md_status md_set_state(md_ctx* ctx, const double* pos_A, const double* vel_A_per_fs, int64_t step);
 
-/* The same checkpoint through caller-owned device arrays [Ntot][3] (float64,
+/* The same checkpoint (positions and velocities of the Sec. II / III MD state)
+ * through caller-owned device arrays [Ntot][3] (float64,
  * current device), converted to and from the context's layout by kernels on
  * the context's stream; both calls return after that work has completed.
  * md_get_state_device: either array may be NULL. md_set_state_device: both are
@@ -297,7 +299,9 @@ md_status md_time_passes(md_ctx* ctx, int32_t reps, double* ms_density, double* 
                          double* pairs);
 
 /*
- * The FP32 lane-operation rate of the current device, measured: every SM runs
+ * The FP32 lane-operation rate of the current device, measured (a property of
+ * the hardware, not of the paper's method: the roofline denominator of the
+ * pair sweeps of Eq. 1 and Eq. 2): every SM runs
  * independent FFMA chains (one FFMA = one lane operation) for reps timed
  * launches, *measured_ops_per_s = lane operations / CUDA-event time. Also
  * *derived_ops_per_s = SMs x 128 FP32 lanes x the maximum SM clock. This is
