@@ -89,3 +89,17 @@ def test_degenerate_and_invalid_configurations_without_gpu(lib):
             scmd.md_create(cfg, sizes, pos, None, mass, prm)
         assert e.value.status == scmd.MD_ERR_INVALID, (sizes, cfg.precision, cfg.path)
         assert scmd.md_last_error() != ""
+
+
+def test_device_entry_points_reject_bad_arguments_without_gpu(lib):
+    """md_create_device and md_fp32_peak check their arguments before any device call."""
+    from paper_1210_3559_gb300 import scmd
+    with pytest.raises(scmd.ScmdError) as e:
+        scmd.md_create_device(scmd.config(), [4], None, None, None)
+    assert e.value.status == scmd.MD_ERR_INVALID
+    with pytest.raises(scmd.ScmdError) as e:
+        scmd.md_create_device(scmd.config(), [0], 1, None, 1)
+    assert e.value.status == scmd.MD_ERR_INVALID
+    with pytest.raises(scmd.ScmdError) as e:
+        scmd.md_fp32_peak(0)
+    assert e.value.status == scmd.MD_ERR_INVALID
