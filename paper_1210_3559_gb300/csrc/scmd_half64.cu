@@ -58,12 +58,12 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 // Unit of row X (i-tile X of the cluster) and half-tile h: (X, h) -> index within the cluster.
 __device__ __forceinline__ int unit_index(int X, int h, int H) { return X * H - X * (X - 1) + (h - 2 * X); }
 
-// The per-atom sum kernels: one CTA of kSW warps per 32-atom group. An atom of tile X has K = (H - 2X) + X
+// The per-atom sum kernels: one CTA of kSW (16) warps per 32-atom group. An atom of tile X has K = (H - 2X) + X
 // unit sums: term k < H - 2X is the i-side sum of unit (X, 2X + k), term k = H - 2X + J the j-side sum of
 // unit (J, its half-tile), J < X. Warp w adds the terms k = w, w + kSW, ... of its lane's atom (every lane
 // of a group has the same X, so the warps' loops are uniform); the kSW partials are then added in a fixed
 // tree. Each dependent FP64 chain is thus ~K / kSW long instead of K (the FP64 add latency is 64 cycles).
-constexpr int kSW = 8;
+constexpr int kSW = 16;
 
 template <int NV>  // NV = 1: the .x component (density); 4: every component (force, pair energy)
 __device__ __forceinline__ dbl4 unit_sums(const Dev& d, int la, int n, size_t ub, int warp) {
@@ -76,8 +76,9 @@ __device__ __forceinline__ dbl4 unit_sums(const Dev& d, int la, int n, size_t ub
     for (int k = warp; k < K; k += kSW) {
         const dbl4* src = k < ni ? pi + (r0 + k) * 32 + (la & 31)
                                  : pj + (ub + unit_index(k - ni, hA, H)) * 16 + (la & 15);
-        if (NV == 1) {
-            s.x += src->x;
+        if (NV == 1) {  // density: compact doubles (the same slot index, 8 bytes per slot)
+            s.x += k < ni ? reinterpret_cast<const double*>(d.h_pi)[(r0 + k) * 32 + (la & 31)]
+                          : reinterpret_cast<const double*>(d.h_pj)[(ub + unit_index(k - ni, hA, H)) * 16 + (la & 15)];
         } else {
             const dbl4 t = *src;
             s.x += t.x;
@@ -90,7 +91,7 @@ __device__ __forceinline__ dbl4 unit_sums(const Dev& d, int la, int n, size_t ub
 }
 
 // Fixed-order tree over the kSW warp partials of lane t (red[w * 32 + t]).
-__device__ __forceinline__ dbl4 tree8(const dbl4* red, int t) {
+__device__ __forceinline__ dbl4 tree_sw(const dbl4* red, int t) {
     dbl4 q[kSW];
 #pragma unroll
     for (int w = 0; w < kSW; ++w) q[w] = red[w * 32 + t];
@@ -142,8 +143,9 @@ __global__ void __launch_bounds__(32 * kHW) k_h_density(const Dev d) {
         if (!diag) acc[warp][cbase + jj] += t;
         __syncwarp();
     }
-    reinterpret_cast<dbl4*>(d.h_pi)[(size_t)u * 32 + lane].x = si;
-    if (!diag && lane < 16) reinterpret_cast<dbl4*>(d.h_pj)[(size_t)u * 16 + lane].x = acc[warp][lane] + acc[warp][16 + lane];
+    // the density pass stores its sums as compact doubles (a quarter of the force pass's slot)
+    reinterpret_cast<double*>(d.h_pi)[(size_t)u * 32 + lane] = si;
+    if (!diag && lane < 16) reinterpret_cast<double*>(d.h_pj)[(size_t)u * 16 + lane] = acc[warp][lane] + acc[warp][16 + lane];
 }
 
 // rho_i from the unit sums, then what the ordered-pair density pass's epilogue does: rho (FP64),
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(32 * kSW) k_h_density_sum(const Dev d, int obs
     red[warp * 32 + lane] = real ? unit_sums<1>(d, la, n, (size_t)d.h_ubase[cl], warp) : dbl4{0.0, 0.0, 0.0, 0.0};
     __syncthreads();
     if (warp != 0) return;
-    const double tot = tree8(red, lane).x;
+    const double tot = tree_sw(red, lane).x;
     const double rho = tot * d.pot.am;
     if (real) {
         dbl4 p = reinterpret_cast<const dbl4*>(d.mirror)[i];
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(32 * kSW) k_h_force_sum(const Dev d, int mode,
     if (warp != 0) return;
     const bool energy = mode == 1 || (mode == 2 && (flags & 2));
     const bool last = flags & 1;
-    const dbl4 S = tree8(red, lane);
+    const dbl4 S = tree_sw(red, lane);
     const double Fx = S.x, Fy = S.y, Fz = S.z, Ep = S.w;
     const int np = d.npad;
     double* fo = reinterpret_cast<double*>(d.f);
