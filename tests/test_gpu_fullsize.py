@@ -19,6 +19,9 @@ from paper_1210_3559_gb300 import inputs
 
 FP64, MIXED = 0, 1
 TOL = {FP64: dict(eF=1e-12, E=1e-13, rho=1e-13), MIXED: dict(eF=1e-5, E=1e-6, rho=2e-5)}
+# At these sizes the MIXED energy also meets the tighter 1e-7 of the original specification: its error comes
+# from the FP32 pair terms, whose sums are folded in FP64 every 128 pairs and which average out over ~1e7 pairs.
+E_FULLSIZE_MIXED = 1e-7
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +79,7 @@ def test_single_cluster_full_size(scmd, prec, n, amp, seed):
     print(f"N={n} prec={prec} shapes={scmd.md_get_launch(ctx, 0)},{scmd.md_get_launch(ctx, 1)} "
           f"e_F={eF:.3e} dE/E={eE:.3e} rho={erho:.3e}")
     assert eF <= tol["eF"], eF
-    assert eE <= tol["E"], eE
+    assert eE <= (E_FULLSIZE_MIXED if prec == MIXED else tol["E"]), eE
     assert erho <= tol["rho"], erho
     scmd.md_destroy(ctx)
 
@@ -96,7 +99,7 @@ def test_single_cluster_full_size_liquid_state(scmd):
     rho = scmd.md_get_density(ctx)
     eF, eE, erho = errors(F, E[0], rho, p)
     print(f"N={n} liquid e_F={eF:.3e} dE/E={eE:.3e} rho={erho:.3e}")
-    assert eF <= TOL[MIXED]["eF"] and eE <= TOL[MIXED]["E"] and erho <= TOL[MIXED]["rho"], (eF, eE, erho)
+    assert eF <= TOL[MIXED]["eF"] and eE <= E_FULLSIZE_MIXED and erho <= TOL[MIXED]["rho"], (eF, eE, erho)
     scmd.md_destroy(ctx)
 
 
@@ -119,5 +122,6 @@ def test_full_512_cluster_ensemble(scmd, prec):
         worst = [max(w, x) for w, x in zip(worst, err)]
     print(f"512 clusters prec={prec} worst e_F={worst[0]:.3e} dE/E={worst[1]:.3e} rho={worst[2]:.3e}")
     tol = TOL[prec]
-    assert worst[0] <= tol["eF"] and worst[1] <= tol["E"] and worst[2] <= tol["rho"], worst
+    e_tol = E_FULLSIZE_MIXED if prec == MIXED else tol["E"]
+    assert worst[0] <= tol["eF"] and worst[1] <= e_tol and worst[2] <= tol["rho"], worst
     scmd.md_destroy(ctx)
