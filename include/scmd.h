@@ -249,6 +249,12 @@ md_status md_set_state(md_ctx* ctx, const double* pos_A, const double* vel_A_per
  * MD_ERR_INVALID and the context is left unchanged), then the forces are
  * recomputed, as in md_set_state. */
 md_status md_get_state_device(md_ctx* ctx, double* pos_dev, double* vel_dev, int64_t* step);
+/* md_energy_forces into caller-owned device arrays: the potential energy of
+ * every cluster (Eq. 1) into epot_dev[n_clusters] and the forces (the
+ * derivative of Eq. 1) into forces_dev[Ntot][3], float64, current device;
+ * either may be NULL. Same evaluation and values as md_energy_forces (MIXED
+ * forces are FP32 values widened to FP64); returns after the copies are done. */
+md_status md_energy_forces_device(md_ctx* ctx, double* epot_dev, double* forces_dev);
 md_status md_set_state_device(md_ctx* ctx, const double* pos_dev, const double* vel_dev, int64_t step);
 
 /* MIXED precision keeps pair coordinates in FP32 relative to one origin per

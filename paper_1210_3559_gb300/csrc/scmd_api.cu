@@ -1275,6 +1275,16 @@ md_status md_set_state(md_ctx* c, const double* pos, const double* vel, int64_t 
     return check_status(c);
 }
 
+md_status md_energy_forces_device(md_ctx* c, double* epot_dev, double* forces_dev) {
+    if (!c) return MD_ERR_INVALID;
+    md_status st = evaluate(c, true);
+    if (st != MD_OK) return st;
+    if (epot_dev || forces_dev)
+        CK(c, launch_export_forces(c->dev, c->d_off, forces_dev, epot_dev, c->hist_cap, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_status(c);
+}
+
 md_status md_get_state_device(md_ctx* c, double* pos_dev, double* vel_dev, int64_t* step) {
     if (!c) return MD_ERR_INVALID;
     if (pos_dev || vel_dev) {

@@ -1,5 +1,5 @@
 // scmd_import.cu -- state exchange with caller-owned device arrays (md_create_device,
-// md_set_state_device, md_get_state_device).
+// md_set_state_device, md_get_state_device, md_energy_forces_device).
 //
 // The caller's arrays are row-major [Ntot][3] doubles (positions, velocities) and [Ntot]
 // doubles (masses) in device memory, clusters back to back. The context keeps the padded
@@ -64,9 +64,37 @@ __global__ void k_export(const Dev d, const int32_t* __restrict__ off, double* _
     }
 }
 
+// Forces (context layout, FP32 in MIXED or FP64) -> caller layout [Ntot][3] doubles, and each cluster's
+// potential energy from the observables record of the last fresh evaluation.
+template <int PREC>
+__global__ void k_export_forces(const Dev d, const int32_t* __restrict__ off, double* __restrict__ forces,
+                                double* __restrict__ epot, int hist_slot) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (epot && p < d.B) epot[p] = d.hist[((size_t)hist_slot * d.B + p) * kHistFields];
+    if (!forces || p >= d.npad) return;
+    const int cl = d.cl_of_group[p >> 5];
+    const int a = p - d.poff[cl];
+    if (a >= d.nreal[cl]) return;
+    const int64_t s = (int64_t)off[cl] + a;
+    const int np = d.npad;
+    for (int c = 0; c < 3; ++c)
+        forces[3 * s + c] = PREC == 1 ? (double)reinterpret_cast<const float*>(d.f)[c * np + p]
+                                      : reinterpret_cast<const double*>(d.f)[c * np + p];
+}
+
 }  // namespace
 
 int invalid_input_bit() { return kInvalidInputBit; }
+
+cudaError_t launch_export_forces(const Dev& d, const int32_t* off, double* forces, double* epot, int hist_slot,
+                                 cudaStream_t s) {
+    const int n = d.npad > d.B ? d.npad : d.B;
+    if (d.prec == 1)
+        k_export_forces<1><<<(n + 255) / 256, 256, 0, s>>>(d, off, forces, epot, hist_slot);
+    else
+        k_export_forces<0><<<(n + 255) / 256, 256, 0, s>>>(d, off, forces, epot, hist_slot);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_check_input(const double* pos, const double* vel, const double* mass, int64_t ntot,
                                int32_t* status, cudaStream_t s) {

@@ -268,6 +268,9 @@ cudaError_t launch_check_input(const double* pos, const double* vel, const doubl
 cudaError_t launch_import(const Dev& d, const int32_t* off, const double* pos, const double* vel,
                           const double* mass, cudaStream_t s);
 cudaError_t launch_export(const Dev& d, const int32_t* off, double* pos, double* vel, cudaStream_t s);
+// forces (caller layout, doubles) and per-cluster potential energies from history slot hist_slot
+cudaError_t launch_export_forces(const Dev& d, const int32_t* off, double* forces, double* epot, int hist_slot,
+                                 cudaStream_t s);
 // The calling thread's error message returned by md_last_error(NULL) (defined in scmd_api.cu).
 void set_thread_error(const char* msg);
 cudaError_t configure_kernels();

@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
                 "md_create_device": ([P(md_config), i32, P(i32), _VP, _VP, _VP, P(md_sc_params), P(_VP)], i32),
                 "md_get_state": ([_VP, _DP, _DP, P(i64)], i32),
                 "md_get_state_device": ([_VP, _VP, _VP, P(i64)], i32),
+                "md_energy_forces_device": ([_VP, _VP, _VP], i32),
                 "md_set_state_device": ([_VP, _VP, _VP, i64], i32),
                 "md_fp32_peak": ([i32, _DP, _DP], i32),
                 "md_set_state": ([_VP, _DP, _DP, i64], i32),
@@ -118,7 +119,7 @@ def exported_symbols():
             "md_get_launch", "md_set_launch", "md_autotune", "md_time_passes", "md_launch_counts", "md_get_path",
             "md_last_error", "md_destroy", "md_philox4x32_10", "md_langevin_normals",
             "md_energy_forces_noalloc", "md_rdf", "md_msd_reference", "md_msd", "md_cna", "md_create_device",
-            "md_get_state_device", "md_set_state_device", "md_fp32_peak"]
+            "md_get_state_device", "md_set_state_device", "md_fp32_peak", "md_energy_forces_device"]
 
 
 def md_abi_version() -> int:
@@ -225,6 +226,11 @@ def md_get_state_device(ctx: Context, pos_dev, vel_dev) -> int:
     _check(lib().md_get_state_device(ctx.handle, _dptr(pos_dev) or None, _dptr(vel_dev) or None, ctypes.byref(step)),
            ctx.handle)
     return step.value
+
+
+def md_energy_forces_device(ctx: Context, epot_dev, forces_dev):
+    """Energies [n_clusters] and forces [Ntot][3] (float64) into caller-owned device arrays (either may be None)."""
+    _check(lib().md_energy_forces_device(ctx.handle, _dptr(epot_dev) or None, _dptr(forces_dev) or None), ctx.handle)
 
 
 def md_set_state_device(ctx: Context, pos_dev, vel_dev, step: int):

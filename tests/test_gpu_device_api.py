@@ -135,3 +135,19 @@ def test_fp32_peak_is_measured(env):
     _, scmd = env
     meas, derived = scmd.md_fp32_peak(5)
     assert 0.5 * derived < meas < 1.1 * derived, (meas, derived)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_energy_forces_into_device_arrays(env, prec):
+    torch, scmd = env
+    sizes = [700, 55]
+    pos = np.concatenate([inputs.jitter(inputs.fcc_sphere(700), 0.15, 31), inputs.fcc_sphere(55) + 40.0])
+    ctx = scmd.md_create(scmd.config(precision=prec), sizes, pos, None, inputs.masses(755))
+    E, F = scmd.md_energy_forces(ctx)
+    tE = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    tF = torch.full((755, 3), float("nan"), dtype=torch.float64, device="cuda")
+    scmd.md_energy_forces_device(ctx, tE, tF)
+    assert np.array_equal(tE.cpu().numpy(), E) and np.array_equal(tF.cpu().numpy(), F)
+    only = torch.zeros((2,), dtype=torch.float64, device="cuda")
+    scmd.md_energy_forces_device(ctx, only, None)
+    assert np.array_equal(only.cpu().numpy(), E)
