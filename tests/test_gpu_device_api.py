@@ -1,8 +1,7 @@
 """Contexts made from, and state exchanged with, caller-owned device memory (PyTorch CUDA tensors):
 md_create_device, md_get_state_device, md_set_state_device, md_energy_forces_device. The results must
 equal those of the host entry points bit for bit (the same values reach the same kernels) and the oracle
-within the usual
-tolerances (e_F <= 1e-5 / 1e-12, |dE|/|E| <= 1e-6 / 1e-13 for MIXED / FP64)."""
+within the usual tolerances (e_F <= 1e-5 / 1e-12, |dE|/|E| <= 1e-6 / 1e-13 for MIXED / FP64)."""
 import numpy as np
 import pytest
 
