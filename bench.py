@@ -406,7 +406,9 @@ def main():
     pair_rate = pairs_per_eval * md_steps_total * world / t_max
     peak_clock = (clocks or {}).get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    peak_ops = n_sm * FP32_LANES_PER_SM * peak_clock * 1e6
+    # the pair passes run on the FP32 pipe in MIXED and on the FP64 pipe (1/64 of the FP32 lanes) in FP64
+    lanes = FP32_LANES_PER_SM if prec == "mixed" else FP32_LANES_PER_SM / 64
+    peak_ops = n_sm * lanes * peak_clock * 1e6
     ffma_measured, _ = scmd.md_fp32_peak(10)
     # algorithmic work of a launch: every ordered pair for all pairs; the pairs closer than rcut with a
     # cutoff (the candidates the cell or neighbour lists test are reported beside)
@@ -545,13 +547,14 @@ def main():
                     "wall_s_timed_region": t_wall},
             "pair_evals_per_s": pair_rate if not cells else useful_pairs * md_steps_total * world / t_max,
             "candidate_pairs_per_s": pair_rate if cells else None,
-            "fp32_pipe_frac_force_pass": achieved / peak_ops,
+            "fp32_pipe_frac_force_pass": achieved / peak_ops if prec == "mixed" else None,
             "force_err_vs_oracle": force_err,
             "force_err_snapshots": snap_err or None,
             "nve_drift": drift,
             "structure": structure,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "T FP32-lane-ops/s", "frac": achieved / peak_ops,
+                         "unit": "T FP32-lane-ops/s" if prec == "mixed" else "T FP64-lane-ops/s",
+                         "frac": achieved / peak_ops,
                          "traffic": force_traffic(args.config, path_name) if prec == "mixed" else None,
                          "kernel": {"cells": "k_cell_force (force pass, cell list)",
                                     "neighbour lists": "k_q_force (force pass, quad lists)" if prec == "mixed"
@@ -560,9 +563,11 @@ def main():
                          "ms_per_launch": ms_f,
                          "density_pass_ms_per_launch": ms_d, "pairs_per_launch": alg_pairs,
                          "tested_pairs_per_launch": pairs if cells else None,
-                         "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {peak_clock:.0f} MHz (max SM clock)",
+                         "peak_basis": (f"{n_sm} SMs x 128 FP32 lanes x {peak_clock:.0f} MHz (max SM clock)"
+                                        if prec == "mixed" else
+                                        f"{n_sm} SMs x 2 FP64 lanes (1/64 of FP32) x {peak_clock:.0f} MHz (max SM clock)"),
                          "peak_measured_ffma": ffma_measured / 1e12,
-                         "frac_of_measured_ffma": achieved / ffma_measured,
+                         "frac_of_measured_ffma": achieved / ffma_measured if prec == "mixed" else None,
                          "launch_timing": "CUDA events over back-to-back launches (PDL overlap as in the step graph)",
                          "passes_ms_per_md_step": ms_d + ms_f if not cells else None,
                          "ms_per_md_step": 1e3 * t_max / md_steps_total},
