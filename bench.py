@@ -418,7 +418,10 @@ def main():
         pf, _, _ = scmd.md_get_state(ctx)
         useful_pairs = 2.0 * len(cKDTree(pf).query_pairs(rcut, output_type="ndarray"))
     alg_pairs = useful_pairs if cells else pairs
-    achieved = FORCE_OPS_PER_PAIR * alg_pairs / (ms_f * 1e-3)
+    ops_per_pair = FORCE_OPS_PER_PAIR
+    if path == scmd.MD_PATH_ALLPAIRS_HALF:  # each unordered pair once: its 16 ops plus 3 for the partner's force
+        alg_pairs, ops_per_pair = pairs / 2, FORCE_OPS_PER_PAIR + 3
+    achieved = ops_per_pair * alg_pairs / (ms_f * 1e-3)
     shapes = {"density": scmd.md_get_launch(ctx, 0), "force": scmd.md_get_launch(ctx, 1)}
     per_step, per_chunk = scmd.md_launch_counts(ctx)
     chunk = min(M, 512)
