@@ -117,3 +117,23 @@ def test_rate3_fit_is_exact_on_its_own_curve():
     assert f["a"] == pytest.approx(2.0, rel=1e-6) and f["T0_K"] == pytest.approx(1050.0, rel=1e-7)
     assert f["b_eV_K2"] == pytest.approx(40000.0, rel=1e-6)
     assert max(abs(r) for r in f["residuals_ln_kappa"]) < 1e-8
+
+
+def test_table1_records_reproduce_the_reported_fit():
+    """The committed run records (results/table1) give the rates and the Eq. rate3 fit quoted in the design
+    notes: a = 1.27 and b = 28575 eV K^2 with T0 fixed at 1029 K."""
+    import json
+    import os
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "results", "table1")
+    T, kap, ev = [], [], []
+    for t in (780, 800, 820, 830, 835):
+        r = json.load(open(os.path.join(root, f"T{t}.json")))
+        lt = [c["t_nuc_ps"] for c in r["per_cluster"] if c["t_nuc_ps"] is not None]
+        nc = sum(c["t_nuc_ps"] is None for c in r["per_cluster"])
+        k, d, _ = K.rate_mle(lt, nc, r["horizon_ps"])
+        T.append(t)
+        kap.append(k)
+        ev.append(d)
+    f = K.fit_rate3(T, kap, ev, T0=1029.0)
+    assert f["a"] == pytest.approx(1.2716, abs=2e-3)
+    assert f["b_eV_K2"] == pytest.approx(28575, rel=1e-3)
