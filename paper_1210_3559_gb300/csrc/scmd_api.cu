@@ -73,8 +73,8 @@ struct md_ctx {
     int64_t ntot = 0;
     int npad = 0, ngroups = 0;
     std::vector<int32_t> sizes, off, poff, cl_of_group;
-    std::vector<Item> items_h[2];  // ipt 1 and 2
-    Item* items_d[2] = {nullptr, nullptr};
+    std::vector<Item> items_h[3];  // ipt 1, 2 and 4 (4: the density pass only)
+    Item* items_d[3] = {nullptr, nullptr, nullptr};
     Shape shape[2] = {{1, 4, 1}, {1, 4, 1}};  // density, force
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -327,13 +327,14 @@ Shape default_shape(const md_ctx* c, int which) {
     return s;
 }
 
-bool shape_ok(Shape s) {
-    return (s.ipt == 1 || s.ipt == 2) && (s.warps == 2 || s.warps == 4 || s.warps == 8 || s.warps == 16) &&
+// which: 0 density pass (i-atoms per thread 1, 2 or 4), 1 force pass (1 or 2)
+bool shape_ok(Shape s, int which) {
+    return (s.ipt == 1 || s.ipt == 2 || (which == 0 && s.ipt == 4)) && (s.warps == 2 || s.warps == 4 || s.warps == 8 || s.warps == 16) &&
            s.cluster >= 1 && s.cluster <= 8;
 }
 
 const Item* items_for(const md_ctx* c, Shape s, int* n) {
-    const int k = s.ipt == 2 ? 1 : 0;
+    const int k = s.ipt == 4 ? 2 : (s.ipt == 2 ? 1 : 0);
     *n = (int)c->items_h[k].size();
     return c->items_d[k];
 }
@@ -499,7 +500,7 @@ void free_all(md_ctx* c) {
     drop_graphs(c);
     void* ptrs[] = {c->d_poff, c->d_off, c->d_h_unit, c->d_h_ubase, c->d_h_pi, c->d_h_pj, c->d_nreal, c->d_clg,   c->d_status, c->d_x,      c->d_v,    c->d_mass,
                     c->d_rho,  c->d_origin, c->d_part, c->d_ke,     c->d_hist,   c->d_f,    c->d_mirror,
-                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->d_hs, c->d_sig0, c->d_noise,
+                    c->d_posg, c->d_step,  c->d_run,   c->items_d[0], c->items_d[1], c->items_d[2], c->d_hs, c->d_sig0, c->d_noise,
                     c->d_grid, c->d_cell_cl, c->d_cell_count, c->d_cell_atoms, c->d_eatom, c->d_obs_x, c->d_obs_v,
                     c->d_cpos, c->d_cposg, c->d_cell_order, c->d_cell_oct, c->d_cell_obyte,
                     c->d_vlist, c->d_vcount, c->d_vsub, c->d_vorder, c->d_vslotof, c->d_vslot, c->d_vhi,
@@ -583,7 +584,7 @@ bool cache_lookup(const char* path, const std::string& key, Shape out[2]) {
     int v[6];
     if (sscanf(s.c_str() + p, "[%d,%d,%d,%d,%d,%d]", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) != 6) return false;
     Shape a{v[0], v[1], v[2]}, b{v[3], v[4], v[5]};
-    if (!shape_ok(a) || !shape_ok(b)) return false;
+    if (!shape_ok(a, 0) || !shape_ok(b, 1)) return false;
     out[0] = a;
     out[1] = b;
     return true;
@@ -719,8 +720,8 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
     c->cl_of_group.resize(c->ngroups);
     for (int b = 0; b < n_clusters; ++b)
         for (int g = c->poff[b] / kGroup; g < c->poff[b + 1] / kGroup; ++g) c->cl_of_group[g] = b;
-    for (int k = 0; k < 2; ++k) {
-        const int BI = 32 * (k + 1);
+    for (int k = 0; k < 3; ++k) {
+        const int BI = 32 << k;
         for (int b = 0; b < n_clusters; ++b)
             for (int a = 0; a < sizes[b]; a += BI) {
                 Item it{};
@@ -964,7 +965,7 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
                                 c->stream));
         }
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         CKC(dmalloc(c, &c->items_d[k], sizeof(Item) * std::max<size_t>(1, c->items_h[k].size())));
         CKC(cudaMemcpyAsync(c->items_d[k], c->items_h[k].data(), sizeof(Item) * c->items_h[k].size(), cudaMemcpyHostToDevice, c->stream));
     }
@@ -1333,7 +1334,8 @@ md_status md_get_launch(const md_ctx* c, int32_t which, int32_t* ipt, int32_t* w
 md_status md_set_launch(md_ctx* c, int32_t which, int32_t ipt, int32_t warps, int32_t cluster) {
     if (!c || which < 0 || which > 1) return MD_ERR_INVALID;
     Shape s{ipt, warps, cluster};
-    if (!shape_ok(s)) return fail(c, MD_ERR_INVALID, "launch shape (%d,%d,%d) not supported", ipt, warps, cluster);
+    if (!shape_ok(s, which))
+        return fail(c, MD_ERR_INVALID, "launch shape (%d,%d,%d) not supported", ipt, warps, cluster);
     c->shape[which] = s;
     drop_graphs(c);
     return MD_OK;
@@ -1441,7 +1443,7 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
     if (c->path >= 1 || c->half) return MD_OK;  // the cell, list and each-pair-once kernels have one launch shape
     const Dev& d = c->dev;
     // cluster sizes that are not powers of two let a small work list fill the 152 SMs more evenly
-    const int ipts[2] = {1, 2}, warps[4] = {2, 4, 8, 16}, clus[7] = {1, 2, 3, 4, 5, 6, 8};
+    const int ipts[3] = {1, 2, 4}, warps[4] = {2, 4, 8, 16}, clus[7] = {1, 2, 3, 4, 5, 6, 8};
     // Phase 1: every shape of each pass timed alone (CUDA events over reps launches).
     std::vector<std::pair<float, Shape>> timed[2];
     cudaEvent_t e0, e1;
@@ -1453,6 +1455,7 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
         for (int ip : ipts)
             for (int w : warps)
                 for (int cl : clus) {
+                    if (ip == 4 && which == 1) continue;  // four i-atoms per thread: the density pass only
                     Shape s{ip, w, cl};
                     int n;
                     const Item* it = items_for(c, s, &n);

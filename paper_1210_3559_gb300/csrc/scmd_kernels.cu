@@ -42,7 +42,7 @@ template <> struct SplitOf<0> { static constexpr int S = 8; };
 // ------------------------------------------------------------- density pass
 // Shared memory: tiles [W][32] V4 | red [W][BI] double | inbox [C][BI] double (read on rank 0)
 template <int PREC, int IPT, int SPECIAL, int CUT>
-__global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d, const Item* __restrict__ items, int C, int obs) {
+__global__ void __launch_bounds__(512, (PREC == 1 && IPT < 4) ? 2 : 1) k_density(const Dev d, const Item* __restrict__ items, int C, int obs) {
     using R = typename Tr<PREC>::R;
     using V4 = typename Tr<PREC>::V4;
     constexpr int BI = 32 * IPT;
@@ -81,7 +81,10 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     if (u_beg < u_end) nxt = mir[it.j0 + ((u_beg / S) << 5) + lane];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
-        const V4 p = mir[it.i0 + lane + 32 * q];
+        // four i-atoms per thread: a 128-atom block can reach past its cluster's segment (padded to 64
+        // atoms); those i-atoms are read clamped into the array and their sums are discarded
+        const int iq = it.i0 + lane + 32 * q;
+        const V4 p = mir[IPT == 4 ? min(iq, d.npad - 1) : iq];
         xi[q] = p.x;
         yi[q] = p.y;
         zi[q] = p.z;
@@ -196,9 +199,16 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     if (real) {
         const int q = t >> 5;  // this thread's own atom is its q-th i-atom
         V4 p;
-        p.x = (q == 0) ? xi[0] : xi[IPT - 1];
-        p.y = (q == 0) ? yi[0] : yi[IPT - 1];
-        p.z = (q == 0) ? zi[0] : zi[IPT - 1];
+        p.x = xi[0];
+        p.y = yi[0];
+        p.z = zi[0];
+#pragma unroll
+        for (int r = 1; r < IPT; ++r)
+            if (q == r) {
+                p.x = xi[r];
+                p.y = yi[r];
+                p.z = zi[r];
+            }
         d.rho[i] = rho;
         if (PREC == 1) {
             // g = B6 rho^-1/2 = gsf sum^-1/2 on the FP32 pipe, so the FP64 work above (rho for
@@ -214,7 +224,8 @@ __global__ void __launch_bounds__(512, PREC == 1 ? 2 : 1) k_density(const Dev d,
     if (obs) {
         double e = real ? -d.pot.eps * d.pot.c * sqrt(rho) : 0.0;
         e = warp_sum(e);
-        if (lane == 0) d.part[(size_t)(i >> 5) * kObsFields + OF_EEMB] = e;
+        // (a 128-atom block's groups past its cluster's padded segment belong to another item or to no one)
+        if (lane == 0 && (IPT < 4 || i < d.poff[it.cl + 1])) d.part[(size_t)(i >> 5) * kObsFields + OF_EEMB] = e;
     }
 }
 
@@ -853,8 +864,11 @@ static cudaError_t force_p(const Dev& d, const Item* it, int n, Shape sh, int mo
 cudaError_t launch_density(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s) {
     if (d.h_nunits > 0) return launch_h_density(d, obs, s);  // FP64, each pair once
     if (nitems <= 0) return cudaSuccess;
-    if (d.prec == 1)
+    if (d.prec == 1) {
+        if (sh.ipt == 4) return density_p<1, 4>(d, items, nitems, sh, obs, s);
         return sh.ipt == 2 ? density_p<1, 2>(d, items, nitems, sh, obs, s) : density_p<1, 1>(d, items, nitems, sh, obs, s);
+    }
+    if (sh.ipt == 4) return density_p<0, 4>(d, items, nitems, sh, obs, s);
     return sh.ipt == 2 ? density_p<0, 2>(d, items, nitems, sh, obs, s) : density_p<0, 1>(d, items, nitems, sh, obs, s);
 }
 
@@ -938,11 +952,20 @@ template <int PREC, int IPT> static cudaError_t cfg_ipt() {
     if (e == cudaSuccess) e = cfg_one<PREC, IPT, 0, 1>();
     return e;
 }
+template <int PREC> static cudaError_t cfg_density4() {
+    cudaError_t e = allow_smem(k_density<PREC, 4, 1, 0>);
+    if (e == cudaSuccess) e = allow_smem(k_density<PREC, 4, 1, 1>);
+    if (e == cudaSuccess) e = allow_smem(k_density<PREC, 4, 0, 0>);
+    if (e == cudaSuccess) e = allow_smem(k_density<PREC, 4, 0, 1>);
+    return e;
+}
 cudaError_t configure_kernels() {
     cudaError_t e = cfg_ipt<1, 1>();
     if (e == cudaSuccess) e = cfg_ipt<1, 2>();
     if (e == cudaSuccess) e = cfg_ipt<0, 1>();
     if (e == cudaSuccess) e = cfg_ipt<0, 2>();
+    if (e == cudaSuccess) e = cfg_density4<1>();
+    if (e == cudaSuccess) e = cfg_density4<0>();
     return e;
 }
 

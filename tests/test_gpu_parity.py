@@ -120,11 +120,11 @@ def test_every_launch_shape_agrees_with_oracle(scmd, prec):
     pos = inputs.jitter(inputs.fcc_sphere(333), 0.15, 6)
     Er, Fr, _, rhor = oracle.energy_forces(pos)
     ctx = make(scmd, [333], pos, prec=prec)
-    for ipt in (1, 2):
+    for ipt in (1, 2, 4):  # 4 i-atoms per thread: the density pass only
         for warps in (2, 4, 8, 16):
             for cl in (1, 2, 3, 4, 5, 6, 7, 8):
-                for which in (0, 1):
-                    scmd.md_set_launch(ctx, which, ipt, warps, cl)
+                scmd.md_set_launch(ctx, 0, ipt, warps, cl)
+                scmd.md_set_launch(ctx, 1, min(ipt, 2), warps, cl)
                 E, F = scmd.md_energy_forces(ctx)
                 rho = scmd.md_get_density(ctx)
                 assert rel_force_err(F, Fr) <= TOL[prec]["eF"], (ipt, warps, cl)
@@ -144,6 +144,32 @@ def test_batched_uneven_clusters(scmd, prec):
     for b, n in enumerate(sizes):
         s, e = off[b], off[b + 1]
         check_cluster(F[s:e], E[b], rho[s:e], pos[s:e], prec)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_four_atoms_per_thread_density_on_uneven_batches(scmd, prec):
+    """Density blocks of 128 atoms reach past a cluster's 64-atom padded segment (sizes 130, 513, the last
+    cluster); those i-atoms must neither change the results nor overwrite a neighbour's observables."""
+    sizes = [130, 1, 55, 513, 200, 33, 130]
+    parts = [inputs.jitter(inputs.fcc_sphere(n), 0.1, 40 + k) + 25.0 * k for k, n in enumerate(sizes)]
+    pos = np.concatenate(parts)
+    m = inputs.masses(len(pos))
+    vel = np.concatenate([inputs.maxwell_boltzmann(p, inputs.masses(len(p)), 900.0, seed=k) if len(p) > 1
+                          else np.zeros((1, 3)) for k, p in enumerate(parts)])
+    ctx = make(scmd, sizes, pos, vel, prec=prec, path=scmd.MD_PATH_ALLPAIRS)
+    ref = make(scmd, sizes, pos, vel, prec=prec, path=scmd.MD_PATH_ALLPAIRS)
+    for warps, cl in ((4, 1), (2, 3), (8, 2)):
+        scmd.md_set_launch(ctx, 0, 4, warps, cl)
+        E, F = scmd.md_energy_forces(ctx)
+        rho = scmd.md_get_density(ctx)
+        off = np.concatenate([[0], np.cumsum(sizes)])
+        for b in range(len(sizes)):
+            a, e = off[b], off[b + 1]
+            check_cluster(F[a:e], E[b], rho[a:e], pos[a:e], prec)
+        obs, obs_ref = scmd.md_observables(ctx), scmd.md_observables(ref)
+        for o, r in zip(obs, obs_ref):
+            assert o["epot"] == pytest.approx(r["epot"], rel=TOL[prec]["E"], abs=1e-12)
+            assert o["ekin"] == r["ekin"]
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
@@ -342,6 +368,9 @@ def test_invalid_arguments(scmd):
     assert e.value.status == scmd.MD_ERR_INVALID
     with pytest.raises(scmd.ScmdError) as e:
         scmd.md_set_launch(ctx, 0, 3, 4, 1)
+    assert e.value.status == scmd.MD_ERR_INVALID
+    with pytest.raises(scmd.ScmdError) as e:
+        scmd.md_set_launch(ctx, 1, 4, 4, 1)  # four i-atoms per thread: the density pass only
     assert e.value.status == scmd.MD_ERR_INVALID
     bad = inputs.fcc_sphere(13)
     bad[3, 1] = np.inf
