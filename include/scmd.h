@@ -273,8 +273,8 @@ md_status md_get_forces(md_ctx* ctx, double* forces_eV_per_A);
  * Launch shape of the two pair passes: i-atoms per thread (ipt), warps per
  * CTA (warps) and CTAs per thread-block cluster (cluster). md_get_launch
  * reads the current choice; md_set_launch overrides it (values outside
- * ipt in {1,2} (or 4 for the density pass), warps in {2,4,8,16}, cluster in 1..8 ->
- * MD_ERR_INVALID).
+ * ipt in {1,2} (or 4 for the density pass), warps in {2,4,8,16} with warps >= ipt,
+ * cluster in 1..8 -> MD_ERR_INVALID).
  * which: 0 = density pass, 1 = force pass.
  */
 md_status md_get_launch(const md_ctx* ctx, int32_t which, int32_t* ipt, int32_t* warps, int32_t* cluster);

@@ -327,9 +327,10 @@ Shape default_shape(const md_ctx* c, int which) {
     return s;
 }
 
-// which: 0 density pass (i-atoms per thread 1, 2 or 4), 1 force pass (1 or 2)
+// which: 0 density pass (i-atoms per thread 1, 2 or 4), 1 force pass (1 or 2). A CTA needs at least one
+// thread per i-atom of its block (the reduction and the epilogue take one atom per thread): ipt <= warps.
 bool shape_ok(Shape s, int which) {
-    return (s.ipt == 1 || s.ipt == 2 || (which == 0 && s.ipt == 4)) && (s.warps == 2 || s.warps == 4 || s.warps == 8 || s.warps == 16) &&
+    return (s.ipt == 1 || s.ipt == 2 || (which == 0 && s.ipt == 4)) && s.ipt <= s.warps && (s.warps == 2 || s.warps == 4 || s.warps == 8 || s.warps == 16) &&
            s.cluster >= 1 && s.cluster <= 8;
 }
 
@@ -1455,8 +1456,8 @@ md_status md_autotune(md_ctx* c, int32_t reps) {
         for (int ip : ipts)
             for (int w : warps)
                 for (int cl : clus) {
-                    if (ip == 4 && which == 1) continue;  // four i-atoms per thread: the density pass only
                     Shape s{ip, w, cl};
+                    if (!shape_ok(s, which)) continue;  // e.g. four i-atoms per thread: density only, >= 4 warps
                     int n;
                     const Item* it = items_for(c, s, &n);
                     auto run = [&]() {

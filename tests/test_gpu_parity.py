@@ -120,8 +120,8 @@ def test_every_launch_shape_agrees_with_oracle(scmd, prec):
     pos = inputs.jitter(inputs.fcc_sphere(333), 0.15, 6)
     Er, Fr, _, rhor = oracle.energy_forces(pos)
     ctx = make(scmd, [333], pos, prec=prec)
-    for ipt in (1, 2, 4):  # 4 i-atoms per thread: the density pass only
-        for warps in (2, 4, 8, 16):
+    for ipt in (1, 2, 4):  # 4 i-atoms per thread: the density pass only, with >= 4 warps
+        for warps in (w for w in (2, 4, 8, 16) if w >= ipt):
             for cl in (1, 2, 3, 4, 5, 6, 7, 8):
                 scmd.md_set_launch(ctx, 0, ipt, warps, cl)
                 scmd.md_set_launch(ctx, 1, min(ipt, 2), warps, cl)
@@ -371,6 +371,9 @@ def test_invalid_arguments(scmd):
     assert e.value.status == scmd.MD_ERR_INVALID
     with pytest.raises(scmd.ScmdError) as e:
         scmd.md_set_launch(ctx, 1, 4, 4, 1)  # four i-atoms per thread: the density pass only
+    assert e.value.status == scmd.MD_ERR_INVALID
+    with pytest.raises(scmd.ScmdError) as e:
+        scmd.md_set_launch(ctx, 0, 4, 2, 1)  # ... and with at least one thread per i-atom
     assert e.value.status == scmd.MD_ERR_INVALID
     bad = inputs.fcc_sphere(13)
     bad[3, 1] = np.inf
