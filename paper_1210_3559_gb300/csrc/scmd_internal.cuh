@@ -213,7 +213,7 @@ cudaError_t launch_advance(const Dev& d, int nsteps, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int n, cudaStream_t s);
 cudaError_t launch_normals(uint64_t seed, uint32_t cluster, int64_t step, int n, int prec, double* out,
                            cudaStream_t s);
-size_t pass_smem_bytes(int prec, Shape sh);
+size_t pass_smem_bytes(int prec, Shape sh, int which);  // which: 0 density pass, 1 force pass
 // Cell-list path (defined in scmd_cells.cu).
 // clear, bin, sort; cond != 0: only when a neighbour-list rebuild is due at local step k_local
 cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond = 0, int k_local = 0);

@@ -820,12 +820,13 @@ __global__ void k_normals(uint64_t seed, uint32_t cl, int64_t step, int n, int p
 }
 
 // ---------------------------------------------------------------- launchers
-size_t pass_smem_bytes(int prec, Shape sh) {
+size_t pass_smem_bytes(int prec, Shape sh, int which) {
     const size_t v4 = prec == 1 ? sizeof(float4) : sizeof(dbl4);
     const size_t r = prec == 1 ? sizeof(float) : sizeof(double);
     const size_t BI = 32 * (size_t)sh.ipt, W = sh.warps, C = sh.cluster;
     const size_t tiles = W * 32 * v4;
     const size_t dens = (W + C) * BI * sizeof(double);
+    if (which == 0) return tiles + dens;  // density pass: tiles, per-warp partials, the cluster inbox
     const size_t force = (W + C) * BI * sizeof(double) + (W + C) * BI * 3 * r;
     // force pass: the epilogue slots follow the reduction buffers, 16-byte aligned
     const size_t force_slots = ((tiles + force + 15) / 16) * 16 - tiles + BI * sizeof(EpiSlot);
@@ -835,13 +836,13 @@ size_t pass_smem_bytes(int prec, Shape sh) {
 template <int PREC, int IPT, int SPECIAL, int CUT>
 static cudaError_t density_t(const Dev& d, const Item* items, int nitems, Shape sh, int obs, cudaStream_t s) {
     return launch_cluster(k_density<PREC, IPT, SPECIAL, CUT>, nitems * sh.cluster, sh.warps * 32,
-                          pass_smem_bytes(PREC, sh), sh.cluster, s, d, items, sh.cluster, obs);
+                          pass_smem_bytes(PREC, sh, 0), sh.cluster, s, d, items, sh.cluster, obs);
 }
 template <int PREC, int IPT, int SPECIAL, int CUT, int ENERGY>
 static cudaError_t force_t(const Dev& d, const Item* items, int nitems, Shape sh, int mode, int k_local, int last,
                            cudaStream_t s) {
     return launch_cluster(k_force<PREC, IPT, SPECIAL, CUT, ENERGY>, nitems * sh.cluster, sh.warps * 32,
-                          pass_smem_bytes(PREC, sh), sh.cluster, s, d, items, sh.cluster, mode, k_local, last);
+                          pass_smem_bytes(PREC, sh, 1), sh.cluster, s, d, items, sh.cluster, mode, k_local, last);
 }
 
 template <int PREC, int IPT>
