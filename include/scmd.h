@@ -297,8 +297,8 @@ md_status md_autotune(md_ctx* ctx, int32_t reps);
  * pass includes its gather kernel). Pair-evaluation counts per launch are returned in *pairs
  * (ordered pairs visited per pass: sum N_b (N_b - 1) for all pairs; for the cell
  * path, every atom times the atoms of the 5 x 5 x 5 cell octants around its own,
- * self included, as binned at the current positions; for the MIXED lists, 16
- * per listed quad plus the 12 within each quad; for the FP64 lists, twice the
+ * self included, as binned at the current positions; for the MIXED lists, 4
+ * per listed atom (one per atom of the quad) plus the 12 within each quad; for the FP64 lists, twice the
  * half-list entries). Any output
  * may be NULL.
  */
@@ -319,7 +319,7 @@ md_status md_fp32_peak(int32_t reps, double* measured_ops_per_s, double* derived
 
 /* Number of GPU kernels issued per md_step step (all pairs: 2, or 4 with
  * MD_PATH_ALLPAIRS_HALF, cells: 5,
- * neighbour lists: 8 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
+ * neighbour lists: 7 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
  * cells or lists, and the observable kernels of recorded steps) and per graph
  * replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);

@@ -1388,7 +1388,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
     if (st != MD_OK) return fail(c, st, "pass launch failed while timing: %s", cudaGetErrorString(cudaGetLastError()));
     if (ms_d) *ms_d = td / reps;
     if (ms_f) *ms_f = tf / reps;
-    if (pairs && vl && c->nqmax > 0) {  // quad lists: 16 pairs per listed quad, 12 within each quad
+    if (pairs && vl && c->nqmax > 0) {  // quad lists: 4 pairs per listed atom, 12 within each quad
         int32_t nq = 0;
         std::vector<int32_t> cnt(c->nqmax);
         CK(c, cudaMemcpyAsync(&nq, c->d_q_n, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -1396,7 +1396,7 @@ md_status md_time_passes(md_ctx* c, int32_t reps, double* ms_d, double* ms_f, do
                               c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
         double p = 0;
-        for (int q = 0; q < nq && q < c->nqmax; ++q) p += 16.0 * cnt[q] + 12.0;
+        for (int q = 0; q < nq && q < c->nqmax; ++q) p += 4.0 * cnt[q] + 12.0;
         *pairs = p;
     } else if (pairs && vl) {  // half-list entries: each an unordered pair, i.e. two ordered pairs
         std::vector<int32_t> cnt(c->ntot);
@@ -1563,10 +1563,10 @@ md_status md_get_path(const md_ctx* c, int32_t* path) {
 
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
-    // lists: positions, cell build (3), list build (MIXED scan, order, list; FP64 build, sort, reverse sort,
-    // commit), passes (MIXED 2; FP64 compaction, 2 passes, 2 gathers)
+    // lists: positions, cell build (FP64 3: clear, bin, sort; MIXED 2: clear, bin), list build (MIXED scan,
+    // order, list; FP64 build, sort, reverse sort, commit), passes (MIXED 2; FP64 compaction, 2 passes, 2 gathers)
     // (MIXED: the position kernel runs once per chunk, and every step with Berendsen)
-    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 8 : 13) : (c->path == 1 ? 5 : (c->half ? 4 : 2));
+    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 7 : 13) : (c->path == 1 ? 5 : (c->half ? 4 : 2));
     if (per_chunk) *per_chunk = c->path == 2 && c->nqmax > 0 ? 4 : 3;
     return MD_OK;
 }

@@ -397,6 +397,9 @@ cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond, int k_loca
     e = d.prec == 1 ? launch_ex(k_cell_bin<1>, (d.npad + 255) / 256, 256, 0, 0, s, d, cond, k_local)
                     : launch_ex(k_cell_bin<0>, (d.npad + 255) / 256, 256, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
+    // MIXED neighbour lists: the quad build ranks each cell's atoms itself (by sub-cell, then index), from
+    // the binned order, so the sort would not change any result
+    if (d.path == 2 && d.prec == 1) return cudaSuccess;
     return d.prec == 1 ? launch_ex(k_cell_sort<1>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d, cond, k_local)
                        : launch_ex(k_cell_sort<0>, (d.n_cells + 7) / 8, kCellThreads, 0, 0, s, d, cond, k_local);
 }

@@ -30,7 +30,7 @@ constexpr int kCellCap = 256;   // atoms a cell of the cell-list path can hold
 constexpr int kVMax = 512;      // entries a neighbour list can hold
 constexpr int kVLog = 3;        // a list is split into kVLanes sub-lists, one per thread of its atom
 constexpr int kVLanes = 1 << kVLog;
-constexpr int kQMax = 768;      // quads a quad's neighbour list can hold (MIXED lists; a multiple of 16)
+constexpr int kQMax = 2048;     // atoms a quad's neighbour list can hold (MIXED lists)
 constexpr float kQuadFar = 1.0e5f;  // MIXED lists: offset of an empty slot (the padding quad's slots sit at -kQuadFar)
 
 // Fields of an observable partial record (per 32-atom group).
@@ -178,9 +178,9 @@ struct Dev {
     float4* q_ref;       // [nqmax] reference point of each quad relative to the origin (a multiple of 2^-12 A)
     float4* q_box;       // [nqmax][2] bounding box (lo, hi) of its atoms at the rebuild, relative to the origin
     int32_t* q_cell;     // [nqmax] cell of each quad
-    int32_t* q_list;     // [nqmax][kQMax] the other quads with an atom within rcut + skin of one of this one's,
-                         // padded to a multiple of 16 entries with the padding quad nqmax (reference point 0,
-                         // its 4 slots at -kQuadFar)
+    int32_t* q_list;     // [nqmax][kQMax] the slots of the atoms, not of the quad, within rcut + skin of one of
+                         // its atoms at the rebuild (lanes past a list's end read the padding quad nqmax,
+                         // reference point 0, its 4 slots at -kQuadFar)
     int32_t* q_count;    // [nqmax]
     // FP64 all pairs with each pair evaluated once (scmd_half64.cu); h_nunits == 0: ordered pairs
     int32_t h_nunits;    // work units: (i-tile of 32 atoms, j half-tile of 16) with the half-tile at or after the i-tile

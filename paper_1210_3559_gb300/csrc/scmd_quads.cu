@@ -1,31 +1,31 @@
-// scmd_quads.cu -- MIXED neighbour lists as lists of atom quads (the pair passes with a strict cutoff).
+// scmd_quads.cu -- MIXED neighbour lists kept per atom quad (the pair passes with a strict cutoff).
 //
 // Per-atom lists make every tested pair a gather of a random neighbour, and in FP32 those gathers,
 // not the arithmetic, bound the passes. Here the unit is a quad: 4 consecutive slots of one cell,
-// with a cell's atoms in Morton order (sub-cells of side h/8), so a quad is a compact group. Each
-// quad keeps the list of quads with an atom within rcut + skin of one of its own at the last
-// rebuild. A pass runs one warp per quad: lane l holds atom l % 4 of the (l / 4)-th of 8 listed
-// quads and tests it against the 4 atoms of the warp's own quad, so one warp-wide load brings 32
-// neighbours for 128 pairs. Per step:
+// a compact group found by recursive bisection of the cell's atoms. Each quad keeps the list of
+// the atoms, other than its own, within rcut + skin of one of its atoms at the last rebuild. A pass
+// gives each quad a group of lanes, its 4 atoms in their registers: a lane gathers one listed atom
+// at a time and tests it against all 4, so one gather serves 4 pairs. Per step:
 //   k_q_pos    : every slot's offset from its quad's reference point, and the largest squared
 //                displacement since the last rebuild (at a chunk's first step and with Berendsen;
 //                otherwise the previous step's force pass, which moved the atoms, did this);
 //   rebuild, when that displacement exceeds the trigger (the kernels exit at once otherwise):
-//     the cell build of the cell-list path (clear, bin, sort), then
+//     the cell build of the cell-list path (clear, bin; the ranking below makes its sort needless), then
 //     k_q_scan   : the first slot of every cell (cells padded to whole quads), and the quad count;
-//     k_q_order  : one CTA per cell: its atoms in Morton order into slots; per quad the reference
-//                  point, the bounding box and the offsets;
-//     k_q_list   : one warp per quad: the quads of the 27 cells around it with an atom in reach of
-//                  one of its atoms (boxes tested first);
-//   k_q_density, k_q_force : one warp per quad; per CTA of 8 quads, one warp then finishes the 32
-//                atoms (the FP64 per-atom work on full warps).
+//     k_q_order  : one CTA per cell: its atoms bisected into quads and placed in slots; per quad the
+//                  reference point, the bounding box and the offsets;
+//     k_q_list   : one warp per quad: the atoms of the 27 cells around it in reach of one of its
+//                  atoms (the quads' boxes tested first);
+//   k_q_density, k_q_force : kQLanes lanes per quad; per CTA of 8 quads, one warp then finishes the
+//                32 atoms (the FP64 per-atom work on full warps).
 // Coordinates: a quad's reference point C is its atoms' centroid rounded to a multiple of 2^-12 A,
 // exact in FP32, so C_i - C_j is exact; an atom is stored as its FP32 offset o = x - C (|o| of a
 // few A). A listed atom enters a pair as o_j - (C_i - C_j), rounded once, like the staged positions
-// of the cell-list passes. The self pair gives r^2 = 0 exactly and is masked with the cutoff test.
-// The sums run over quads in list order, which depends on when the lists were built: unlike the
-// FP64 lists, a resumed MIXED run agrees with an uninterrupted one to rounding, not bit for bit.
-// Runs are deterministic: slots follow the cell order and lists the fixed order of the 27 cells.
+// of the cell-list passes. The quad's own pairs are summed apart, where the self pair (r^2 = 0
+// exactly) is masked; the lists hold no own atom, so their loop tests the cutoff alone.
+// The sums run in list order, which depends on when the lists were built: unlike the FP64 lists,
+// a resumed MIXED run agrees with an uninterrupted one to rounding, not bit for bit. Runs are
+// deterministic: slots follow the cell order and lists the fixed order of the 27 cells.
 #include <algorithm>
 
 #include "scmd_cells.cuh"
@@ -34,21 +34,31 @@ namespace scmd {
 
 namespace {
 
-constexpr int kQThreads = 256;  // 8 warps, one quad each
+constexpr int kQThreads = 256;  // the per-slot and list kernels (the list kernel: one warp per quad)
 constexpr float kFar = kQuadFar;  // coordinate of an empty slot: outside every cutoff of every atom
 
-// Sub-cell (side h/8) of an offset from the cell centre along one axis, clamped to the cell.
-__device__ __forceinline__ uint32_t sub8(float o, float h) {
-    const int k = (int)floorf((o + 0.5f * h) * (8.0f / h));
-    return (uint32_t)min(max(k, 0), 7);
+// Quads by recursive bisection: a cell's n places (in atom-index order to start) form a segment; a
+// segment of more than 4 places splits into a first part of 4 * floor(q / 2) places (q: its quads)
+// and the rest, each part taking the atoms below / above the median along the segment's widest axis.
+// Every part but a cell's last is then a whole number of quads, and the leaves are its quads.
+// Place r's segment after lev splits:
+__device__ __forceinline__ int2 kd_segment(int r, int n, int lev) {
+    int b = 0, e = n;
+    for (int l = 0; l < lev && e - b > 4; ++l) {
+        const int n1 = 4 * (((e - b + 3) >> 2) >> 1);
+        if (r < b + n1)
+            e = b + n1;
+        else
+            b += n1;
+    }
+    return make_int2(b, e);
 }
-__device__ __forceinline__ uint32_t morton9(const float4& p, float h) {
-    const uint32_t x = sub8(p.x, h), y = sub8(p.y, h), z = sub8(p.z, h);
-    uint32_t k = 0;
-#pragma unroll
-    for (int b = 2; b >= 0; --b) k = (k << 3) | (((x >> b) & 1u) << 2) | (((y >> b) & 1u) << 1) | ((z >> b) & 1u);
-    return k;
+// A coordinate as an integer of the same order (a total order, NaN included, so ranks stay distinct).
+__device__ __forceinline__ int ord_key(float v) {
+    const int b = __float_as_int(v);
+    return b >= 0 ? b : b ^ 0x7fffffff;
 }
+__device__ __forceinline__ float axis_of(const float4& p, int ax) { return ax == 0 ? p.x : (ax == 1 ? p.y : p.z); }
 
 // ---------------------------------------------------------------- every step
 __global__ void __launch_bounds__(kQThreads) k_q_pos(const Dev d, int k_local) {
@@ -117,11 +127,13 @@ __global__ void __launch_bounds__(1024) k_q_scan(const Dev d, int cond, int k_lo
     if (threadIdx.x == 0) *d.q_n = s_carry >> 2;
 }
 
-// One CTA per cell: rank its atoms by (Morton key of the sub-cell, index), place them, and set up
-// each of its quads.
+// One CTA per cell: order its atoms into quads by recursive bisection, place them, and set up each of
+// its quads.
 __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond, int k_local) {
-    __shared__ uint32_t s_key[kCellCap];
+    __shared__ float4 s_p[kCellCap];
     __shared__ int s_atom[kCellCap];
+    __shared__ int s_ord[kCellCap];  // place -> entry of s_p / s_atom
+    __shared__ int s_tmp[kCellCap];
     __shared__ int s_sorted[kCellCap];
     pdl_launch_dependents();
     pdl_wait();
@@ -131,20 +143,50 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
         const int n = min(d.cell_count[c], kCellCap);
         if (n == 0) continue;
         const int cl = d.cell_cl[c];
-        const float h = (float)d.grid[cl].h;
-        const float4* cp = reinterpret_cast<const float4*>(d.cpos);
+        const float4* cp = reinterpret_cast<const float4*>(d.cposg);  // the binned order (no cell sort)
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            s_key[k] = morton9(cp[(size_t)c * kCellCap + k], h);
+            s_p[k] = cp[(size_t)c * kCellCap + k];
             s_atom[k] = d.cell_atoms[(size_t)c * kCellCap + k];
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const uint32_t key = s_key[k];
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {  // start: atom-index order
             const int a = s_atom[k];
             int r = 0;
-            for (int m = 0; m < n; ++m) r += (s_key[m] < key) || (s_key[m] == key && s_atom[m] < a);
-            s_sorted[r] = a;
+            for (int m = 0; m < n; ++m) r += s_atom[m] < a;
+            s_ord[r] = k;
         }
+        __syncthreads();
+        const int nq = (n + 3) >> 2;
+        for (int lev = 0; (1 << lev) < nq; ++lev) {
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                const int2 sg = kd_segment(r, n, lev);
+                const int k = s_ord[r];
+                int to = r;
+                if (sg.y - sg.x > 4) {
+                    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+                    for (int m = sg.x; m < sg.y; ++m) {
+                        const float4 p = s_p[s_ord[m]];
+                        lo[0] = fminf(lo[0], p.x), hi[0] = fmaxf(hi[0], p.x);
+                        lo[1] = fminf(lo[1], p.y), hi[1] = fmaxf(hi[1], p.y);
+                        lo[2] = fminf(lo[2], p.z), hi[2] = fmaxf(hi[2], p.z);
+                    }
+                    const float ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+                    const int ax = (ex >= ey && ex >= ez) ? 0 : (ey >= ez ? 1 : 2);
+                    const int v = ord_key(axis_of(s_p[k], ax)), a = s_atom[k];
+                    int cnt = 0;
+                    for (int m = sg.x; m < sg.y; ++m) {
+                        const int km = s_ord[m], vm = ord_key(axis_of(s_p[km], ax));
+                        cnt += vm < v || (vm == v && s_atom[km] < a);
+                    }
+                    to = sg.x + cnt;
+                }
+                s_tmp[to] = k;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < n; r += blockDim.x) s_ord[r] = s_tmp[r];
+            __syncthreads();
+        }
+        for (int r = threadIdx.x; r < n; r += blockDim.x) s_sorted[r] = s_atom[s_ord[r]];
         __syncthreads();
         const int base = d.cell_base[c], n4 = (n + 3) & ~3, ns = d.nslot, np = d.npad;
         for (int r = threadIdx.x; r < n4; r += blockDim.x) {
@@ -197,9 +239,10 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
     }
 }
 
-// One warp per quad: the quads of the 27 cells around its cell (fixed order) with some atom closer
-// than rcut + skin to one of its atoms at the rebuild, appended in that order. The bounding boxes
-// screen the candidates; the 16 atom pairs decide.
+// One warp per quad: the atoms of the 27 cells around its cell (fixed order; slot order within a
+// cell) closer than rcut + skin to one of its atoms at the rebuild, its own atoms apart, appended in
+// that order. One lane per candidate slot: the bounding boxes of the quads screen the candidates,
+// then the lane's atom is tested against the 4 atoms of the warp's quad.
 __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int k_local) {
     pdl_launch_dependents();
     pdl_wait();
@@ -223,27 +266,22 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
             const int x = cx + nb % 3 - 1, y = cy + (nb / 3) % 3 - 1, z = cz + nb / 9 - 1;
             if (x < 0 || x >= g.G || y < 0 || y >= g.G || z < 0 || z >= g.G) continue;
             const int c2 = g.off + (z * g.G + y) * g.G + x;
-            const int q0 = d.cell_base[c2] >> 2, nq = (min(d.cell_count[c2], kCellCap) + 3) >> 2;
-            for (int t0 = 0; t0 < nq; t0 += 32) {
+            const int s0 = d.cell_base[c2], ns2 = (min(d.cell_count[c2], kCellCap) + 3) & ~3;
+            for (int t0 = 0; t0 < ns2; t0 += 32) {
                 bool in = false;
-                const int J = q0 + t0 + lane;
-                if (t0 + lane < nq && J != Q) {  // the quad's own pairs are summed apart from its list
+                const int sj = s0 + t0 + lane, J = sj >> 2;
+                if (t0 + lane < ns2 && J != Q) {  // the quad's own pairs are summed apart from its list
                     const float4 l2 = d.q_box[2 * J], h2 = d.q_box[2 * J + 1];
                     const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
                     const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
                     const float ez = fmaxf(0.f, fmaxf(l2.z - hi.z, lo.z - h2.z));
-                    if (ex * ex + ey * ey + ez * ez < rl2) {  // boxes in reach: is some atom pair?
-                        const float4 CJ = d.q_ref[J];
-                        const float Dx = CI.x - CJ.x, Dy = CI.y - CJ.y, Dz = CI.z - CJ.z;
+                    if (ex * ex + ey * ey + ez * ez < rl2) {  // boxes in reach: is the atom?
+                        const float4 CJ = d.q_ref[J], pj = vp[sj];  // an empty slot is far from all
+                        const float px = pj.x - (CI.x - CJ.x), py = pj.y - (CI.y - CJ.y), pz = pj.z - (CI.z - CJ.z);
     #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float4 pj = vp[4 * J + u];
-                            const float px = pj.x - Dx, py = pj.y - Dy, pz = pj.z - Dz;
-    #pragma unroll
-                            for (int a = 0; a < 4; ++a) {
-                                const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
-                                in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
-                            }
+                        for (int a = 0; a < 4; ++a) {
+                            const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
+                            in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
                         }
                     }
                 }
@@ -251,41 +289,50 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
                 const int pos = n + __popc(b & ((1u << lane) - 1u));
                 if (in) {
                     if (pos < kQMax)
-                        out[pos] = J;
+                        out[pos] = sj;
                     else
                         overflow = true;
                 }
                 n += __popc(b);
             }
         }
-        // pad to a whole number of 16-entry iterations of the passes with the padding quad
-        for (int k = min(n, kQMax) + lane; k < min((n + 15) & ~15, kQMax); k += 32) out[k] = d.nqmax;
         if (lane == 0) d.q_count[Q] = min(n, kQMax);
         if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(d.status, 4);
     }
 }
 
 // ---------------------------------------------------------------- passes
-// Atom q of listed quad J as an offset from the warp's quad reference point (the padding quad's atoms
-// land far from every atom and every empty slot).
-__device__ __forceinline__ float4 q_neighbour(const Dev& d, const float4* vp, int J, int q, const float4& CI) {
-    const float4 pj = vp[4 * J + q];
-    const float4 CJ = d.q_ref[J];
+// A pass CTA takes 8 quads (32 slots) with kQLanes lanes per quad: lane seg of a quad's group takes
+// list entries seg, seg + kQLanes, ... and pairs each with the 4 atoms of the quad, kept in registers.
+// Then warp 0 finishes the 32 atoms with one lane each, so the FP64 per-atom work runs on full warps.
+constexpr int kQLanes = 16;
+constexpr int kQCta = 8;
+constexpr int kQPassThreads = kQCta * kQLanes;
+constexpr int kQPassMinCtas = 26 * 32 / kQPassThreads;  // resident CTAs per SM for >= 26 warps (the register cap)
+
+// A listed atom pj of the quad with reference point CJ as an offset from the reference point CI of
+// the lane's quad (the padding quad's slots land far from every atom and every empty slot).
+__device__ __forceinline__ float4 q_shift(const float4& pj, const float4& CJ, const float4& CI) {
     return make_float4(pj.x - (CI.x - CJ.x), pj.y - (CI.y - CJ.y), pj.z - (CI.z - CJ.z), pj.w);
 }
-// List entry k of a list padded to n16 entries (the padding quad past the end).
-__device__ __forceinline__ int q_entry(const Dev& d, const int* L, int k, int n16) { return k < n16 ? L[k] : d.nqmax; }
-// Lanes 0..3: atom (lane) of the warp's own quad, to be paired with its other three atoms before the
-// list loop; the other lanes: far away.
-__device__ __forceinline__ float4 q_self(const float4 oi[4], int lane) {
+// Entry k of a list of n entries; past its end, a slot of the padding quad.
+__device__ __forceinline__ int q_entry(const Dev& d, const int* L, int k, int n) { return k < n ? L[k] : 4 * d.nqmax; }
+// Lanes 0..3 of a quad's group: atom seg of the quad, to be paired with its other three atoms before
+// the list loop; the other lanes: far away.
+__device__ __forceinline__ float4 q_self(const float4 oi[4], int seg) {
     float4 p = make_float4(-kFar, -kFar, -kFar, 0.f);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
-        if (lane == a) p = oi[a];
+        if (seg == a) p = oi[a];
     return p;
 }
+// Loop length of a warp: the longest list of its quads, rounded up to whole iterations (two entries per lane).
+__device__ __forceinline__ int q_warp_len(int n) {
+    const int m = __reduce_max_sync(0xffffffffu, n);
+    return (m + 2 * kQLanes - 1) & ~(2 * kQLanes - 1);
+}
 
-// The 4 atoms of this warp's quad (far away for a warp past the last quad).
+// The 4 atoms of a quad (far away past the last quad) and the length of its list.
 __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int nq, float4 oi[4], float4& CI) {
     if (Q >= nq) {
 #pragma unroll
@@ -299,10 +346,8 @@ __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int 
     return d.q_count[Q];
 }
 
-// Each CTA takes 8 quads (32 slots). The warps sum their quads' pairs; then warp 0 finishes all 32
-// atoms with one lane each, so the FP64 per-atom work runs on full warps.
 template <int SPECIAL, int SHIFT>
-__global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const Dev d, int obs, int k_local) {
+__global__ void __launch_bounds__(kQPassThreads, kQPassMinCtas) k_q_density(const Dev d, int obs, int k_local) {
     __shared__ f2sum s_sum[32];  // per slot: the density sum as double-float (FP64 only in warp 0's finish)
     __shared__ int s_nin[32];
     __shared__ float4 s_own[32];
@@ -310,9 +355,9 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
     pdl_wait();
     // in an MD step: clear the displacement record the force pass fills for the next step
     if (k_local >= 0 && blockIdx.x == 0 && threadIdx.x == 0) d.vdmax[(*d.step_base + k_local + 1) & 1] = 0u;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 3;
-    const int nq = *d.q_n, Q = blockIdx.x * (kQThreads / 32) + w;
-    if (blockIdx.x * (kQThreads / 32) >= nq) return;  // the whole CTA is past the last quad
+    const int lane = threadIdx.x & 31, g = threadIdx.x / kQLanes, seg = threadIdx.x % kQLanes;
+    const int nq = *d.q_n, Q = blockIdx.x * kQCta + g;
+    if (blockIdx.x * kQCta >= nq) return;  // the whole CTA is past the last quad
     const float4* vp = reinterpret_cast<const float4*>(d.vhi);
     float4 oi[4], CI;
     const int n = q_own(d, vp, Q, nq, oi, CI);
@@ -336,19 +381,28 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
             tacc[A] += rpow(ir * ir, ir, mexp);                                 \
         }                                                                       \
     }
-    if (n > 0) {  // the quad's own pairs (lanes 0..3); r2 > 0 also drops two empty slots of one quad
-        const float4 p = q_self(oi, lane);
+    {  // the quad's own pairs (lanes 0..3 of the group); r2 > 0 also drops two empty slots of one quad
+        const float4 p = q_self(oi, seg);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) SCMD_Q_DENSITY_PAIR(p, a, && r2 > 0.f && a != lane)
+        for (int a = 0; a < 4; ++a) SCMD_Q_DENSITY_PAIR(p, a, && r2 > 0.f && a != seg)
     }
-    // two listed quads per lane and iteration; the list entries of the next iteration are loaded
-    // one iteration ahead; only the cutoff decides (no listed atom coincides with an own one)
-    const int n16 = (n + 15) & ~15;
-    int J0 = q_entry(d, L, lane >> 2, n16), J1 = q_entry(d, L, 8 + (lane >> 2), n16);
-    for (int k0 = 0; k0 < n16; k0 += 16) {
-        const float4 pp[2] = {q_neighbour(d, vp, J0, q, CI), q_neighbour(d, vp, J1, q, CI)};
-        J0 = q_entry(d, L, k0 + 16 + (lane >> 2), n16);
-        J1 = q_entry(d, L, k0 + 24 + (lane >> 2), n16);
+    // two listed atoms per lane and iteration; only the cutoff decides (no listed atom is one of the
+    // quad's own)
+    const int nw = q_warp_len(n);
+    // the atoms are gathered one iteration ahead of their use, their list entries two ahead (past a
+    // list's end: the padding quad)
+    int s0 = q_entry(d, L, seg, n), s1 = q_entry(d, L, kQLanes + seg, n);
+    float4 r0 = vp[s0], c0 = d.q_ref[s0 >> 2], r1 = vp[s1], c1 = d.q_ref[s1 >> 2];
+    s0 = q_entry(d, L, 2 * kQLanes + seg, n);
+    s1 = q_entry(d, L, 3 * kQLanes + seg, n);
+    for (int k0 = 0; k0 < nw; k0 += 2 * kQLanes) {
+        const float4 pp[2] = {q_shift(r0, c0, CI), q_shift(r1, c1, CI)};
+        r0 = vp[s0];
+        c0 = d.q_ref[s0 >> 2];
+        r1 = vp[s1];
+        c1 = d.q_ref[s1 >> 2];
+        s0 = q_entry(d, L, k0 + 4 * kQLanes + seg, n);
+        s1 = q_entry(d, L, k0 + 5 * kQLanes + seg, n);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 p = pp[h];
@@ -358,26 +412,26 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
     }
 #undef SCMD_Q_DENSITY_PAIR
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {  // a fixed butterfly over the warp: every lane gets the sums
+    for (int a = 0; a < 4; ++a) {  // a fixed butterfly over the quad's lanes: each of them gets the sums
         // double-float (TwoSum) on the FP32 pipe: an FP64 butterfly here held the 1/64-rate FP64 pipe for
         // ~1/3 of the pass. TwoSum is exact, so both lanes of a pair compute the same sum.
         f2sum v = {tacc[a], 0.f};
         int m = nin[a];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
+        for (int o = 1; o < kQLanes; o <<= 1) {
             const f2sum u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
             v = f2_add(v, u);
             if (SHIFT) m += __shfl_xor_sync(0xffffffffu, m, o);
         }
-        if (lane == a) {
-            s_sum[4 * w + a] = v;
-            if (SHIFT) s_nin[4 * w + a] = m;
-            s_own[4 * w + a] = oi[a];
+        if (seg == a) {
+            s_sum[4 * g + a] = v;
+            if (SHIFT) s_nin[4 * g + a] = m;
+            s_own[4 * g + a] = oi[a];
         }
     }
     __syncthreads();
-    if (w != 0 || blockIdx.x * (kQThreads / 32) + (lane >> 2) >= nq) return;
-    const int s = blockIdx.x * kQThreads / 8 + lane, i = d.vorder[s];
+    if (threadIdx.x >= 32 || blockIdx.x * kQCta + (lane >> 2) >= nq) return;
+    const int s = blockIdx.x * 4 * kQCta + lane, i = d.vorder[s];
     float4 pg = make_float4(kFar, kFar, kFar, 0.f);
     if (i >= 0) {
         const double t = (double)s_sum[lane].hi + (double)s_sum[lane].lo;
@@ -396,14 +450,14 @@ __global__ void __launch_bounds__(kQThreads, SHIFT ? 4 : 5) k_q_density(const De
 // mode 0: forces; 1: forces and per-atom pair energies; 2: MD step (second half kick, per-atom
 // observables if due, then the first half of the next step unless last or Berendsen).
 template <int SPECIAL, int ENERGY>
-__global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, int k_local, int last) {
+__global__ void __launch_bounds__(kQPassThreads, kQPassMinCtas) k_q_force(const Dev d, int mode, int k_local, int last) {
     __shared__ float s_f[3][32];
     __shared__ double s_e[ENERGY ? 32 : 1];
     pdl_launch_dependents();
     pdl_wait();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 3;
-    const int nq = *d.q_n, Q = blockIdx.x * (kQThreads / 32) + w;
-    if (blockIdx.x * (kQThreads / 32) >= nq) return;  // the whole CTA is past the last quad
+    const int lane = threadIdx.x & 31, g = threadIdx.x / kQLanes, seg = threadIdx.x % kQLanes;
+    const int nq = *d.q_n, Q = blockIdx.x * kQCta + g;
+    if (blockIdx.x * kQCta >= nq) return;  // the whole CTA is past the last quad
     const float4* vp = reinterpret_cast<const float4*>(d.vposg);
     float4 oi[4], CI;
     const int n = q_own(d, vp, Q, nq, oi, CI);
@@ -439,19 +493,28 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
             nin[A] += in;                                                       \
         }                                                                       \
     }
-    if (n > 0) {  // the quad's own pairs (lanes 0..3); r2 > 0 also drops two empty slots of one quad
-        const float4 p = q_self(oi, lane);
+    {  // the quad's own pairs (lanes 0..3 of the group); r2 > 0 also drops two empty slots of one quad
+        const float4 p = q_self(oi, seg);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) SCMD_Q_FORCE_PAIR(p, a, && r2 > 0.f && a != lane)
+        for (int a = 0; a < 4; ++a) SCMD_Q_FORCE_PAIR(p, a, && r2 > 0.f && a != seg)
     }
-    // two listed quads per lane and iteration; the list entries of the next iteration are loaded
-    // one iteration ahead; only the cutoff decides (no listed atom coincides with an own one)
-    const int n16 = (n + 15) & ~15;
-    int J0 = q_entry(d, L, lane >> 2, n16), J1 = q_entry(d, L, 8 + (lane >> 2), n16);
-    for (int k0 = 0; k0 < n16; k0 += 16) {
-        const float4 pp[2] = {q_neighbour(d, vp, J0, q, CI), q_neighbour(d, vp, J1, q, CI)};
-        J0 = q_entry(d, L, k0 + 16 + (lane >> 2), n16);
-        J1 = q_entry(d, L, k0 + 24 + (lane >> 2), n16);
+    // two listed atoms per lane and iteration; only the cutoff decides (no listed atom is one of the
+    // quad's own)
+    const int nw = q_warp_len(n);
+    // the atoms are gathered one iteration ahead of their use, their list entries two ahead (past a
+    // list's end: the padding quad)
+    int s0 = q_entry(d, L, seg, n), s1 = q_entry(d, L, kQLanes + seg, n);
+    float4 r0 = vp[s0], c0 = d.q_ref[s0 >> 2], r1 = vp[s1], c1 = d.q_ref[s1 >> 2];
+    s0 = q_entry(d, L, 2 * kQLanes + seg, n);
+    s1 = q_entry(d, L, 3 * kQLanes + seg, n);
+    for (int k0 = 0; k0 < nw; k0 += 2 * kQLanes) {
+        const float4 pp[2] = {q_shift(r0, c0, CI), q_shift(r1, c1, CI)};
+        r0 = vp[s0];
+        c0 = d.q_ref[s0 >> 2];
+        r1 = vp[s1];
+        c1 = d.q_ref[s1 >> 2];
+        s0 = q_entry(d, L, k0 + 4 * kQLanes + seg, n);
+        s1 = q_entry(d, L, k0 + 5 * kQLanes + seg, n);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 p = pp[h];
@@ -466,7 +529,7 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
         double e = ENERGY ? (double)se[a] : 0.0;
         int m = nin[a];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
+        for (int o = 1; o < kQLanes; o <<= 1) {  // a fixed butterfly over the quad's lanes
             x += __shfl_xor_sync(0xffffffffu, x, o);
             y += __shfl_xor_sync(0xffffffffu, y, o);
             z += __shfl_xor_sync(0xffffffffu, z, o);
@@ -475,18 +538,18 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
                 m += __shfl_xor_sync(0xffffffffu, m, o);
             }
         }
-        if (lane == a) {
-            s_f[0][4 * w + a] = x;
-            s_f[1][4 * w + a] = y;
-            s_f[2][4 * w + a] = z;
-            if (ENERGY) s_e[4 * w + a] = e - (d.pot.shift ? (double)m * d.pot.shn : 0.0);
+        if (seg == a) {
+            s_f[0][4 * g + a] = x;
+            s_f[1][4 * g + a] = y;
+            s_f[2][4 * g + a] = z;
+            if (ENERGY) s_e[4 * g + a] = e - (d.pot.shift ? (double)m * d.pot.shn : 0.0);
         }
     }
     __syncthreads();
-    if (w != 0) return;
+    if (threadIdx.x >= 32) return;
     // warp 0: one lane per slot of the CTA's 8 quads
-    const int sl = blockIdx.x * kQThreads / 8 + lane;
-    const int i = blockIdx.x * (kQThreads / 32) + (lane >> 2) < nq ? d.vorder[sl] : -1;
+    const int sl = blockIdx.x * 4 * kQCta + lane;
+    const int i = blockIdx.x * kQCta + (lane >> 2) < nq ? d.vorder[sl] : -1;
     const Run& r = *d.run;
     // in an MD step (not the chunk's last, not Berendsen) this kernel starts the next step, so it also
     // does the position kernel's work for it: the slot's offset and the displacement since the rebuild
@@ -542,16 +605,16 @@ __global__ void __launch_bounds__(kQThreads) k_q_force(const Dev d, int mode, in
     }
 }
 
-int q_pass_grid(const Dev& d) { return (d.nqmax + kQThreads / 32 - 1) / (kQThreads / 32); }
+int q_pass_grid(const Dev& d) { return (d.nqmax + kQCta - 1) / kQCta; }
 
 template <int SHIFT> cudaError_t q_density_s(const Dev& d, int obs, int k_local, cudaStream_t s) {
-    return d.pot.special ? launch_ex(k_q_density<1, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs, k_local)
-                         : launch_ex(k_q_density<0, SHIFT>, q_pass_grid(d), kQThreads, 0, 0, s, d, obs, k_local);
+    return d.pot.special ? launch_ex(k_q_density<1, SHIFT>, q_pass_grid(d), kQPassThreads, 0, 0, s, d, obs, k_local)
+                         : launch_ex(k_q_density<0, SHIFT>, q_pass_grid(d), kQPassThreads, 0, 0, s, d, obs, k_local);
 }
 
 template <int ENERGY> cudaError_t q_force_e(const Dev& d, int mode, int k, int last, cudaStream_t s) {
-    return d.pot.special ? launch_ex(k_q_force<1, ENERGY>, q_pass_grid(d), kQThreads, 0, 0, s, d, mode, k, last)
-                         : launch_ex(k_q_force<0, ENERGY>, q_pass_grid(d), kQThreads, 0, 0, s, d, mode, k, last);
+    return d.pot.special ? launch_ex(k_q_force<1, ENERGY>, q_pass_grid(d), kQPassThreads, 0, 0, s, d, mode, k, last)
+                         : launch_ex(k_q_force<0, ENERGY>, q_pass_grid(d), kQPassThreads, 0, 0, s, d, mode, k, last);
 }
 
 }  // namespace

@@ -158,7 +158,7 @@ def test_four_atoms_per_thread_density_on_uneven_batches(scmd, prec):
                           else np.zeros((1, 3)) for k, p in enumerate(parts)])
     ctx = make(scmd, sizes, pos, vel, prec=prec, path=scmd.MD_PATH_ALLPAIRS)
     ref = make(scmd, sizes, pos, vel, prec=prec, path=scmd.MD_PATH_ALLPAIRS)
-    for warps, cl in ((4, 1), (2, 3), (8, 2)):
+    for warps, cl in ((4, 1), (4, 3), (16, 5)):
         scmd.md_set_launch(ctx, 0, 4, warps, cl)
         E, F = scmd.md_energy_forces(ctx)
         rho = scmd.md_get_density(ctx)
