@@ -27,6 +27,7 @@
 // a resumed MIXED run agrees with an uninterrupted one to rounding, not bit for bit. Runs are
 // deterministic: slots follow the cell order and lists the fixed order of the 27 cells.
 #include <algorithm>
+#include <climits>
 
 #include "scmd_cells.cuh"
 
@@ -53,12 +54,13 @@ __device__ __forceinline__ int2 kd_segment(int r, int n, int lev) {
     }
     return make_int2(b, e);
 }
-// A coordinate as an integer of the same order (a total order, NaN included, so ranks stay distinct).
+// A coordinate as an integer of the same order (a total order, NaN included, so ranks stay distinct),
+// and back.
 __device__ __forceinline__ int ord_key(float v) {
     const int b = __float_as_int(v);
     return b >= 0 ? b : b ^ 0x7fffffff;
 }
-__device__ __forceinline__ float axis_of(const float4& p, int ax) { return ax == 0 ? p.x : (ax == 1 ? p.y : p.z); }
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
 // ---------------------------------------------------------------- every step
 __global__ void __launch_bounds__(kQThreads) k_q_pos(const Dev d, int k_local) {
@@ -130,10 +132,10 @@ __global__ void __launch_bounds__(1024) k_q_scan(const Dev d, int cond, int k_lo
 // One CTA per cell: order its atoms into quads by recursive bisection, place them, and set up each of
 // its quads.
 __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond, int k_local) {
-    __shared__ float4 s_p[kCellCap];
-    __shared__ int s_atom[kCellCap];
-    __shared__ int s_ord[kCellCap];  // place -> entry of s_p / s_atom
-    __shared__ int s_tmp[kCellCap];
+    // per place, in the current order (two buffers): the 3 coordinates as order keys and the atom
+    __shared__ int s_key[2][3][kCellCap];
+    __shared__ int s_at[2][kCellCap];
+    __shared__ int s_lo[kCellCap / 4][3], s_hi[kCellCap / 4][3];  // per segment (by its first quad)
     __shared__ int s_sorted[kCellCap];
     pdl_launch_dependents();
     pdl_wait();
@@ -144,49 +146,56 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
         if (n == 0) continue;
         const int cl = d.cell_cl[c];
         const float4* cp = reinterpret_cast<const float4*>(d.cposg);  // the binned order (no cell sort)
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            s_p[k] = cp[(size_t)c * kCellCap + k];
-            s_atom[k] = d.cell_atoms[(size_t)c * kCellCap + k];
-        }
-        __syncthreads();
+        const int* ca = d.cell_atoms + (size_t)c * kCellCap;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {  // start: atom-index order
-            const int a = s_atom[k];
+            const int a = ca[k];
             int r = 0;
-            for (int m = 0; m < n; ++m) r += s_atom[m] < a;
-            s_ord[r] = k;
+            for (int m = 0; m < n; ++m) r += ca[m] < a;
+            const float4 p = cp[(size_t)c * kCellCap + k];
+            s_key[0][0][r] = ord_key(p.x);
+            s_key[0][1][r] = ord_key(p.y);
+            s_key[0][2][r] = ord_key(p.z);
+            s_at[0][r] = a;
         }
-        __syncthreads();
         const int nq = (n + 3) >> 2;
-        for (int lev = 0; (1 << lev) < nq; ++lev) {
-            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        int cur = 0;
+        for (int lev = 0; (1 << lev) < nq; ++lev, cur ^= 1) {
+            __syncthreads();
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {  // the segments' extents (in key order)
                 const int2 sg = kd_segment(r, n, lev);
-                const int k = s_ord[r];
-                int to = r;
-                if (sg.y - sg.x > 4) {
-                    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-                    for (int m = sg.x; m < sg.y; ++m) {
-                        const float4 p = s_p[s_ord[m]];
-                        lo[0] = fminf(lo[0], p.x), hi[0] = fmaxf(hi[0], p.x);
-                        lo[1] = fminf(lo[1], p.y), hi[1] = fmaxf(hi[1], p.y);
-                        lo[2] = fminf(lo[2], p.z), hi[2] = fmaxf(hi[2], p.z);
-                    }
-                    const float ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-                    const int ax = (ex >= ey && ex >= ez) ? 0 : (ey >= ez ? 1 : 2);
-                    const int v = ord_key(axis_of(s_p[k], ax)), a = s_atom[k];
-                    int cnt = 0;
-                    for (int m = sg.x; m < sg.y; ++m) {
-                        const int km = s_ord[m], vm = ord_key(axis_of(s_p[km], ax));
-                        cnt += vm < v || (vm == v && s_atom[km] < a);
-                    }
-                    to = sg.x + cnt;
-                }
-                s_tmp[to] = k;
+                if (r == sg.x)
+                    for (int q = 0; q < 3; ++q) s_lo[r >> 2][q] = INT_MAX, s_hi[r >> 2][q] = INT_MIN;
             }
             __syncthreads();
-            for (int r = threadIdx.x; r < n; r += blockDim.x) s_ord[r] = s_tmp[r];
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                const int2 sg = kd_segment(r, n, lev);
+                if (sg.y - sg.x > 4)
+                    for (int q = 0; q < 3; ++q) {
+                        atomicMin(&s_lo[sg.x >> 2][q], s_key[cur][q][r]);
+                        atomicMax(&s_hi[sg.x >> 2][q], s_key[cur][q][r]);
+                    }
+            }
             __syncthreads();
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                const int2 sg = kd_segment(r, n, lev);
+                int to = r;
+                if (sg.y - sg.x > 4) {
+                    float w[3];
+                    for (int q = 0; q < 3; ++q) w[q] = key_float(s_hi[sg.x >> 2][q]) - key_float(s_lo[sg.x >> 2][q]);
+                    const int ax = (w[0] >= w[1] && w[0] >= w[2]) ? 0 : (w[1] >= w[2] ? 1 : 2);
+                    const int* kk = s_key[cur][ax];
+                    const int* at = s_at[cur];
+                    const int v = kk[r], a = at[r];
+                    int cnt = 0;
+                    for (int m = sg.x; m < sg.y; ++m) cnt += kk[m] < v || (kk[m] == v && at[m] < a);
+                    to = sg.x + cnt;
+                }
+                for (int q = 0; q < 3; ++q) s_key[cur ^ 1][q][to] = s_key[cur][q][r];
+                s_at[cur ^ 1][to] = s_at[cur][r];
+            }
         }
-        for (int r = threadIdx.x; r < n; r += blockDim.x) s_sorted[r] = s_atom[s_ord[r]];
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) s_sorted[r] = s_at[cur][r];
         __syncthreads();
         const int base = d.cell_base[c], n4 = (n + 3) & ~3, ns = d.nslot, np = d.npad;
         for (int r = threadIdx.x; r < n4; r += blockDim.x) {
@@ -241,13 +250,17 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
 
 // One warp per quad: the atoms of the 27 cells around its cell (fixed order; slot order within a
 // cell) closer than rcut + skin to one of its atoms at the rebuild, its own atoms apart, appended in
-// that order. One lane per candidate slot: the bounding boxes of the quads screen the candidates,
-// then the lane's atom is tested against the 4 atoms of the warp's quad.
+// that order. One lane per candidate quad tests the bounding boxes; the quads whose boxes are in reach
+// queue up (in order) in a per-warp buffer, and 8 at a time, one lane per atom, their atoms are tested
+// against the 4 atoms of the warp's quad. So the exact tests run on full warps.
 __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int k_local) {
+    __shared__ int s_fifo[kQThreads / 32][64];  // quads whose boxes are in reach, not yet tested
     pdl_launch_dependents();
     pdl_wait();
     if (cond && !vlist_rebuild_due(d, k_local)) return;
-    const int lane = threadIdx.x & 31, nq = *d.q_n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nq = *d.q_n;
+    const unsigned lt = (1u << lane) - 1u;
+    int* fifo = s_fifo[w];
     for (int Q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; Q < nq; Q += (gridDim.x * blockDim.x) >> 5) {
         const int c = d.q_cell[Q];
         const CellGrid g = d.grid[d.cell_cl[c]];
@@ -260,44 +273,63 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
         for (int a = 0; a < 4; ++a) oi[a] = vp[4 * Q + a];
         const float4 CI = d.q_ref[Q];
         int* out = d.q_list + (size_t)Q * kQMax;
-        int n = 0;
+        int n = 0, nf = 0;
         bool overflow = false;
+        // the atoms of the first m (<= 8) queued quads: lane 4e + u takes atom u of quad e
+        auto drain = [&](int m) {
+            const int e = lane >> 2, sj = e < m ? 4 * fifo[e] + (lane & 3) : 0;
+            bool in = false;
+            if (e < m) {
+                const float4 CJ = d.q_ref[sj >> 2], pj = vp[sj];  // an empty slot is far from all
+                const float px = pj.x - (CI.x - CJ.x), py = pj.y - (CI.y - CJ.y), pz = pj.z - (CI.z - CJ.z);
+    #pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
+                    in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+                }
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, in);
+            const int pos = n + __popc(b & lt);
+            if (in) {
+                if (pos < kQMax)
+                    out[pos] = sj;
+                else
+                    overflow = true;
+            }
+            n += __popc(b);
+            // the queue moves up by 8 (nf <= 39): every lane reads before any lane writes
+            const int moved = lane + 8 < nf ? fifo[lane + 8] : 0;
+            __syncwarp();
+            if (lane + 8 < nf) fifo[lane] = moved;
+            __syncwarp();
+            nf = max(nf - 8, 0);
+        };
         for (int nb = 0; nb < 27; ++nb) {
             const int x = cx + nb % 3 - 1, y = cy + (nb / 3) % 3 - 1, z = cz + nb / 9 - 1;
             if (x < 0 || x >= g.G || y < 0 || y >= g.G || z < 0 || z >= g.G) continue;
             const int c2 = g.off + (z * g.G + y) * g.G + x;
-            const int s0 = d.cell_base[c2], ns2 = (min(d.cell_count[c2], kCellCap) + 3) & ~3;
-            for (int t0 = 0; t0 < ns2; t0 += 32) {
-                bool in = false;
-                const int sj = s0 + t0 + lane, J = sj >> 2;
-                if (t0 + lane < ns2 && J != Q) {  // the quad's own pairs are summed apart from its list
+            const int q0 = d.cell_base[c2] >> 2, nq2 = (min(d.cell_count[c2], kCellCap) + 3) >> 2;
+            for (int t0 = 0; t0 < nq2; t0 += 32) {
+                const int J = q0 + t0 + lane;
+                bool near = false;
+                if (t0 + lane < nq2 && J != Q) {  // the quad's own pairs are summed apart from its list
                     const float4 l2 = d.q_box[2 * J], h2 = d.q_box[2 * J + 1];
                     const float ex = fmaxf(0.f, fmaxf(l2.x - hi.x, lo.x - h2.x));
                     const float ey = fmaxf(0.f, fmaxf(l2.y - hi.y, lo.y - h2.y));
                     const float ez = fmaxf(0.f, fmaxf(l2.z - hi.z, lo.z - h2.z));
-                    if (ex * ex + ey * ey + ez * ez < rl2) {  // boxes in reach: is the atom?
-                        const float4 CJ = d.q_ref[J], pj = vp[sj];  // an empty slot is far from all
-                        const float px = pj.x - (CI.x - CJ.x), py = pj.y - (CI.y - CJ.y), pz = pj.z - (CI.z - CJ.z);
-    #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            const float dx = oi[a].x - px, dy = oi[a].y - py, dz = oi[a].z - pz;
-                            in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
-                        }
-                    }
+                    near = ex * ex + ey * ey + ez * ez < rl2;
                 }
-                const unsigned b = __ballot_sync(0xffffffffu, in);
-                const int pos = n + __popc(b & ((1u << lane) - 1u));
-                if (in) {
-                    if (pos < kQMax)
-                        out[pos] = sj;
-                    else
-                        overflow = true;
-                }
-                n += __popc(b);
+                const unsigned b = __ballot_sync(0xffffffffu, near);
+                if (near) fifo[nf + __popc(b & lt)] = J;
+                nf += __popc(b);
+                __syncwarp();
+                while (nf >= 8) drain(8);
             }
         }
+        if (nf > 0) drain(nf);
         if (lane == 0) d.q_count[Q] = min(n, kQMax);
         if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(d.status, 4);
+        __syncwarp();  // the next quad reuses the queue
     }
 }
 
