@@ -147,10 +147,13 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
         const int cl = d.cell_cl[c];
         const float4* cp = reinterpret_cast<const float4*>(d.cposg);  // the binned order (no cell sort)
         const int* ca = d.cell_atoms + (size_t)c * kCellCap;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) s_sorted[k] = ca[k];  // (binned order)
+        __syncthreads();
         for (int k = threadIdx.x; k < n; k += blockDim.x) {  // start: atom-index order
-            const int a = ca[k];
+            const int a = s_sorted[k];
             int r = 0;
-            for (int m = 0; m < n; ++m) r += ca[m] < a;
+#pragma unroll 8
+            for (int m = 0; m < n; ++m) r += s_sorted[m] < a;
             const float4 p = cp[(size_t)c * kCellCap + k];
             s_key[0][0][r] = ord_key(p.x);
             s_key[0][1][r] = ord_key(p.y);
@@ -167,13 +170,23 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
                     for (int q = 0; q < 3; ++q) s_lo[r >> 2][q] = INT_MAX, s_hi[r >> 2][q] = INT_MIN;
             }
             __syncthreads();
-            for (int r = threadIdx.x; r < n; r += blockDim.x) {
-                const int2 sg = kd_segment(r, n, lev);
-                if (sg.y - sg.x > 4)
+            for (int r0 = 0; r0 < n; r0 += blockDim.x) {  // (whole warps: the warp reductions below)
+                const int r = r0 + threadIdx.x;
+                const int2 sg = kd_segment(min(r, n - 1), n, lev);
+                const bool act = r < n && sg.y - sg.x > 4;
+                const int lead = __shfl_sync(0xffffffffu, sg.x, 0);
+                if (__all_sync(0xffffffffu, act && sg.x == lead)) {  // one segment: reduce, then one atomic
+                    for (int q = 0; q < 3; ++q) {
+                        const int lo = __reduce_min_sync(0xffffffffu, s_key[cur][q][r]);
+                        const int hi = __reduce_max_sync(0xffffffffu, s_key[cur][q][r]);
+                        if ((threadIdx.x & 31) == 0) atomicMin(&s_lo[lead >> 2][q], lo), atomicMax(&s_hi[lead >> 2][q], hi);
+                    }
+                } else if (act) {
                     for (int q = 0; q < 3; ++q) {
                         atomicMin(&s_lo[sg.x >> 2][q], s_key[cur][q][r]);
                         atomicMax(&s_hi[sg.x >> 2][q], s_key[cur][q][r]);
                     }
+                }
             }
             __syncthreads();
             for (int r = threadIdx.x; r < n; r += blockDim.x) {
@@ -187,6 +200,7 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
                     const int* at = s_at[cur];
                     const int v = kk[r], a = at[r];
                     int cnt = 0;
+#pragma unroll 8
                     for (int m = sg.x; m < sg.y; ++m) cnt += kk[m] < v || (kk[m] == v && at[m] < a);
                     to = sg.x + cnt;
                 }
