@@ -319,7 +319,7 @@ md_status md_fp32_peak(int32_t reps, double* measured_ops_per_s, double* derived
 
 /* Number of GPU kernels issued per md_step step (all pairs: 2, or 4 with
  * MD_PATH_ALLPAIRS_HALF, cells: 5,
- * neighbour lists: 7 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
+ * neighbour lists: 6 in MIXED, 13 in FP64, plus one Berendsen kernel, two with
  * cells or lists, and the observable kernels of recorded steps) and per graph
  * replay overhead (launches per chunk), for launch accounting. */
 md_status md_launch_counts(const md_ctx* ctx, int32_t* per_step, int32_t* per_chunk);

@@ -429,7 +429,7 @@ md_status enqueue_chunk(md_ctx* c, int M, int64_t s0, int kind) {
         if (c->path == 2) {
             // MIXED lists: within a chunk (not Berendsen) the previous force pass did the position kernel's work
             if (c->nqmax == 0 || k == 0 || kind == MD_BERENDSEN) CK(c, launch_v_pos(d, k, c->stream));
-            CK(c, launch_cell_build(d, c->stream, 1, k));
+            CK(c, launch_cell_build(d, c->stream, 1, k, c->nqmax == 0));  // MIXED: the counts are already clear
             CK(c, launch_v_rebuild(d, 1, k, c->stream));
             CK(c, launch_v_density(d, obs ? 1 : 0, c->stream, k));
             CK(c, launch_v_force(d, 2, k, flags, c->stream));
@@ -891,14 +891,14 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
         if (quads) {
             const size_t nq = (size_t)c->nqmax;
             CKC(dmalloc(c, &c->d_q_n, sizeof(int32_t)));
-            CKC(dmalloc(c, &c->d_cell_base, sizeof(int32_t) * c->n_cells));
+            CKC(dmalloc(c, &c->d_cell_base, sizeof(int32_t) * (c->n_cells + 1)));
             CKC(dmalloc(c, &c->d_q_ref, sizeof(float4) * (nq + 1)));
             CKC(dmalloc(c, &c->d_q_box, sizeof(float4) * 2 * nq));
             CKC(dmalloc(c, &c->d_q_cell, sizeof(int32_t) * nq));
             CKC(dmalloc(c, &c->d_q_list, sizeof(int32_t) * kQMax * nq));
             CKC(dmalloc(c, &c->d_q_count, sizeof(int32_t) * nq));
             CKC(cudaMemsetAsync(c->d_q_n, 0, sizeof(int32_t), c->stream));
-            CKC(cudaMemsetAsync(c->d_cell_base, 0, sizeof(int32_t) * c->n_cells, c->stream));
+            CKC(cudaMemsetAsync(c->d_cell_base, 0, sizeof(int32_t) * (c->n_cells + 1), c->stream));
             CKC(cudaMemsetAsync(c->d_q_count, 0, sizeof(int32_t) * nq, c->stream));
             {  // the padding quad of the lists: reference point 0, its 4 slots far from every atom and every
                // empty slot (g = 0)
@@ -1563,10 +1563,10 @@ md_status md_get_path(const md_ctx* c, int32_t* path) {
 
 md_status md_launch_counts(const md_ctx* c, int32_t* per_step, int32_t* per_chunk) {
     if (!c) return MD_ERR_INVALID;
-    // lists: positions, cell build (FP64 3: clear, bin, sort; MIXED 2: clear, bin), list build (MIXED scan,
+    // lists: positions, cell build (FP64 3: clear, bin, sort; MIXED 1: bin, in a step), list build (MIXED scan,
     // order, list; FP64 build, sort, reverse sort, commit), passes (MIXED 2; FP64 compaction, 2 passes, 2 gathers)
     // (MIXED: the position kernel runs once per chunk, and every step with Berendsen)
-    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 7 : 13) : (c->path == 1 ? 5 : (c->half ? 4 : 2));
+    if (per_step) *per_step = c->path == 2 ? (c->nqmax > 0 ? 6 : 13) : (c->path == 1 ? 5 : (c->half ? 4 : 2));
     if (per_chunk) *per_chunk = c->path == 2 && c->nqmax > 0 ? 4 : 3;
     return MD_OK;
 }

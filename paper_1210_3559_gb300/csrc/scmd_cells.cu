@@ -391,8 +391,8 @@ __global__ void k_cell_ke(const Dev d) {
 }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond, int k_local) {
-    cudaError_t e = launch_ex(k_cell_clear, (d.n_cells + 255) / 256, 256, 0, 0, s, d, cond, k_local);
+cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond, int k_local, bool clear) {
+    cudaError_t e = clear ? launch_ex(k_cell_clear, (d.n_cells + 255) / 256, 256, 0, 0, s, d, cond, k_local) : cudaSuccess;
     if (e != cudaSuccess) return e;
     e = d.prec == 1 ? launch_ex(k_cell_bin<1>, (d.npad + 255) / 256, 256, 0, 0, s, d, cond, k_local)
                     : launch_ex(k_cell_bin<0>, (d.npad + 255) / 256, 256, 0, 0, s, d, cond, k_local);

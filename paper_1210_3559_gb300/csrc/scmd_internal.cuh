@@ -174,7 +174,7 @@ struct Dev {
     // the cell; cells padded to whole quads with empty slots, vorder = -1). nslot = 4 * nqmax there.
     int32_t nqmax;       // quads allocated
     int32_t* q_n;        // [1] quads in use since the last rebuild
-    int32_t* cell_base;  // [n_cells] first slot of each cell
+    int32_t* cell_base;  // [n_cells + 1] first slot of each cell, then the end of the last
     float4* q_ref;       // [nqmax] reference point of each quad relative to the origin (a multiple of 2^-12 A)
     float4* q_box;       // [nqmax][2] bounding box (lo, hi) of its atoms at the rebuild, relative to the origin
     int32_t* q_cell;     // [nqmax] cell of each quad
@@ -216,7 +216,8 @@ cudaError_t launch_normals(uint64_t seed, uint32_t cluster, int64_t step, int n,
 size_t pass_smem_bytes(int prec, Shape sh, int which);  // which: 0 density pass, 1 force pass
 // Cell-list path (defined in scmd_cells.cu).
 // clear, bin, sort; cond != 0: only when a neighbour-list rebuild is due at local step k_local
-cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond = 0, int k_local = 0);
+// clear (unless clear == false: MIXED lists inside a step, where k_q_order left the counts clear), bin, sort
+cudaError_t launch_cell_build(const Dev& d, cudaStream_t s, int cond = 0, int k_local = 0, bool clear = true);
 cudaError_t launch_cell_density(const Dev& d, int obs, cudaStream_t s);
 cudaError_t launch_cell_force(const Dev& d, int mode, int k_local, int flags, cudaStream_t s);
 // Observable partials of every 32-atom group from the per-atom data (from_state: read x, v;

@@ -10,7 +10,8 @@
 //                displacement since the last rebuild (at a chunk's first step and with Berendsen;
 //                otherwise the previous step's force pass, which moved the atoms, did this);
 //   rebuild, when that displacement exceeds the trigger (the kernels exit at once otherwise):
-//     the cell build of the cell-list path (clear, bin; the ranking below makes its sort needless), then
+//     the binning of the cell-list path (its sort is needless: the ranking below works from the binned
+//                  order; its clearing too: k_q_order clears each cell's count once it has read it), then
 //     k_q_scan   : the first slot of every cell (cells padded to whole quads), and the quad count;
 //     k_q_order  : one CTA per cell: its atoms bisected into quads and placed in slots; per quad the
 //                  reference point, the bounding box and the offsets;
@@ -126,7 +127,10 @@ __global__ void __launch_bounds__(1024) k_q_scan(const Dev d, int cond, int k_lo
         if (threadIdx.x == 0) s_carry += s_warp[(blockDim.x >> 5) - 1];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *d.q_n = s_carry >> 2;
+    if (threadIdx.x == 0) {
+        *d.q_n = s_carry >> 2;
+        d.cell_base[d.n_cells] = s_carry;  // the end of the last cell
+    }
 }
 
 // One CTA per cell: order its atoms into quads by recursive bisection, place them, and set up each of
@@ -149,6 +153,9 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
         const int* ca = d.cell_atoms + (size_t)c * kCellCap;
         for (int k = threadIdx.x; k < n; k += blockDim.x) s_sorted[k] = ca[k];  // (binned order)
         __syncthreads();
+        // every thread has read the count: clear it for the next rebuild's binning (no clearing kernel;
+        // the list kernel takes a cell's slot count from cell_base)
+        if (threadIdx.x == 0) d.cell_count[c] = 0;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {  // start: atom-index order
             const int a = s_sorted[k];
             int r = 0;
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(kQThreads) k_q_list(const Dev d, int cond, int
             const int x = cx + nb % 3 - 1, y = cy + (nb / 3) % 3 - 1, z = cz + nb / 9 - 1;
             if (x < 0 || x >= g.G || y < 0 || y >= g.G || z < 0 || z >= g.G) continue;
             const int c2 = g.off + (z * g.G + y) * g.G + x;
-            const int q0 = d.cell_base[c2] >> 2, nq2 = (min(d.cell_count[c2], kCellCap) + 3) >> 2;
+            const int q0 = d.cell_base[c2] >> 2, nq2 = (d.cell_base[c2 + 1] >> 2) - q0;
             for (int t0 = 0; t0 < nq2; t0 += 32) {
                 const int J = q0 + t0 + lane;
                 bool near = false;

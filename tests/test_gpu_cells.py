@@ -112,9 +112,9 @@ def test_cells_full_size_parity(scmd, prec):
     vel = inputs.maxwell_boltzmann(pos, inputs.masses(50000), 300.0, seed=3)
     ctx = make(scmd, [50000], pos, vel, prec=prec, rcut=RC, path=AUTO)
     assert scmd.md_get_path(ctx) == 3
-    # cell build (MIXED 2, FP64 3), list build (MIXED 3, FP64 4), passes (MIXED 2, FP64 compaction + 2 + 2 gathers),
+    # cell build (MIXED 1: binning, FP64 3), list build (MIXED 3, FP64 4), passes (MIXED 2, FP64 compaction + 2 + 2 gathers),
     # and in FP64 the position kernel (MIXED: once per chunk)
-    assert scmd.md_launch_counts(ctx)[0] == (7 if prec == MIXED else 13)
+    assert scmd.md_launch_counts(ctx)[0] == (6 if prec == MIXED else 13)
     ctx = make(scmd, [50000], pos, vel, prec=prec, rcut=RC, path=CELLS)
     assert scmd.md_get_path(ctx) == CELLS
     assert scmd.md_launch_counts(ctx)[0] == 5  # clear, bin, sort, density, force
