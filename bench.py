@@ -12,7 +12,7 @@ events.
 
 Other configs (--config): ni2000 (one cluster, Langevin cooling 2000 -> 300 K over 2e5 steps),
 ni6000, ni20000 (all pairs, MIXED), ni50000 (rcut = 8.8 A on the neighbour lists, MIXED: lists of
-atom quads), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one context).
+atoms per atom quad), ni147 (FP64 NVE), ni147x64 (64 replicas of it in one context).
 
 value  : atom-timesteps/s over all ranks (sum of atoms x MD steps / max rank time).
 e2e    : the same metric through the C ABI with host buffers every iteration
@@ -560,7 +560,7 @@ def main():
                          "frac": achieved / peak_ops,
                          "traffic": force_traffic(args.config, path_name) if prec == "mixed" else None,
                          "kernel": {"cells": "k_cell_force (force pass, cell list)",
-                                    "neighbour lists": "k_q_force (force pass, quad lists)" if prec == "mixed"
+                                    "neighbour lists": "k_q_force (force pass, atom lists per quad)" if prec == "mixed"
                                     else "k_v_force (force pass, neighbour lists)"}.get(
                                         path_name, "k_force (force pass)"),
                          "ms_per_launch": ms_f,

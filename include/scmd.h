@@ -79,8 +79,8 @@ typedef enum {
     MD_PATH_CELLS = 2,    /* uniform cell grid of side >= rcut_A; requires rcut_A > 0    */
     MD_PATH_VERLET = 3,   /* neighbour lists of rcut_A + 1 A built on the cell grid, rebuilt
                              when an atom has moved 0.5 A; requires rcut_A > 0. FP64: per
-                             atom, forces independent of the rebuild times. MIXED: per quad
-                             of 4 nearby atoms, summed in list order, so a resumed run
+                             atom, forces independent of the rebuild times. MIXED: the atoms
+                             in reach of each quad of 4 nearby atoms, summed in list order, so a resumed run
                              (md_set_state) agrees to rounding rather than bit for bit      */
     MD_PATH_ALLPAIRS_HALF = 4 /* FP64 only: all pairs, each unordered pair evaluated once and
                              added to both atoms (Newton's third law), in work units of 32 x 16
