@@ -880,7 +880,9 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
         // MIXED: 4 more slots for the padding quad of the lists (index nqmax), far from every atom
         const size_t ns_alloc = quads ? ns + 4 : ns;
         CKC(dmalloc(c, &c->d_vhi, (size_t)vec4_size(c) * ns_alloc));
-        CKC(dmalloc(c, &c->d_vposg, (size_t)vec4_size(c) * ns_alloc));
+        // MIXED: the force pass reads a 32-byte record per slot, the offset and g (float4) then its quad's
+        // reference point (float4)
+        CKC(dmalloc(c, &c->d_vposg, (quads ? 2 * sizeof(float4) : (size_t)vec4_size(c)) * ns_alloc));
         CKC(dmalloc(c, &c->d_vxref, sizeof(double) * 3 * ns));
         CKC(dmalloc(c, &c->d_vdmax, sizeof(uint32_t) * 2));
         CKC(cudaMemsetAsync(c->d_vdmax, 0, sizeof(uint32_t) * 2, c->stream));
@@ -904,10 +906,12 @@ md_status create_impl(const md_config* cfg, int32_t n_clusters, const int32_t* s
                // empty slot (g = 0)
                 constexpr float F = -kQuadFar;
                 static const float far4[4][4] = {{F, F, F, 0.f}, {F, F, F, 0.f}, {F, F, F, 0.f}, {F, F, F, 0.f}};
+                static const float far8[8][4] = {{F, F, F, 0.f}, {0.f, 0.f, 0.f, 0.f}, {F, F, F, 0.f}, {0.f, 0.f, 0.f, 0.f},
+                                                 {F, F, F, 0.f}, {0.f, 0.f, 0.f, 0.f}, {F, F, F, 0.f}, {0.f, 0.f, 0.f, 0.f}};
                 CKC(cudaMemcpyAsync(static_cast<float4*>(c->d_vhi) + ns, far4, sizeof far4, cudaMemcpyHostToDevice,
                                     c->stream));
-                CKC(cudaMemcpyAsync(static_cast<float4*>(c->d_vposg) + ns, far4, sizeof far4, cudaMemcpyHostToDevice,
-                                    c->stream));
+                CKC(cudaMemcpyAsync(static_cast<float4*>(c->d_vposg) + 2 * ns, far8, sizeof far8,
+                                    cudaMemcpyHostToDevice, c->stream));
                 CKC(cudaMemsetAsync(c->d_q_ref + nq, 0, sizeof(float4), c->stream));
             }
         } else {

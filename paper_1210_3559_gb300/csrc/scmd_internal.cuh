@@ -167,7 +167,8 @@ struct Dev {
     int32_t* vslot;      // FP64: [1] slot counter of a rebuild
     void* vhi;           // [nslot] by slot: FP64 double4 (x, y, z, 0); MIXED float4 (offset from the quad's
                          // reference point, 0)
-    void* vposg;         // [nslot] (vhi.xyz, B6 rho^-1/2), written by the density pass
+    void* vposg;         // [nslot] (vhi.xyz, B6 rho^-1/2), written by the density pass; MIXED a 32-byte record:
+                         // that float4, then the quad's reference point (float4, written at the rebuild)
     double* vxref;       // [3][nslot] positions at the last rebuild
     uint32_t* vdmax;     // [2] largest squared displacement since the rebuild (float bits), by step parity
     // MIXED neighbour lists are lists of quads (4 consecutive slots of one cell, in Morton order within

@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond,
                     d.vxref[2 * ns + s] = d.x[2 * np + a];
                 }
                 reinterpret_cast<float4*>(d.vhi)[s] = p;
+                reinterpret_cast<float4*>(d.vposg)[2 * s + 1] = C;  // the force pass's record: its quad's reference point
             }
         }
     }
@@ -386,6 +387,8 @@ __device__ __forceinline__ int q_warp_len(int n) {
 }
 
 // The 4 atoms of a quad (far away past the last quad) and the length of its list.
+// REC: slots stored as 32-byte records (offset, then the quad's reference point: the force pass's array).
+template <int REC>
 __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int nq, float4 oi[4], float4& CI) {
     if (Q >= nq) {
 #pragma unroll
@@ -394,7 +397,7 @@ __device__ __forceinline__ int q_own(const Dev& d, const float4* vp, int Q, int 
         return 0;
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) oi[a] = vp[4 * Q + a];
+    for (int a = 0; a < 4; ++a) oi[a] = vp[(REC ? 2 : 1) * (4 * Q + a)];
     CI = d.q_ref[Q];
     return d.q_count[Q];
 }
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(kQPassThreads, kQPassMinCtas) k_q_density(cons
     if (blockIdx.x * kQCta >= nq) return;  // the whole CTA is past the last quad
     const float4* vp = reinterpret_cast<const float4*>(d.vhi);
     float4 oi[4], CI;
-    const int n = q_own(d, vp, Q, nq, oi, CI);
+    const int n = q_own<0>(d, vp, Q, nq, oi, CI);
     const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
     const float rc2 = d.pot.rcut2f;  // (FP32 constants from the host: a conversion would run on the FP64 pipe)
     const int mexp = d.pot.m;
@@ -497,7 +500,7 @@ __global__ void __launch_bounds__(kQPassThreads, kQPassMinCtas) k_q_density(cons
         pg = make_float4(me.x, me.y, me.z, rho > 0.0 ? (float)d.pot.B6 * y : 0.0f);
         if (obs) d.eatom[2 * i] = -d.pot.eps * d.pot.c * sqrt(rho);
     }
-    reinterpret_cast<float4*>(d.vposg)[s] = pg;
+    reinterpret_cast<float4*>(d.vposg)[2 * s] = pg;
 }
 
 // mode 0: forces; 1: forces and per-atom pair energies; 2: MD step (second half kick, per-atom
@@ -513,7 +516,7 @@ __global__ void __launch_bounds__(kQPassThreads, kQPassMinCtas) k_q_force(const 
     if (blockIdx.x * kQCta >= nq) return;  // the whole CTA is past the last quad
     const float4* vp = reinterpret_cast<const float4*>(d.vposg);
     float4 oi[4], CI;
-    const int n = q_own(d, vp, Q, nq, oi, CI);
+    const int n = q_own<1>(d, vp, Q, nq, oi, CI);
     const int* L = d.q_list + (size_t)min(Q, nq - 1) * kQMax;
     const float A9 = d.pot.A9f, rc2 = d.pot.rcut2f;
     const int nexp = d.pot.n, mexp = d.pot.m;
@@ -557,15 +560,16 @@ __global__ void __launch_bounds__(kQPassThreads, kQPassMinCtas) k_q_force(const 
     // the atoms are gathered one iteration ahead of their use, their list entries two ahead (past a
     // list's end: the padding quad)
     int s0 = q_entry(d, L, seg, n), s1 = q_entry(d, L, kQLanes + seg, n);
-    float4 r0 = vp[s0], c0 = d.q_ref[s0 >> 2], r1 = vp[s1], c1 = d.q_ref[s1 >> 2];
+    // the slots are 32-byte records here: the listed atom and its quad's reference point in one sector
+    float4 r0 = vp[2 * s0], c0 = vp[2 * s0 + 1], r1 = vp[2 * s1], c1 = vp[2 * s1 + 1];
     s0 = q_entry(d, L, 2 * kQLanes + seg, n);
     s1 = q_entry(d, L, 3 * kQLanes + seg, n);
     for (int k0 = 0; k0 < nw; k0 += 2 * kQLanes) {
         const float4 pp[2] = {q_shift(r0, c0, CI), q_shift(r1, c1, CI)};
-        r0 = vp[s0];
-        c0 = d.q_ref[s0 >> 2];
-        r1 = vp[s1];
-        c1 = d.q_ref[s1 >> 2];
+        r0 = vp[2 * s0];
+        c0 = vp[2 * s0 + 1];
+        r1 = vp[2 * s1];
+        c1 = vp[2 * s1 + 1];
         s0 = q_entry(d, L, k0 + 4 * kQLanes + seg, n);
         s1 = q_entry(d, L, k0 + 5 * kQLanes + seg, n);
 #pragma unroll
