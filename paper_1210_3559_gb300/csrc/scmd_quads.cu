@@ -38,6 +38,12 @@ namespace {
 
 constexpr int kQThreads = 256;  // the per-slot and list kernels (the list kernel: one warp per quad)
 constexpr float kFar = kQuadFar;  // coordinate of an empty slot: outside every cutoff of every atom
+// The quad build: one CTA of 128 threads per cell (a cell holds ~90 atoms at the fcc density), the grid
+// capped at 16 CTAs per SM (larger batches stride). With 608 CTAs striding over the cells, a CTA that
+// drew four occupied cells set the kernel's length (SM active cycles: 154 k at most against 88 k on
+// average at Ni~50000).
+constexpr int kQOrderThreads = 128;
+constexpr int kQOrderGrid = 152 * 16;
 
 // Quads by recursive bisection: a cell's n places (in atom-index order to start) form a segment; a
 // segment of more than 4 places splits into a first part of 4 * floor(q / 2) places (q: its quads)
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(1024) k_q_scan(const Dev d, int cond, int k_lo
 
 // One CTA per cell: order its atoms into quads by recursive bisection, place them, and set up each of
 // its quads.
-__global__ void __launch_bounds__(kCellThreads) k_q_order(const Dev d, int cond, int k_local) {
+__global__ void __launch_bounds__(kQOrderThreads) k_q_order(const Dev d, int cond, int k_local) {
     // per place, in the current order (two buffers): the 3 coordinates as order keys and the atom
     __shared__ int s_key[2][3][kCellCap];
     __shared__ int s_at[2][kCellCap];
@@ -684,8 +690,8 @@ cudaError_t launch_q_pos(const Dev& d, int k_local, cudaStream_t s) {
 cudaError_t launch_q_rebuild(const Dev& d, int cond, int k_local, cudaStream_t s) {
     cudaError_t e = launch_ex(k_q_scan, 1, 1024, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
-    // grid-stride kernels on about 4 CTAs per SM: most steps they only check that no rebuild is due
-    e = launch_ex(k_q_order, std::min(d.n_cells, 608), kCellThreads, 0, 0, s, d, cond, k_local);
+    // small grids: most steps these kernels only check that no rebuild is due
+    e = launch_ex(k_q_order, std::min(d.n_cells, kQOrderGrid), kQOrderThreads, 0, 0, s, d, cond, k_local);
     if (e != cudaSuccess) return e;
     return launch_ex(k_q_list, std::min(q_pass_grid(d), 608), kQThreads, 0, 0, s, d, cond, k_local);
 }
