@@ -545,7 +545,8 @@ md_status check_status(md_ctx* c) {
         return fail(c, MD_ERR_STATE, "a cell of the cell grid overflowed (more than %d atoms); forces are invalid",
                     kCellCap);
     if (s & 4)
-        return fail(c, MD_ERR_STATE, "a neighbour list overflowed (more than %d entries); forces are invalid", kVMax);
+        return fail(c, MD_ERR_STATE, "a neighbour list overflowed (more than %d entries); forces are invalid",
+                    c->nqmax > 0 ? kQMax : kVMax);
     if (s & kStatusTimeout)
         return fail(c, MD_ERR_TIMEOUT, "a pair pass gave up waiting for its partial sums; forces are invalid");
     return MD_OK;
