@@ -59,7 +59,7 @@ FORCE_SOURCES = {
     "neighbour lists": ("paper_1210_3559_gb300/csrc/scmd_quads.cu", "paper_1210_3559_gb300/csrc/scmd_device.cuh",
                         "paper_1210_3559_gb300/csrc/scmd_internal.cuh", "paper_1210_3559_gb300/csrc/scmd_cells.cuh"),
 }
-FORCE_DRAM_BYTES_PER_LAUNCH = {"batched512": (51968000 + 838144, "46cf77fc053e465f")}
+FORCE_DRAM_BYTES_PER_LAUNCH = {"batched512": (51968000 + 838144, "2a201b4d53587c99")}
 DENSITY_OPS_PER_PAIR = 8   # FP32 pipe lane-ops per ordered pair, density pass
 
 

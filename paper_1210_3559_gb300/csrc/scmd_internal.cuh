@@ -171,8 +171,8 @@ struct Dev {
                          // that float4, then the quad's reference point (float4, written at the rebuild)
     double* vxref;       // [3][nslot] positions at the last rebuild
     uint32_t* vdmax;     // [2] largest squared displacement since the rebuild (float bits), by step parity
-    // MIXED neighbour lists are lists of quads (4 consecutive slots of one cell, in Morton order within
-    // the cell; cells padded to whole quads with empty slots, vorder = -1). nslot = 4 * nqmax there.
+    // MIXED neighbour lists are kept per quad (4 consecutive slots of one cell, from a bisection of its
+    // atoms; cells padded to whole quads with empty slots, vorder = -1). nslot = 4 * nqmax there.
     int32_t nqmax;       // quads allocated
     int32_t* q_n;        // [1] quads in use since the last rebuild
     int32_t* cell_base;  // [n_cells + 1] first slot of each cell, then the end of the last
